@@ -1,0 +1,106 @@
+"""Disconnected loops L(x) = Tr[Gamma G(x;x)] (Eq. loop), exact and stochastic.
+
+* exact: G(x;x) column (beta, b) is the solution phi of D phi = e_{x,beta,b}
+  at site x (point source); L_Gamma(x) = sum_{alpha,beta,a} Gamma[beta, alpha]
+  G(x;x)[(alpha,a), (beta,a)].
+* stochastic (Eq. loop stochastic): L(x) = (1/N_r) sum_r sum_d
+  xi_d(x)^+ Gamma phi_d(x) with phi_d = D^{-1} xi_d over the dilution pieces d
+  of noise vector r (the pieces of one vector are summed, not averaged).
+* truncated solver method (Sec. II; Bali, Collins, Schafer, CPC 181 (2010)
+  1570): L = (1/N_LP) sum_{r in LP} xi_r^+ Gamma phi_r^{LP}
+           + (1/N_HP) sum_{r in HP} xi_r^+ Gamma (phi_r^{HP} - phi_r^{LP}),
+  with the HP set drawn from stream 1 and phi^{LP} from the same truncated
+  solver on both sets.
+
+Per-time-slice loops are sums (not averages) over the sites of a time slice.
+Gamma order: 1, gamma5, gamma1, gamma2, gamma3, gamma4.
+
+Parity: pinned by the free-field momentum sum, the hopping expansion to
+O(kappa^4), gauge invariance, reality and charge-conjugation properties, and
+the reduction of fully (site-)diluted noise to the exact loop
+(tests/test_oracle_loops.py, tests/test_oracle_tsm.py).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .dirac import GAMMA_SET
+from .philox import diluted_sources, z2_noise, DIL_NONE
+from .solver import solve
+
+
+def contract(src, sol):
+    """Per-site sum over the leading batch of src(x)^+ Gamma sol(x), all Gammas.
+
+    src, sol: (n, Lt, Lz, Ly, Lx, 4, 3).  Returns (Lt, Lz, Ly, Lx, 6) complex.
+    """
+    return np.einsum("n...ac,gab,n...bc->...g", np.conj(src), GAMMA_SET, sol)
+
+
+def per_timeslice(per_site):
+    """Sum a (Lt, Lz, Ly, Lx, 6) per-site array over each time slice -> (Lt, 6)."""
+    return per_site.sum(axis=(1, 2, 3))
+
+
+def point_source(dims, site_txyz, spin, colour):
+    """e_{x, spin, colour}: one at site (t, z, y, x), zero elsewhere."""
+    lx, ly, lz, lt = dims
+    e = np.zeros((lt, lz, ly, lx, 4, 3), dtype=np.complex128)
+    t, z, y, x = site_txyz
+    e[t, z, y, x, spin, colour] = 1.0
+    return e
+
+
+def exact_propagator_diag(U, kappa, dims, sites, tol=1e-12):
+    """G(x;x) as (n_sites, 4, 3, 4, 3) [alpha, a, beta, b] for the listed (t,z,y,x) sites."""
+    out = np.zeros((len(sites), 4, 3, 4, 3), dtype=np.complex128)
+    for i, s in enumerate(sites):
+        srcs = np.stack([point_source(dims, s, beta, b) for beta in range(4) for b in range(3)])
+        phi, info = solve(U, kappa, srcs, tol=tol)
+        t, z, y, x = s
+        # phi[(beta,b)] at site x is column (beta,b) of G(x;x)
+        col = phi[:, t, z, y, x]  # (12, 4, 3) = [(beta,b), alpha, a]
+        out[i] = np.transpose(col.reshape(4, 3, 4, 3), (2, 3, 0, 1))
+    return out
+
+
+def loops_from_G(Gxx):
+    """L_Gamma = Tr[Gamma G(x;x)] from (n, 4, 3, 4, 3) diagonal blocks -> (n, 6)."""
+    return np.einsum("gba,nacbc->ng", GAMMA_SET, Gxx)
+
+
+def exact_loops(U, kappa, dims, sites, tol=1e-12):
+    """Exact L_Gamma(x) (n_sites, 6) from 12 point-source solves per site."""
+    return loops_from_G(exact_propagator_diag(U, kappa, dims, sites, tol))
+
+
+def stochastic_loops(U, kappa, dims, seed, noise_indices, scheme, tol=1e-10, stream=0):
+    """Eq. (loop stochastic) with dilution; returns per-site (Lt,Lz,Ly,Lx,6) loops."""
+    acc = None
+    for r in noise_indices:
+        srcs = diluted_sources(dims, seed, r, scheme, stream)
+        phi, _ = solve(U, kappa, srcs, tol=tol)
+        c = contract(srcs, phi)
+        acc = c if acc is None else acc + c
+    return acc / len(noise_indices)
+
+
+def tsm_loops(U, kappa, dims, seed, n_lp, n_hp, tol_lp, tol_hp, scheme=DIL_NONE):
+    """Truncated solver method estimate, per site (Lt,Lz,Ly,Lx,6).
+
+    LP vectors are noise indices 0..n_lp-1 of stream 0; HP correction vectors
+    are noise indices 0..n_hp-1 of stream 1, each solved at both tolerances.
+    """
+    lp = stochastic_loops(U, kappa, dims, seed, range(n_lp), scheme, tol_lp, stream=0)
+    corr = None
+    for r in range(n_hp):
+        srcs = diluted_sources(dims, seed, r, scheme, stream=1)
+        phi_hp, _ = solve(U, kappa, srcs, tol=tol_hp)
+        phi_lp, _ = solve(U, kappa, srcs, tol=tol_lp)
+        c = contract(srcs, phi_hp - phi_lp)
+        corr = c if corr is None else corr + c
+    return lp + corr / n_hp
+
+
+__all__ = ["contract", "per_timeslice", "point_source", "exact_propagator_diag",
+           "loops_from_G", "exact_loops", "stochastic_loops", "tsm_loops", "z2_noise"]

@@ -1,0 +1,175 @@
+"""Pins of the oracle's loops L(x) = Tr[Gamma G(x;x)] (Eq. loop) and the noise estimator.
+
+* free field: G(x;x) = (1/V) sum_p D(p)^{-1} in closed form (momentum sum);
+* hopping expansion: Tr G(x;x) = 12 + kappa^4 c4(x) + O(kappa^6), with c4(x)
+  computed here by brute-force enumeration of all closed 4-step walks;
+* gauge invariance, reality / imaginarity from gamma5-hermiticity, charge
+  conjugation U -> U^*, invariance under moving the antiperiodic boundary;
+* the estimator of Eq. (loop stochastic) with noise on single
+  (site, spin, colour) pieces reproduces the exact loop.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+from lattice_inputs import haar_su3_field, unit_gauge_field, random_gauge_transform
+from oracle import dirac
+from oracle.loops import exact_loops, contract, point_source, exact_propagator_diag
+from oracle.philox import z2_noise
+
+DIMS = (4, 4, 4, 4)
+
+
+def free_field_loops(dims, kappa):
+    """(1/V) sum_p Tr[Gamma D(p)^{-1}] with antiperiodic time momenta."""
+    lx, ly, lz, lt = dims
+    V = lx * ly * lz * lt
+    out = np.zeros(6, dtype=np.complex128)
+    G6 = dirac.GAMMA_SET
+    for nx, ny, nz, nt in itertools.product(range(lx), range(ly), range(lz), range(lt)):
+        p = (2 * np.pi * nx / lx, 2 * np.pi * ny / ly, 2 * np.pi * nz / lz, (2 * nt + 1) * np.pi / lt)
+        Dp = (1 - 2 * kappa * sum(np.cos(p))) * np.eye(4) + 2j * kappa * sum(dirac.GAMMA[m] * np.sin(p[m]) for m in range(4))
+        Gp = np.linalg.inv(Dp)
+        out += 3 * np.array([np.trace(g @ Gp) for g in G6])  # colour trace of the identity = 3
+    return out / V
+
+
+def test_free_field_closed_form():
+    kappa = 0.125
+    U = unit_gauge_field(DIMS)
+    L = exact_loops(U, kappa, DIMS, [(0, 0, 0, 0), (3, 1, 2, 1)], tol=1e-13)
+    ref = free_field_loops(DIMS, kappa)
+    # scalar trace in closed form: 12/V sum_p M / (M^2 + 4 kappa^2 sum_mu sin^2 p_mu),
+    # M = 1 - 2 kappa sum_mu cos p_mu
+    lx, ly, lz, lt = DIMS
+    scal = 0.0
+    for n in itertools.product(range(lx), range(ly), range(lz), range(lt)):
+        p = np.array([2 * np.pi * n[0] / lx, 2 * np.pi * n[1] / ly, 2 * np.pi * n[2] / lz, (2 * n[3] + 1) * np.pi / lt])
+        M = 1 - 2 * kappa * np.cos(p).sum()
+        scal += 12 * M / (M * M + 4 * kappa ** 2 * (np.sin(p) ** 2).sum())
+    assert abs(ref[0] - scal / (lx * ly * lz * lt)) < 1e-12
+    for row in L:
+        assert np.max(np.abs(row - ref)) < 1e-11
+    assert np.max(np.abs(ref[1:])) < 1e-13  # gamma5 and gamma_mu loops vanish for U = 1
+
+
+def _c4_by_walks(U, dims, site):
+    """Coefficient of kappa^4 in Tr G(x;x): sum over closed 4-step walks from x of Tr[spin] Tr[colour]."""
+    lx, ly, lz, lt = dims
+    L = (lx, ly, lz, lt)
+    steps = [(mu, +1) for mu in range(4)] + [(mu, -1) for mu in range(4)]
+    x0 = list(site)  # (x, y, z, t)
+    total = 0.0 + 0.0j
+    for walk in itertools.product(steps, repeat=4):
+        pos = list(x0)
+        spin = np.eye(4, dtype=np.complex128)
+        col = np.eye(3, dtype=np.complex128)
+        sign = 1.0
+        for mu, d in walk:
+            if d > 0:
+                u = U[pos[3], pos[2], pos[1], pos[0], mu]
+                spin = spin @ (np.eye(4) - dirac.GAMMA[mu])
+                col = col @ u
+                if mu == 3 and pos[3] == lt - 1:
+                    sign = -sign
+                pos[mu] = (pos[mu] + 1) % L[mu]
+            else:
+                pos[mu] = (pos[mu] - 1) % L[mu]
+                u = U[pos[3], pos[2], pos[1], pos[0], mu]
+                spin = spin @ (np.eye(4) + dirac.GAMMA[mu])
+                col = col @ u.conj().T
+                if mu == 3 and pos[3] == lt - 1:
+                    sign = -sign
+        if pos == x0:
+            total += sign * np.trace(spin) * np.trace(col)
+    return total
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 6, 6, 6)])
+def test_hopping_expansion_kappa4(dims):
+    U = haar_su3_field(dims, 2)
+    site = (1, 0, 3, 2)  # (x, y, z, t)
+    c4 = _c4_by_walks(U, dims, site)
+    txyz = (site[3], site[2], site[1], site[0])
+    f = []
+    ks = (0.02, 0.01)
+    for k in ks:
+        L1 = exact_loops(U, k, dims, [txyz], tol=1e-14)[0, 0]
+        f.append((L1 - 12.0) / k ** 4)
+    # (L - 12)/k^4 = c4 + c6 k^2 + ...; Richardson in k^2
+    est = (f[1] * ks[0] ** 2 - f[0] * ks[1] ** 2) / (ks[0] ** 2 - ks[1] ** 2)
+    assert abs(est - c4) < 1e-3 * max(1.0, abs(c4))
+    assert abs(c4.imag) < 1e-12
+
+
+def test_hopping_expansion_free_coefficients():
+    """Free field: c4 = -1152 per site for L >= 6 and -768 on 4^4 (winding loops enter)."""
+    for dims, expect in (((4, 4, 4, 4), -768.0), ((6, 6, 6, 6), -1152.0)):
+        U = unit_gauge_field(dims)
+        assert abs(_c4_by_walks(U, dims, (0, 0, 0, 0)) - expect) < 1e-9
+
+
+def test_gauge_invariance_and_reality():
+    U = haar_su3_field(DIMS, 5)
+    kappa = 0.125
+    sites = [(0, 0, 0, 0), (2, 3, 1, 0)]
+    L = exact_loops(U, kappa, DIMS, sites, tol=1e-13)
+    g = random_gauge_transform(DIMS, 6)
+    axis = (3, 2, 1, 0)
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        Ug[..., mu, :, :] = g @ U[..., mu, :, :] @ np.conj(np.swapaxes(np.roll(g, -1, axis=axis[mu]), -1, -2))
+    Lg = exact_loops(Ug, kappa, DIMS, sites, tol=1e-13)
+    assert np.max(np.abs(L - Lg)) < 1e-10
+    # Tr G, Tr g5 G real; Tr g_mu G imaginary (gamma5-hermiticity)
+    assert np.max(np.abs(L[:, :2].imag)) < 1e-11
+    assert np.max(np.abs(L[:, 2:].real)) < 1e-11
+    assert np.max(np.abs(L[:, 2:].imag)) > 1e-4
+
+
+def test_charge_conjugation_and_boundary_move():
+    U = haar_su3_field(DIMS, 8)
+    kappa = 0.125
+    sites = [(1, 1, 2, 3)]
+    L = exact_loops(U, kappa, DIMS, sites, tol=1e-13)
+    Lc = exact_loops(np.conj(U), kappa, DIMS, sites, tol=1e-13)
+    assert np.max(np.abs(Lc[:, :2] - L[:, :2])) < 1e-10
+    assert np.max(np.abs(Lc[:, 2:] + L[:, 2:])) < 1e-10
+    # move the antiperiodic sign from the t = Lt-1 -> 0 links to the t = 1 -> 2 links
+    Um = U.copy()
+    Um[DIMS[3] - 1, :, :, :, 3] *= -1.0
+    Um[1, :, :, :, 3] *= -1.0
+    Lm = exact_loops(Um, kappa, DIMS, sites, tol=1e-13)
+    assert np.max(np.abs(Lm - L)) < 1e-10
+
+
+def test_noise_on_single_components_reproduces_exact():
+    """Eq. (loop stochastic) with each piece a single (x, spin, colour): |xi|^2 = 1 makes it exact."""
+    U = haar_su3_field(DIMS, 9)
+    kappa = 0.125
+    site = (2, 1, 0, 3)
+    xi = z2_noise(DIMS, 31, 0, 0)
+    pieces = []
+    for s in range(4):
+        for c in range(3):
+            pieces.append(point_source(DIMS, site, s, c) * xi[site + (s, c)])
+    pieces = np.stack(pieces)
+    from oracle.solver import solve
+    phi, _ = solve(U, kappa, pieces, tol=1e-13)
+    est = contract(pieces, phi)[site]
+    exact = exact_loops(U, kappa, DIMS, [site], tol=1e-13)[0]
+    assert np.max(np.abs(est - exact)) < 1e-10
+
+
+def test_propagator_diag_block_layout():
+    """G(x;x)[alpha,a,beta,b] equals the dense inverse's diagonal block."""
+    from oracle.dense import dense_D, site_index
+    dims = (2, 2, 2, 2)
+    U = haar_su3_field(dims, 4)
+    kappa = 0.15
+    G = np.linalg.inv(dense_D(U, kappa, dims))
+    t, z, y, x = (1, 0, 1, 1)
+    i = site_index(dims, x, y, z, t)
+    blk = exact_propagator_diag(U, kappa, dims, [(t, z, y, x)], tol=1e-13)[0].reshape(12, 12)
+    assert np.max(np.abs(blk - G[12 * i:12 * i + 12, 12 * i:12 * i + 12])) < 1e-11
