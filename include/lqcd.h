@@ -1,0 +1,183 @@
+/*
+ * lqcd.h -- C ABI of the GB300 disconnected-loop library.
+ *
+ * The library computes the hot path behind the exact and stochastic
+ * evaluation of disconnected fermion loops L(x) = Tr[Gamma G(x;x)] of
+ * arXiv:1108.2473 (Eq. loop, Eq. loop stochastic): many right-hand-side
+ * solves of the Wilson-Dirac operator, complex Z2 noise sources with
+ * dilution, the loop contraction, the truncated solver method, and gradients
+ * of the loops by adjoint solves.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - dims = (Lx, Ly, Lz, Lt), all even, Lx >= 2.  V = Lx*Ly*Lz*Lt.
+ *    Site index s = x + Lx*(y + Ly*(z + Lz*t)); parity (x+y+z+t) mod 2.
+ *  - Wilson-Dirac operator (the "Wilson Dirac operator M" of Sec. III):
+ *      D psi(x) = psi(x) - kappa sum_mu [ (1-gamma_mu) U_mu(x) psi(x+mu)
+ *                                       + (1+gamma_mu) U_mu(x-mu)^+ psi(x-mu) ]
+ *    periodic in space, every hop across t = Lt-1 <-> 0 multiplied by -1.
+ *    G = D^{-1}.  Gamma matrices: DeGrand-Rossi basis,
+ *      g1 = [[0,0,0,i],[0,0,i,0],[0,-i,0,0],[-i,0,0,0]]
+ *      g2 = [[0,0,0,-1],[0,0,1,0],[0,1,0,0],[-1,0,0,0]]
+ *      g3 = [[0,0,i,0],[0,0,0,-i],[-i,0,0,0],[0,i,0,0]]
+ *      g4 = [[0,0,1,0],[0,0,0,1],[1,0,0,0],[0,1,0,0]],  g5 = g1 g2 g3 g4 = diag(1,1,-1,-1).
+ *  - Gauge field layout: [V][4 (mu = x,y,z,t)][3][3] complex128 (re, im
+ *    interleaved), U[s][mu] is the link from s to s + mu.
+ *  - Colour-spinor field layout: [nrhs][V][4 spin][3 colour] complex128.
+ *  - Loop outputs: per site [V][6] and per time slice [Lt][6] complex128 with
+ *    Gamma order (1, g5, g1, g2, g3, g4); per-time-slice loops are sums over
+ *    the sites of the slice.
+ *  - Array arguments are device pointers unless a call says otherwise; the
+ *    caller owns them and the library never frees them.  Calls that accept
+ *    host pointers say so; they stage through library-owned device memory and
+ *    synchronise the stream before returning.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  Calls that return host results synchronise that stream.
+ *  - Every call returns an lqcd status (0 = LQCD_OK, < 0 = error);
+ *    lqcd_last_error() describes the most recent error.  A context is not
+ *    thread-safe: one host thread at a time per context.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lqcd_ctx lqcd_ctx;
+typedef struct lqcd_batch lqcd_batch;
+typedef struct CUstream_st *lqcd_stream_t; /* same type as cudaStream_t */
+
+/* ---- status codes ------------------------------------------------------ */
+#define LQCD_OK 0
+#define LQCD_ERR_INVALID (-1)       /* bad argument (size, pointer, enum)          */
+#define LQCD_ERR_CUDA (-2)          /* a CUDA runtime call failed                  */
+#define LQCD_ERR_NOT_CONVERGED (-3) /* iteration cap reached above tolerance       */
+#define LQCD_ERR_BREAKDOWN (-4)     /* Krylov breakdown persisted after restart    */
+#define LQCD_ERR_NONFINITE (-5)     /* NaN / Inf in a source or a reduction        */
+#define LQCD_ERR_TIMEOUT (-6)       /* wall-clock budget or a bounded wait expired */
+#define LQCD_ERR_NO_GAUGE (-7)      /* operator used before lqcd_set_gauge         */
+#define LQCD_ERR_NOT_SU3 (-8)       /* a link is not in SU(3) within 1e-12         */
+#define LQCD_ERR_OOM (-9)           /* device allocation failed                    */
+
+/* ---- enums ------------------------------------------------------------- */
+#define LQCD_PREC_FP64 0        /* FP64 storage and arithmetic throughout           */
+#define LQCD_PREC_MIXED_FP16 1  /* FP16 (+ per-site FP32 norm) spinors, FP16 links,
+                                   FP32 arithmetic, FP64 defect correction          */
+#define LQCD_PREC_MIXED_BF16 2  /* BF16 spinors, FP16 links, otherwise as above     */
+
+#define LQCD_SOLVER_BICGSTAB 0
+#define LQCD_SOLVER_CG 1 /* CG on the normal equations of the Schur operator */
+
+#define LQCD_DILUTE_NONE 0 /* one piece: the whole vector                         */
+#define LQCD_DILUTE_T 1    /* Lt pieces, piece = t                                */
+#define LQCD_DILUTE_TS 2   /* 4 Lt pieces, piece = 4 t + spin                     */
+#define LQCD_DILUTE_TSC 3  /* 12 Lt pieces, piece = 12 t + 3 spin + colour        */
+
+#define LQCD_STREAM_LP 0 /* noise stream of the plain / low-precision set      */
+#define LQCD_STREAM_HP 1 /* noise stream of the TSM high-precision correction  */
+
+/* ---- parameter and statistics records ---------------------------------- */
+typedef struct {
+  double tol;        /* target true relative residual |b - D x| / |b| (full lattice,
+                        computed in FP64), the stopping rule of Sec. III             */
+  int max_iter;      /* cap on Krylov iterations per RHS, summed over restarts      */
+  int precision;     /* LQCD_PREC_*                                                 */
+  int solver;        /* LQCD_SOLVER_*                                               */
+  double delta;      /* mixed precision: reliable update when the iterated residual
+                        drops below delta * its maximum since the last update;
+                        <= 0 selects 0.1                                            */
+  int rhs_block;     /* RHS solved together per launch; 0 = automatic (autotuned
+                        for mixed precision, 1 for FP64 = the plain solver)         */
+  double timeout_ms; /* wall-clock budget of the call; <= 0 = none                  */
+} lqcd_solver_params;
+
+typedef struct {
+  int iterations;           /* Krylov iterations (all restarts / refinement cycles) */
+  int status;               /* LQCD_OK or the per-RHS error code                    */
+  double true_rel_residual; /* |b - D x| / |b| in FP64 on the full lattice          */
+  int reliable_updates;     /* mixed precision: reliable updates performed          */
+  int restarts;             /* outer restarts / defect-correction cycles            */
+} lqcd_solve_stats;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context for one lattice on CUDA device `device`.  dims: host
+ * array of 4 ints.  Errors: LQCD_ERR_INVALID for odd or non-positive extents,
+ * LQCD_ERR_CUDA if the device cannot be selected. */
+int lqcd_create(lqcd_ctx **out, const int dims[4], int device);
+
+/* Release the context and all library-owned device memory. */
+int lqcd_destroy(lqcd_ctx *ctx);
+
+/* Text of the most recent error on ctx (NULL: of the calling thread's last
+ * context-free call).  Owned by the library; valid until the next call. */
+const char *lqcd_last_error(const lqcd_ctx *ctx);
+
+/* Upload and pack the gauge field (Sec. II: the configuration the loops are
+ * computed on).  U: [V][4][3][3] complex128, device or host pointer.  Keeps an
+ * FP64 copy, an FP32 and an FP16 reconstruct-12 copy (first two rows; the
+ * third row is (row1 x row2)^*).  Errors: LQCD_ERR_NOT_SU3 if a link deviates
+ * from unitarity or unit determinant by more than 1e-12 (nothing is kept). */
+int lqcd_set_gauge(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream);
+
+/* Set the hopping parameter kappa of D (Sec. II: kappa = 0.157 for SESAM). */
+int lqcd_set_kappa(lqcd_ctx *ctx, double kappa);
+
+/* Average plaquette (1/(18V)) sum_{x,mu<nu} Re Tr U_mu U_nu U_mu^+ U_nu^+ of
+ * the current gauge field; *plaq is a host double.  Synchronises stream. */
+int lqcd_plaquette(lqcd_ctx *ctx, double *plaq, lqcd_stream_t stream);
+
+/* out = D in (dagger = 0) or D^+ in (dagger != 0) in FP64 on the full lattice,
+ * for nrhs fields [nrhs][V][4][3] complex128 (device).  in and out must not
+ * overlap. */
+int lqcd_apply_dirac(lqcd_ctx *ctx, const double *in, double *out, int nrhs, int dagger,
+                     lqcd_stream_t stream);
+
+/* Solve D x_i = b_i for nrhs right-hand sides (Sec. II: the inversions of the
+ * all-to-all propagator; Sec. III: stopping rule |M x - b| / |b| < tol).
+ * b, x: [nrhs][V][4][3] complex128, device or host (host: staged, and the
+ * stream is synchronised).  Even-odd preconditioned BiCGstab (or CG), in FP64
+ * or mixed precision with reliable updates and FP64 defect correction.
+ * stats: host array of nrhs records, always filled.  Returns LQCD_OK only if
+ * every RHS reached tol; otherwise the first error status among the RHS.
+ * A zero b_i gives x_i = 0.  Synchronises stream. */
+int lqcd_solve_batch(lqcd_ctx *ctx, const double *b, double *x, int nrhs,
+                     const lqcd_solver_params *params, lqcd_solve_stats *stats,
+                     lqcd_stream_t stream);
+
+/* Point sources e_{x,spin,colour} (Sec. II: exact all-to-all propagator from
+ * one inversion per site, spin and colour).  sites: host array of n_sites
+ * site indices; out: [12 n_sites][V][4][3] complex128 (device), source
+ * 12 k + 3 spin + colour = e_{sites[k], spin, colour}. */
+int lqcd_point_sources(lqcd_ctx *ctx, const int64_t *sites, int n_sites, double *out,
+                       lqcd_stream_t stream);
+
+/* Complex Z2 noise (Sec. II, Eq. delta functions) with dilution.
+ * Generator: Philox4x64-10 (Salmon et al., SC'11), key = (seed, noise_stream),
+ * counter = (site, noise_index, 0, 0); bits 2k, 2k+1 of output word 0 give the
+ * signs of Re, Im of component k = 3 spin + colour; value (+-1 +- i)/sqrt(2).
+ * Writes pieces first_piece .. first_piece + n_pieces - 1 of the dilution
+ * scheme (LQCD_DILUTE_*) of noise vector noise_index: out [n_pieces][V][4][3]
+ * complex128 (device), zero outside each piece.  Bit-exact with the CPU
+ * definition.  dims: host array of 4 ints. */
+int lqcd_noise_generate(uint64_t seed, uint64_t noise_stream, uint64_t noise_index,
+                        const int dims[4], int dilution, int first_piece, int n_pieces,
+                        double *out, lqcd_stream_t stream);
+
+/* Loop contraction (Eq. loop stochastic; with point sources Eq. loop):
+ *   per_site[x][g] += weight * sum_i src_i(x)^+ Gamma_g sol_i(x)
+ *   per_t[t][g]    += weight * sum_{x in slice t} sum_i src_i(x)^+ Gamma_g sol_i(x)
+ * src, sol: [nrhs][V][4][3] complex128 (device).  per_site (may be NULL):
+ * [V][6] complex128 device; per_t (may be NULL): [Lt][6] complex128, device
+ * or host (host: the stream is synchronised).  FP64 accumulation in a fixed
+ * order (bit-reproducible). */
+int lqcd_loops_batch(lqcd_ctx *ctx, const double *src, const double *sol, int nrhs,
+                     double weight, double *per_site, double *per_t, lqcd_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LQCD_H */

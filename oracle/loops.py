@@ -74,6 +74,22 @@ def exact_loops(U, kappa, dims, sites, tol=1e-12):
     return loops_from_G(exact_propagator_diag(U, kappa, dims, sites, tol))
 
 
+def exact_loops_dense(U, kappa):
+    """Exact L_Gamma(x) at every site (Lt, Lz, Ly, Lx, 6) from the dense inverse of D.
+
+    For lattices small enough for a dense 12V x 12V inverse (4^4: 3072^2):
+    G(x;x) is the 12x12 diagonal block of numpy.linalg.inv(D).
+    """
+    from .dense import dense_D
+    from .dirac import dims_of
+    dims = dims_of(U)
+    lx, ly, lz, lt = dims
+    V = lx * ly * lz * lt
+    G = np.linalg.inv(dense_D(U, kappa, dims))
+    blocks = np.stack([G[12 * i:12 * i + 12, 12 * i:12 * i + 12] for i in range(V)]).reshape(V, 4, 3, 4, 3)
+    return loops_from_G(blocks).reshape(lt, lz, ly, lx, 6)
+
+
 def stochastic_loops(U, kappa, dims, seed, noise_indices, scheme, tol=1e-10, stream=0):
     """Eq. (loop stochastic) with dilution; returns per-site (Lt,Lz,Ly,Lx,6) loops."""
     acc = None
@@ -103,4 +119,4 @@ def tsm_loops(U, kappa, dims, seed, n_lp, n_hp, tol_lp, tol_hp, scheme=DIL_NONE)
 
 
 __all__ = ["contract", "per_timeslice", "point_source", "exact_propagator_diag",
-           "loops_from_G", "exact_loops", "stochastic_loops", "tsm_loops", "z2_noise"]
+           "loops_from_G", "exact_loops", "exact_loops_dense", "stochastic_loops", "tsm_loops", "z2_noise"]

@@ -1,0 +1,96 @@
+// Complex Z2 noise sources (Sec. II, Eq. delta functions) from Philox4x64-10
+// (Salmon, Moraes, Dror, Shaw, SC'11), with time / spin / colour dilution.
+#include "internal.cuh"
+
+namespace lqcd {
+
+// Philox4x64 round constants and Weyl key increments (SC'11).
+#define PHILOX_M0 0xD2E7470EE14C6C93ULL
+#define PHILOX_M1 0xCA5A826395121157ULL
+#define PHILOX_W0 0x9E3779B97F4A7C15ULL
+#define PHILOX_W1 0xBB67AE8584CAA73BULL
+
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += PHILOX_W0;
+      k1 += PHILOX_W1;
+    }
+    uint64_t hi0 = __umul64hi(PHILOX_M0, c[0]), lo0 = PHILOX_M0 * c[0];
+    uint64_t hi1 = __umul64hi(PHILOX_M1, c[2]), lo1 = PHILOX_M1 * c[2];
+    uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+  }
+}
+
+// One thread per (piece, site): 12 complex components of the diluted source.
+__global__ void k_noise(Geom g, uint64_t seed, uint64_t stream_tag, uint64_t noise_index, int dilution,
+                        int first_piece, int n_pieces, double2 *out) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)n_pieces * g.V) return;
+  int piece = first_piece + (int)(idx / g.V);
+  int s = (int)(idx % g.V);
+  int t = s / (g.L[0] * g.L[1] * g.L[2]);
+  int pt = -1, ps = -1, pc = -1;  // kept time slice / spin / colour (-1: all)
+  if (dilution == LQCD_DILUTE_T) {
+    pt = piece;
+  } else if (dilution == LQCD_DILUTE_TS) {
+    pt = piece / 4;
+    ps = piece % 4;
+  } else if (dilution == LQCD_DILUTE_TSC) {
+    pt = piece / 12;
+    ps = (piece % 12) / 3;
+    pc = piece % 3;
+  }
+  double2 *o = out + idx * 12;
+  if (pt >= 0 && t != pt) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = make_double2(0.0, 0.0);
+    return;
+  }
+  uint64_t c[4] = {(uint64_t)s, noise_index, 0ULL, 0ULL};
+  philox4x64_10(c, seed, stream_tag);
+  const double h = 0.70710678118654752440;  // 1/sqrt(2), correctly rounded
+  uint64_t w = c[0];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    bool keep = (ps < 0 || k / 3 == ps) && (pc < 0 || k % 3 == pc);
+    double re = ((w >> (2 * k)) & 1ULL) ? -h : h;
+    double im = ((w >> (2 * k + 1)) & 1ULL) ? -h : h;
+    o[k] = keep ? make_double2(re, im) : make_double2(0.0, 0.0);
+  }
+}
+
+}  // namespace lqcd
+
+using namespace lqcd;
+
+extern "C" int lqcd_noise_generate(uint64_t seed, uint64_t noise_stream, uint64_t noise_index, const int dims[4],
+                                   int dilution, int first_piece, int n_pieces, double *out, lqcd_stream_t stream) {
+  if (!dims || !out || n_pieces < 0 || first_piece < 0)
+    return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_noise_generate: bad argument");
+  for (int i = 0; i < 4; ++i)
+    if (dims[i] < 2 || (dims[i] & 1)) return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_noise_generate: bad dims");
+  if (dilution < LQCD_DILUTE_NONE || dilution > LQCD_DILUTE_TSC)
+    return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_noise_generate: unknown dilution %d", dilution);
+  int npieces_total = dilution == LQCD_DILUTE_NONE ? 1
+                      : dilution == LQCD_DILUTE_T  ? dims[3]
+                      : dilution == LQCD_DILUTE_TS ? 4 * dims[3]
+                                                   : 12 * dims[3];
+  if (first_piece + n_pieces > npieces_total)
+    return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_noise_generate: pieces %d..%d beyond %d", first_piece,
+                     first_piece + n_pieces - 1, npieces_total);
+  if (n_pieces == 0) return LQCD_OK;
+  Geom g = make_geom(dims);
+  size_t total = (size_t)n_pieces * g.V;
+  k_noise<<<(unsigned)((total + 255) / 256), 256, 0, (cudaStream_t)stream>>>(g, seed, noise_stream, noise_index,
+                                                                             dilution, first_piece, n_pieces,
+                                                                             (double2 *)out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(nullptr, e, "k_noise");
+  return LQCD_OK;
+}

@@ -1,0 +1,209 @@
+"""Thin ctypes binding of liblqcd (include/lqcd.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Arrays are
+torch tensors (complex128 fields, device tensors unless the C call accepts
+host memory); each is passed as its data pointer, with the current CUDA
+stream of the tensor's device.  No computation happens in Python, and there is
+no fallback: if the library is not built, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblqcd.so")
+
+LQCD_OK = 0
+LQCD_ERR_INVALID = -1
+LQCD_ERR_CUDA = -2
+LQCD_ERR_NOT_CONVERGED = -3
+LQCD_ERR_BREAKDOWN = -4
+LQCD_ERR_NONFINITE = -5
+LQCD_ERR_TIMEOUT = -6
+LQCD_ERR_NO_GAUGE = -7
+LQCD_ERR_NOT_SU3 = -8
+LQCD_ERR_OOM = -9
+STATUS_NAMES = {0: "OK", -1: "INVALID", -2: "CUDA", -3: "NOT_CONVERGED", -4: "BREAKDOWN", -5: "NONFINITE",
+                -6: "TIMEOUT", -7: "NO_GAUGE", -8: "NOT_SU3", -9: "OOM"}
+
+LQCD_PREC_FP64 = 0
+LQCD_PREC_MIXED_FP16 = 1
+LQCD_PREC_MIXED_BF16 = 2
+LQCD_SOLVER_BICGSTAB = 0
+LQCD_SOLVER_CG = 1
+LQCD_DILUTE_NONE = 0
+LQCD_DILUTE_T = 1
+LQCD_DILUTE_TS = 2
+LQCD_DILUTE_TSC = 3
+LQCD_STREAM_LP = 0
+LQCD_STREAM_HP = 1
+
+
+class LqcdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class lqcd_solver_params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("solver", ctypes.c_int), ("delta", ctypes.c_double), ("rhs_block", ctypes.c_int),
+                ("timeout_ms", ctypes.c_double)]
+
+
+class lqcd_solve_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("true_rel_residual", ctypes.c_double),
+                ("reliable_updates", ctypes.c_int), ("restarts", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def solver_params(tol=1e-10, max_iter=20000, precision=LQCD_PREC_FP64, solver=LQCD_SOLVER_BICGSTAB, delta=0.1,
+                  rhs_block=0, timeout_ms=0.0):
+    return lqcd_solver_params(tol, max_iter, precision, solver, delta, rhs_block, timeout_ms)
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+_u64 = ctypes.c_uint64
+_SIGS = {
+    "lqcd_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_i), _i]),
+    "lqcd_destroy": (_i, [_vp]),
+    "lqcd_last_error": (ctypes.c_char_p, [_vp]),
+    "lqcd_set_gauge": (_i, [_vp, _vp, _vp]),
+    "lqcd_set_kappa": (_i, [_vp, _d]),
+    "lqcd_plaquette": (_i, [_vp, ctypes.POINTER(_d), _vp]),
+    "lqcd_apply_dirac": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
+    "lqcd_solve_batch": (_i, [_vp, _vp, _vp, _i, ctypes.POINTER(lqcd_solver_params),
+                              ctypes.POINTER(lqcd_solve_stats), _vp]),
+    "lqcd_point_sources": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), _i, _vp, _vp]),
+    "lqcd_noise_generate": (_i, [_u64, _u64, _u64, ctypes.POINTER(_i), _i, _i, _i, _vp, _vp]),
+    "lqcd_loops_batch": (_i, [_vp, _vp, _vp, _i, _d, _vp, _vp, _vp]),
+}
+OPTIONAL_SIGS = {}
+
+
+def load():
+    """Load liblqcd.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise OSError(f"liblqcd.so not built at {LIB_PATH}; run paper_1108_2473_gb300.build_lib.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in list(_SIGS.items()) + list(OPTIONAL_SIGS.items()):
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def declared_symbols():
+    return sorted(list(_SIGS) + list(OPTIONAL_SIGS))
+
+
+def _err(h):
+    msg = load().lqcd_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def _check(rc, h=None):
+    if rc != LQCD_OK:
+        raise LqcdError(rc, _err(h))
+    return rc
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(t=None):
+    if t is not None and t.is_cuda:
+        return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+    if torch.cuda.is_available():
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return None
+
+
+def _dims(dims):
+    arr = (ctypes.c_int * 4)(*[int(d) for d in dims])
+    return arr
+
+
+# --------------------------------------------------------------------- calls
+def lqcd_create(dims, device=0):
+    h = ctypes.c_void_p()
+    rc = load().lqcd_create(ctypes.byref(h), _dims(dims), int(device))
+    _check(rc, None)
+    return h
+
+
+def lqcd_destroy(h):
+    return load().lqcd_destroy(h)
+
+
+def lqcd_last_error(h=None):
+    return _err(h)
+
+
+def lqcd_set_gauge(h, U):
+    """U: complex128 [V][4][3][3] (any shape with that element count), device or host."""
+    return _check(load().lqcd_set_gauge(h, _ptr(U), _stream(U)), h)
+
+
+def lqcd_set_kappa(h, kappa):
+    return _check(load().lqcd_set_kappa(h, float(kappa)), h)
+
+
+def lqcd_plaquette(h):
+    out = ctypes.c_double()
+    _check(load().lqcd_plaquette(h, ctypes.byref(out), _stream()), h)
+    return out.value
+
+
+def lqcd_apply_dirac(h, inp, out, dagger=False):
+    nrhs = inp.shape[0]
+    return _check(load().lqcd_apply_dirac(h, _ptr(inp), _ptr(out), nrhs, int(bool(dagger)), _stream(inp)), h)
+
+
+def lqcd_solve_batch(h, b, x, params):
+    """Solve D x = b for the leading dimension of b, x.  Returns (status, [stats dicts]).
+
+    Non-convergence is reported in the status and stats, not raised; argument
+    and CUDA errors raise LqcdError.
+    """
+    nrhs = b.shape[0]
+    stats = (lqcd_solve_stats * max(nrhs, 1))()
+    rc = load().lqcd_solve_batch(h, _ptr(b), _ptr(x), nrhs, ctypes.byref(params), stats, _stream(b))
+    if rc in (LQCD_ERR_INVALID, LQCD_ERR_CUDA, LQCD_ERR_NO_GAUGE, LQCD_ERR_OOM):
+        raise LqcdError(rc, _err(h))
+    return rc, [stats[k].as_dict() for k in range(nrhs)]
+
+
+def lqcd_point_sources(h, sites, out):
+    arr = (ctypes.c_int64 * len(sites))(*[int(s) for s in sites])
+    return _check(load().lqcd_point_sources(h, arr, len(sites), _ptr(out), _stream(out)), h)
+
+
+def lqcd_noise_generate(seed, noise_stream, noise_index, dims, dilution, first_piece, n_pieces, out):
+    rc = load().lqcd_noise_generate(int(seed), int(noise_stream), int(noise_index), _dims(dims), int(dilution),
+                                    int(first_piece), int(n_pieces), _ptr(out), _stream(out))
+    return _check(rc, None)
+
+
+def lqcd_loops_batch(h, src, sol, weight=1.0, per_site=None, per_t=None):
+    nrhs = src.shape[0]
+    st = _stream(src)
+    return _check(load().lqcd_loops_batch(h, _ptr(src), _ptr(sol), nrhs, float(weight), _ptr(per_site),
+                                          _ptr(per_t), st), h)

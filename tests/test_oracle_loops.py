@@ -173,3 +173,13 @@ def test_propagator_diag_block_layout():
     i = site_index(dims, x, y, z, t)
     blk = exact_propagator_diag(U, kappa, dims, [(t, z, y, x)], tol=1e-13)[0].reshape(12, 12)
     assert np.max(np.abs(blk - G[12 * i:12 * i + 12, 12 * i:12 * i + 12])) < 1e-11
+
+
+def test_dense_exact_loops_match_point_source_solves():
+    from oracle.loops import exact_loops_dense
+    U = haar_su3_field(DIMS, 0)
+    full = exact_loops_dense(U, 0.125)
+    sites = [(0, 0, 0, 0), (3, 2, 1, 0)]
+    L = exact_loops(U, 0.125, DIMS, sites, tol=1e-13)
+    for k, s in enumerate(sites):
+        assert np.max(np.abs(full[s] - L[k])) < 1e-10
