@@ -1,0 +1,381 @@
+"""Benchmark of the disconnected-loop hot path on GB300.
+
+One step = one complex Z2 noise vector, fully time+spin+colour diluted
+(12 Lt = 384 right-hand sides on 16^3 x 32), pushed through the whole path:
+noise generation -> batched mixed-precision even-odd BiCGstab to a true FP64
+relative residual of 1e-10 -> loop contraction Tr[Gamma G] per site and per
+time slice for Gamma = 1, g5, g1..g4.  Gauge field: U = exp(i eps H),
+eps = 0.35 (seed 1), kappa = 0.120; the paper's SESAM ensemble (16^3 x 32,
+Sec. II) is replaced by this synthetic field of the same shape.
+
+Metric: RHS solves per second (whole job).  The same JSON line carries the
+plain single-RHS FP64 GPU solver on a sample of the same right-hand sides,
+the roofline of the dominant kernel (reduced-precision Wilson hopping term),
+the oracle timed on the host cores, and an end-to-end number through the C ABI
+with host buffers (gauge field uploaded from pinned host memory every step,
+per-time-slice loops read back).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs independent noise vectors on its own
+GPU (replicas: no data-path collective); timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (16, 16, 16, 32)
+KAPPA = 0.120
+EPS = 0.35
+GAUGE_SEED = 1
+NOISE_SEED = 20111108
+TOL = 1e-10
+METRIC = "RHS solves/s at rel. residual 1e-10 (batched mixed FP16 vs plain FP64; dslash HBM GB/s)"
+WORKLOAD = ("16^3x32 eps=0.35 SU(3) field (seed 1), kappa=0.120, one t+s+c-diluted complex-Z2 noise vector "
+            "(384 RHS) per step: noise -> mixed FP16/FP32 BiCGstab with FP64 defect correction to 1e-10 -> loops")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP32 ALU peak of the hopping term: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+# DRAM bytes per hopping-term launch from the ncu capture summarised in
+# profiles/hop_sloppy_fp16_16x16x16x32.md (None until captured for this kernel)
+HOP_DRAM_BYTES_PER_SITE_RHS = None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index):
+        self.dev = dev_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- oracle
+def _oracle_worker(args):
+    """Solve one diluted noise source with the CPU oracle and contract it (timed)."""
+    piece, = args
+    import numpy as np
+    from lattice_inputs import eps_su3_field
+    from oracle import loops as ol, philox as oph, solver as osv
+    U = eps_su3_field(DIMS, EPS, GAUGE_SEED)
+    src = oph.dilute(oph.z2_noise(DIMS, NOISE_SEED, 0, 0), oph.DIL_TSC, piece)[None]
+    t0 = time.perf_counter()
+    phi, info = osv.solve(U, KAPPA, src, tol=TOL)
+    ol.contract(src, phi)
+    dt = time.perf_counter() - t0
+    return dt, float(info["true_rel_residual"][0])
+
+
+def _oracle_warmup():
+    from lattice_inputs import haar_su3_field, gaussian_spinors
+    from oracle import solver as osv
+    osv.solve(haar_su3_field((4, 4, 4, 4), 0), 0.125, gaussian_spinors((4, 4, 4, 4), 1, 0), tol=1e-10)
+
+
+def oracle_rate(n_workers, n_rhs):
+    """RHS solves/s of the oracle on n_rhs sources over n_workers spawned processes."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    pieces = [(17 * k) % (12 * DIMS[3]) for k in range(n_rhs)]
+    t0 = time.perf_counter()
+    with ctx.Pool(n_workers) as pool:
+        res = pool.map(_oracle_worker, [(p,) for p in pieces])
+    wall = time.perf_counter() - t0
+    busy = max(r[0] for r in res) if n_workers >= n_rhs else wall
+    return n_rhs / busy, {"rhs": n_rhs, "max_worker_s": busy, "wall_s": wall,
+                          "max_residual": max(r[1] for r in res)}
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ reference
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    cores = host_cores()
+    workers = min(cores, args.ref_rhs)
+    for _ in range(args.warmup):
+        _oracle_warmup()  # imports and one tiny 4^4 solve: the oracle keeps no state between steps
+    vals = []
+    infos = []
+    for _ in range(args.steps):
+        v, info = oracle_rate(workers, args.ref_rhs)
+        vals.append(v)
+        infos.append(info)
+    total_rhs = args.ref_rhs * args.steps
+    total_s = sum(i["max_worker_s"] for i in infos)
+    value = total_rhs / total_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "RHS solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": args.ref_rhs, "lattice": "16x16x16x32",
+                   "inputs_vs_l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": "RHS solves/s", "cores": workers, "kind": "oracle",
+                         "sample": f"{args.ref_rhs} of the 384 diluted sources per step, one per process, "
+                                   f"FP64 numpy even-odd BiCGstab to 1e-10 + contraction"},
+        "e2e": {"value": value, "unit": "RHS solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------ ours
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from lattice_inputs import eps_su3_field
+    from paper_1108_2473_gb300 import build_lib
+    build_lib.build()
+    from paper_1108_2473_gb300 import lqcd as L
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    V = int(np.prod(DIMS))
+    nrhs = args.nrhs
+    U = eps_su3_field(DIMS, EPS, GAUGE_SEED)
+    Ud = torch.from_numpy(U.reshape(-1)).to(dev)
+    Uh = torch.from_numpy(U.reshape(-1)).pin_memory()
+    h = L.lqcd_create(DIMS, local_rank)
+    L.lqcd_set_gauge(h, Ud)
+    L.lqcd_set_kappa(h, KAPPA)
+    plaq = L.lqcd_plaquette(h)
+    prec = L.LQCD_PREC_MIXED_FP16 if args.prec == "fp16" else L.LQCD_PREC_MIXED_BF16
+    params = L.solver_params(tol=TOL, precision=prec)
+    src = torch.empty((nrhs, V, 4, 3), dtype=torch.complex128, device=dev)
+    x = torch.empty_like(src)
+    per_site = torch.zeros((V, 6), dtype=torch.complex128, device=dev)
+    per_t = torch.zeros((DIMS[3], 6), dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(r, host=False):
+        if host:  # end to end: a new gauge configuration arrives from pinned host memory
+            L.lqcd_set_gauge(h, Uh)
+        L.lqcd_noise_generate(NOISE_SEED, L.LQCD_STREAM_LP, r, DIMS, L.LQCD_DILUTE_TSC, 0, nrhs, src)
+        rc, st = L.lqcd_solve_batch(h, src, x, params)
+        if rc != 0:
+            raise RuntimeError(f"solve failed: {L.STATUS_NAMES.get(rc, rc)} {st[:2]}")
+        if host:
+            pt = torch.zeros((DIMS[3], 6), dtype=torch.complex128).pin_memory()
+            L.lqcd_loops_batch(h, src, x, 1.0, per_site, pt)
+            return st, pt
+        L.lqcd_loops_batch(h, src, x, 1.0, per_site, per_t)
+        return st, None
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    base = rank * 1000003
+    for w in range(args.warmup):
+        step(base + w)
+    # ---------------------------------------------------------- timed region
+    clocks = Clocks(local_rank)
+    barrier()
+    clocks.start()
+    L.lqcd_profile_begin(h)
+    launches0 = L.lqcd_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters, resid = [], []
+    for k in range(args.steps):
+        st, _ = step(base + 100 + k)
+        iters += [s["iterations"] for s in st]
+        resid += [s["true_rel_residual"] for s in st]
+    e1.record(stream)
+    barrier()
+    launches = L.lqcd_launch_count() - launches0
+    prof = L.lqcd_profile_end(h)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    solves = nrhs * args.steps * world
+    value = solves / (t_max / 1e3)
+
+    # ---------------------------------------- end to end through the C ABI
+    for w in range(1):
+        step(base + 500 + w, host=True)
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        _, pt = step(base + 600 + k, host=True)
+        _ = pt.numpy().sum()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e_t = torch.tensor([e2e_s], device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = solves / float(e2e_t.item())
+
+    if rank != 0:
+        L.lqcd_destroy(h)
+        return
+
+    # ------------------------------- plain single-RHS FP64 on a sample
+    n64 = max(1, args.fp64_rhs)
+    xs = torch.empty((n64, V, 4, 3), dtype=torch.complex128, device=dev)
+    L.lqcd_noise_generate(NOISE_SEED, L.LQCD_STREAM_LP, base + 100, DIMS, L.LQCD_DILUTE_TSC, 0, n64, src[:n64])
+    p64 = L.solver_params(tol=TOL, precision=L.LQCD_PREC_FP64, rhs_block=1)
+    L.lqcd_solve_batch(h, src[:n64].contiguous(), xs, p64)  # warm-up
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    rc, st64 = L.lqcd_solve_batch(h, src[:n64].contiguous(), xs, p64)
+    torch.cuda.synchronize(dev)
+    fp64_rate = n64 / (time.perf_counter() - t0)
+    L.lqcd_destroy(h)
+
+    # ---------------------------------------------------------- roofline
+    peak, peak_kind = _peaks()
+    hop_s = prof["hop_ms"] / 1e3
+    achieved = prof["hop_bytes"] / hop_s / 1e9 if hop_s > 0 else 0.0
+    traffic = None
+    if HOP_DRAM_BYTES_PER_SITE_RHS is not None and prof["hop_launches"] > 0:
+        traffic = HOP_DRAM_BYTES_PER_SITE_RHS * prof["hop_site_rhs"] / prof["hop_launches"]
+    roofline = {
+        "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+        "traffic": traffic, "peak_kind": peak_kind,
+        "kernel": "k_hop_s (FP16 sloppy Wilson hopping term, all epilogues)",
+        "alg_bytes_per_launch": prof["hop_bytes"] / max(prof["hop_launches"], 1),
+        "avg_launch_ms": prof["hop_ms"] / max(prof["hop_launches"], 1),
+        "launches": prof["hop_launches"],
+        "fp32_tflops": prof["hop_flops"] / hop_s / 1e12 if hop_s > 0 else 0.0,
+        "fp32_frac_of_alu_peak": (prof["hop_flops"] / hop_s / 1e12) / FP32_PEAK_TFLOPS if hop_s > 0 else 0.0,
+        "hop_share_of_step": hop_s / (ms / 1e3),
+    }
+    # ------------------------------------------------------ CPU baseline
+    cpu = None
+    if not args.no_cpu:
+        cores = host_cores()
+        nw = min(cores, args.cpu_rhs)
+        v, info = oracle_rate(nw, args.cpu_rhs)
+        cpu = {"value": v, "unit": "RHS solves/s", "cores": nw, "kind": "oracle",
+               "sample": f"{args.cpu_rhs} of the 384 diluted sources, one per spawned process, FP64 numpy "
+                         f"even-odd BiCGstab to 1e-10 + contraction; slowest process {info['max_worker_s']:.1f} s"}
+
+    h2d = Uh.numel() * Uh.element_size()
+    d2h = DIMS[3] * 6 * 16
+    line = {
+        "metric": METRIC, "value": value, "unit": "RHS solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "fp16/fp32 (sloppy) + f64 (residual, loops)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": nrhs * world, "lattice": "16x16x16x32",
+                   "precision": args.prec, "parallelism": f"replicas x{world}",
+                   "inputs_vs_l2": "working set ~30 GB per step >> 129 MB L2 (no flush needed)",
+                   "plaquette": plaq},
+        "mixed_vs_plain_fp64": value / world / fp64_rate,
+        "fp64_plain": {"value": fp64_rate, "unit": "RHS solves/s", "sample_rhs": n64,
+                       "iterations": [s["iterations"] for s in st64]},
+        "solver": {"iterations_min": min(iters), "iterations_max": max(iters), "max_true_rel_residual": max(resid)},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "RHS solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp16", choices=["fp16", "bf16"])
+    ap.add_argument("--nrhs", type=int, default=12 * DIMS[3], help="diluted sources per step (384 = all)")
+    ap.add_argument("--fp64-rhs", type=int, default=4)
+    ap.add_argument("--cpu-rhs", type=int, default=16)
+    ap.add_argument("--ref-rhs", type=int, default=16)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -177,6 +177,31 @@ int lqcd_noise_generate(uint64_t seed, uint64_t noise_stream, uint64_t noise_ind
 int lqcd_loops_batch(lqcd_ctx *ctx, const double *src, const double *sol, int nrhs,
                      double weight, double *per_site, double *per_t, lqcd_stream_t stream);
 
+/* ---- measurement (the paper has no counterpart: instrumentation) -------- */
+
+/* Work of the dominant kernel, the reduced-precision Wilson hopping term of
+ * the mixed solver, between lqcd_profile_begin and lqcd_profile_end. */
+typedef struct {
+  long long launches;     /* kernels launched by the library on any context       */
+  long long hop_launches; /* launches of the reduced-precision hopping term       */
+  double hop_ms;          /* their summed CUDA-event durations on the solve stream */
+  double hop_site_rhs;    /* output (site, RHS) pairs they computed               */
+  double hop_bytes;       /* algorithmic bytes: one read of every input spinor and
+                             epilogue operand, one write of the output, and the
+                             links once per launch                                 */
+  double hop_flops;       /* 1320 flops per output site and RHS                    */
+} lqcd_profile;
+
+/* Start recording: events are placed around every reduced-precision hopping
+ * launch of ctx until lqcd_profile_end.  Adds a little host overhead. */
+int lqcd_profile_begin(lqcd_ctx *ctx);
+
+/* Stop recording and fill *out (host).  Synchronises the device. */
+int lqcd_profile_end(lqcd_ctx *ctx, lqcd_profile *out);
+
+/* Total kernel launches made by the library since it was loaded. */
+long long lqcd_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

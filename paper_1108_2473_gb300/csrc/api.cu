@@ -219,6 +219,8 @@ int lqcd_destroy(lqcd_ctx *ctx) {
   cudaFree(ctx->U32);
   cudaFree(ctx->U16);
   cudaFree(ctx->d_flag);
+  cudaFree(ctx->d_prof);
+  for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
   delete ctx;
   return LQCD_OK;
 }
@@ -243,7 +245,7 @@ int lqcd_set_gauge(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream) {
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(stage, U, n64 * sizeof(double2), kind, st));
   LQCD_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));
   int threads = 256, blocks = (g.V * 4 + threads - 1) / threads;
-  k_pack_gauge<<<blocks, threads, 0, st>>>(stage, g, ctx->U32, ctx->U16, ctx->d_flag);
+  KL k_pack_gauge<<<blocks, threads, 0, st>>>(stage, g, ctx->U32, ctx->U16, ctx->d_flag);
   LQCD_LAUNCH_CHECK(ctx, "k_pack_gauge");
   int flag = 0;
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -277,7 +279,7 @@ int lqcd_plaquette(lqcd_ctx *ctx, double *plaq, lqcd_stream_t stream) {
   int rc = LQCD_OK;
   double *part = (double *)workspace(ctx, WS_LOOP_PART, blocks * sizeof(double), &rc);
   if (!part) return rc;
-  k_plaquette<<<blocks, threads, 0, st>>>(ctx->U64, g, part);
+  KL k_plaquette<<<blocks, threads, 0, st>>>(ctx->U64, g, part);
   LQCD_LAUNCH_CHECK(ctx, "k_plaquette");
   std::vector<double> h(blocks);
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), part, blocks * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -354,10 +356,65 @@ int lqcd_point_sources(lqcd_ctx *ctx, const int64_t *sites, int n_sites, double 
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(dsites, sites, n_sites * sizeof(int64_t), cudaMemcpyHostToDevice, st));
   LQCD_CUDA_TRY(ctx, cudaMemsetAsync(out, 0, (size_t)12 * n_sites * g.V * 12 * sizeof(double2), st));
   size_t total = (size_t)12 * n_sites;
-  k_point_sources<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(dsites, n_sites, g.V, (double2 *)out);
+  KL k_point_sources<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(dsites, n_sites, g.V, (double2 *)out);
   LQCD_LAUNCH_CHECK(ctx, "k_point_sources");
   // the staged site list must outlive the copy: synchronise before returning
   LQCD_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  return LQCD_OK;
+}
+
+}  // extern "C"
+
+// ============================================================== profiling
+namespace lqcd {
+std::atomic<long long> g_launches{0};
+}
+
+extern "C" {
+
+long long lqcd_launch_count(void) { return lqcd::g_launches.load(); }
+
+int lqcd_profile_begin(lqcd_ctx *ctx) {
+  if (!ctx) return LQCD_ERR_INVALID;
+  cudaSetDevice(ctx->device);
+  if (!ctx->d_prof) LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->d_prof, 8 * sizeof(unsigned long long)));
+  LQCD_CUDA_TRY(ctx, cudaMemset(ctx->d_prof, 0, 8 * sizeof(unsigned long long)));
+  ctx->prof_used = 0;
+  ctx->prof_hop_launches = 0;
+  ctx->prof_launch_base = lqcd::g_launches.load();
+  ctx->prof_on = true;
+  return LQCD_OK;
+}
+
+int lqcd_profile_end(lqcd_ctx *ctx, lqcd_profile *out) {
+  if (!ctx || !out) return LQCD_ERR_INVALID;
+  cudaSetDevice(ctx->device);
+  LQCD_CUDA_TRY(ctx, cudaDeviceSynchronize());
+  ctx->prof_on = false;
+  double ms = 0.0;
+  for (size_t k = 0; k + 1 < ctx->prof_used; k += 2) {
+    float t = 0.f;
+    LQCD_CUDA_TRY(ctx, cudaEventElapsedTime(&t, ctx->prof_ev[k], ctx->prof_ev[k + 1]));
+    ms += t;
+  }
+  unsigned long long h[8] = {0};
+  if (ctx->d_prof) LQCD_CUDA_TRY(ctx, cudaMemcpy(h, ctx->d_prof, sizeof(h), cudaMemcpyDeviceToHost));
+  // h[EPI kind]: output (site, RHS) pairs computed by the sloppy hop with that epilogue;
+  // spinor operands per pair: PLAIN 2 (in, out), DOTR 4 (in, A, B, out), TS 3 (in, A, out)
+  const int operands[5] = {2, 2, 4, 3, 4};
+  double spinor_bytes = ctx->prof_prec == LQCD_PREC_MIXED_FP16 ? 52.0 : 48.0;  // 24 x 16-bit (+ FP32 norm)
+  double pairs = 0.0, bytes = 0.0;
+  for (int e = 0; e < 5; ++e) {
+    pairs += (double)h[e];
+    bytes += (double)h[e] * operands[e] * spinor_bytes;
+  }
+  bytes += (double)ctx->prof_hop_launches * ctx->geom.Vh * 8 * 24.0;  // FP16 recon-12 links once per launch
+  out->launches = lqcd::g_launches.load() - ctx->prof_launch_base;
+  out->hop_launches = ctx->prof_hop_launches;
+  out->hop_ms = ms;
+  out->hop_site_rhs = pairs;
+  out->hop_bytes = bytes;
+  out->hop_flops = 1320.0 * pairs;
   return LQCD_OK;
 }
 

@@ -104,7 +104,7 @@ int launch_hop64(lqcd_ctx *ctx, cudaStream_t st, bool dag, bool in_canon, bool o
   dim3 grid((g.Vh + 127) / 128, nrhs);
 #define HOP64_CASE(D, IC, OC)                                                                          \
   if (dag == D && in_canon == IC && out_canon == OC) {                                                 \
-    k_hop64<D, IC, OC><<<grid, 128, 0, st>>>(g, p_out, ctx->U64, in, in_stride, out, out_stride, A, cA, B, cB, \
+    KL k_hop64<D, IC, OC><<<grid, 128, 0, st>>>(g, p_out, ctx->U64, in, in_stride, out, out_stride, A, cA, B, cB, \
                                              cH, active);                                              \
     LQCD_LAUNCH_CHECK(ctx, "k_hop64");                                                                 \
     return LQCD_OK;                                                                                    \
@@ -449,9 +449,9 @@ int fp64_true_residual(lqcd_ctx *ctx, const double2 *b, const double2 *x, int nr
                       nrhs);
     if (rc) return rc;
   }
-  k_norms64<<<dim3(nb, nrhs), RED_THREADS, 0, st>>>(stride, res, b, part);
+  KL k_norms64<<<dim3(nb, nrhs), RED_THREADS, 0, st>>>(stride, res, b, part);
   LQCD_LAUNCH_CHECK(ctx, "k_norms64");
-  k_fin_norms<<<nrhs, 32, 0, st>>>(part, nb, d_rr, d_bb);
+  KL k_fin_norms<<<nrhs, 32, 0, st>>>(part, nb, d_rr, d_bb);
   LQCD_LAUNCH_CHECK(ctx, "k_fin_norms");
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(rr, d_rr, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(bb, d_bb, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -480,9 +480,9 @@ int fp64_residual_into(lqcd_ctx *ctx, const double2 *b, const double2 *x, double
                       nrhs);
     if (rc) return rc;
   }
-  k_norms64<<<dim3(nb, nrhs), RED_THREADS, 0, st>>>(stride, res, b, part);
+  KL k_norms64<<<dim3(nb, nrhs), RED_THREADS, 0, st>>>(stride, res, b, part);
   LQCD_LAUNCH_CHECK(ctx, "k_norms64");
-  k_fin_norms<<<nrhs, 32, 0, st>>>(part, nb, d_rr, d_bb);
+  KL k_fin_norms<<<nrhs, 32, 0, st>>>(part, nb, d_rr, d_bb);
   LQCD_LAUNCH_CHECK(ctx, "k_fin_norms");
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(rr, d_rr, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(bb, d_bb, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -529,8 +529,8 @@ static int fp64_solve_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrh
     if (rc) return rc;
   }
   // b_e, b_o and b_hat = b_e + kappa H_eo b_o
-  k_split64<<<gv, 128, 0, st>>>(g, 1, b, bo);
-  k_split64<<<gv, 128, 0, st>>>(g, 0, b, tmp);
+  KL k_split64<<<gv, 128, 0, st>>>(g, 1, b, bo);
+  KL k_split64<<<gv, 128, 0, st>>>(g, 0, b, tmp);
   LQCD_LAUNCH_CHECK(ctx, "k_split64");
   rc = launch_hop64(ctx, st, false, false, false, 0, bo, n, bhat, n, tmp, 1.0, nullptr, 0.0, kappa, nullptr, nrhs);
   if (rc) return rc;
@@ -551,26 +551,26 @@ static int fp64_solve_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrh
     if (rc) return rc;
     rc = launch_hop64(ctx, st, false, false, false, 0, tmp, n, r, n, bhat, 1.0, xe, -1.0, kappa * kappa, active, nrhs);
     if (rc) return rc;
-    k_dot64<<<gr, RED_THREADS, 0, st>>>(n, active, r, r, part);
-    k_fin_init<<<nrhs, 32, 0, st>>>(sc, active, part, nb, p.max_iter);
+    KL k_dot64<<<gr, RED_THREADS, 0, st>>>(n, active, r, r, part);
+    KL k_fin_init<<<nrhs, 32, 0, st>>>(sc, active, part, nb, p.max_iter);
     LQCD_LAUNCH_CHECK(ctx, "init");
     bool any = true, timed_out = false;
     while (any) {
       for (int it = 0; it < 4; ++it) {
-        k_bicg_p<<<gr, RED_THREADS, 0, st>>>(n, sc, active, r, rhat, pp, v);
+        KL k_bicg_p<<<gr, RED_THREADS, 0, st>>>(n, sc, active, r, rhat, pp, v);
         launch_hop64(ctx, st, false, false, false, 1, pp, n, tmp, n, nullptr, 0.0, nullptr, 0.0, 1.0, active, nrhs);
         launch_hop64(ctx, st, false, false, false, 0, tmp, n, v, n, pp, 1.0, nullptr, 0.0, -kappa * kappa, active,
                      nrhs);
-        k_dot64<<<gr, RED_THREADS, 0, st>>>(n, active, rhat, v, part);
-        k_fin_alpha<<<nrhs, 32, 0, st>>>(sc, active, part, nb);
-        k_bicg_s<<<gr, RED_THREADS, 0, st>>>(n, sc, active, r, v, s);
+        KL k_dot64<<<gr, RED_THREADS, 0, st>>>(n, active, rhat, v, part);
+        KL k_fin_alpha<<<nrhs, 32, 0, st>>>(sc, active, part, nb);
+        KL k_bicg_s<<<gr, RED_THREADS, 0, st>>>(n, sc, active, r, v, s);
         launch_hop64(ctx, st, false, false, false, 1, s, n, tmp, n, nullptr, 0.0, nullptr, 0.0, 1.0, active, nrhs);
         launch_hop64(ctx, st, false, false, false, 0, tmp, n, t, n, s, 1.0, nullptr, 0.0, -kappa * kappa, active,
                      nrhs);
-        k_dot_ts<<<gr, RED_THREADS, 0, st>>>(n, active, t, s, part);
-        k_fin_omega<<<nrhs, 32, 0, st>>>(sc, active, part, nb);
-        k_bicg_xr<<<gr, RED_THREADS, 0, st>>>(n, sc, active, xe, pp, s, t, r, rhat, part);
-        k_fin_conv<<<nrhs, 32, 0, st>>>(sc, active, part, nb, p.max_iter);
+        KL k_dot_ts<<<gr, RED_THREADS, 0, st>>>(n, active, t, s, part);
+        KL k_fin_omega<<<nrhs, 32, 0, st>>>(sc, active, part, nb);
+        KL k_bicg_xr<<<gr, RED_THREADS, 0, st>>>(n, sc, active, xe, pp, s, t, r, rhat, part);
+        KL k_fin_conv<<<nrhs, 32, 0, st>>>(sc, active, part, nb, p.max_iter);
       }
       LQCD_LAUNCH_CHECK(ctx, "bicgstab iteration");
       LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(hact.data(), active, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -587,8 +587,8 @@ static int fp64_solve_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrh
     // x_o = b_o + kappa H_oe x_e ; merge into canonical x
     rc = launch_hop64(ctx, st, false, false, false, 1, xe, n, tmp, n, bo, 1.0, nullptr, 0.0, kappa, nullptr, nrhs);
     if (rc) return rc;
-    k_merge64<<<gv, 128, 0, st>>>(g, 0, xe, x, nullptr);
-    k_merge64<<<gv, 128, 0, st>>>(g, 1, tmp, x, nullptr);
+    KL k_merge64<<<gv, 128, 0, st>>>(g, 0, xe, x, nullptr);
+    KL k_merge64<<<gv, 128, 0, st>>>(g, 1, tmp, x, nullptr);
     LQCD_LAUNCH_CHECK(ctx, "k_merge64");
     rc = fp64_true_residual(ctx, b, x, nrhs, rr.data(), bb.data(), st);
     if (rc) return rc;

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -162,6 +163,14 @@ struct lqcd_ctx {
   lqcd::SloppyState *sloppy = nullptr;
   std::string err;
   int *d_flag = nullptr;      // device error flag scratch
+  // profiling of the dominant kernel (sloppy hopping term)
+  bool prof_on = false;
+  unsigned long long *d_prof = nullptr;  // [8] sites processed per hop epilogue kind
+  std::vector<cudaEvent_t> prof_ev;       // start/stop pairs
+  size_t prof_used = 0;
+  long long prof_hop_launches = 0;
+  long long prof_launch_base = 0;
+  int prof_prec = 0;
 };
 
 namespace lqcd {
@@ -180,6 +189,10 @@ struct Carver {
   }
   size_t size() const { return (off + 255) & ~(size_t)255; }
 };
+
+// Kernel launches made by the library (all contexts): KL prefixes every launch.
+extern std::atomic<long long> g_launches;
+#define KL ++lqcd::g_launches,
 
 // error helpers (api.cu)
 int set_error(lqcd_ctx *ctx, int code, const char *fmt, ...);

@@ -115,11 +115,11 @@ extern "C" int lqcd_loops_batch(lqcd_ctx *ctx, const double *src, const double *
     if (host_pt)
       LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(dpt, per_t, (size_t)lt * 6 * sizeof(double2), cudaMemcpyHostToDevice, st));
   }
-  k_loops<<<dim3(nbx, lt), LOOP_THREADS, 0, st>>>(g, (const double2 *)src, (const double2 *)sol, nrhs, weight,
+  KL k_loops<<<dim3(nbx, lt), LOOP_THREADS, 0, st>>>(g, (const double2 *)src, (const double2 *)sol, nrhs, weight,
                                                   (double2 *)per_site, part);
   LQCD_LAUNCH_CHECK(ctx, "k_loops");
   if (per_t) {
-    k_loops_fin<<<lt, 32, 0, st>>>(nbx, part, dpt);
+    KL k_loops_fin<<<lt, 32, 0, st>>>(nbx, part, dpt);
     LQCD_LAUNCH_CHECK(ctx, "k_loops_fin");
     if (host_pt) {
       LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(per_t, dpt, (size_t)lt * 6 * sizeof(double2), cudaMemcpyDeviceToHost, st));

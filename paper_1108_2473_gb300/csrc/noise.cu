@@ -87,7 +87,7 @@ extern "C" int lqcd_noise_generate(uint64_t seed, uint64_t noise_stream, uint64_
   if (n_pieces == 0) return LQCD_OK;
   Geom g = make_geom(dims);
   size_t total = (size_t)n_pieces * g.V;
-  k_noise<<<(unsigned)((total + 255) / 256), 256, 0, (cudaStream_t)stream>>>(g, seed, noise_stream, noise_index,
+  KL k_noise<<<(unsigned)((total + 255) / 256), 256, 0, (cudaStream_t)stream>>>(g, seed, noise_stream, noise_index,
                                                                              dilution, first_piece, n_pieces,
                                                                              (double2 *)out);
   cudaError_t e = cudaGetLastError();

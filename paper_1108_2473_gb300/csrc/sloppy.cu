@@ -229,11 +229,12 @@ __device__ __forceinline__ void block_reduce_store(D4S v, D4S *dst) {
 template <class IN, class OUT, bool L32, int EPI>
 __global__ void __launch_bounds__(ST) k_hop_s(Geom g, int p_out, const void *links, IN in, OUT out, OUT A, OUT B,
                                               float cA, float cB, float cH, const int *list, const int *count,
-                                              D4S *part, int nbx) {
+                                              D4S *part, int nbx, unsigned long long *prof) {
   const int n_items = *count * nbx;
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
     const int rhs = list[w / nbx], sb = w % nbx;
     const int i = sb * ST + threadIdx.x;
+    if (prof && threadIdx.x == 0) atomicAdd(prof + EPI, (unsigned long long)min(ST, g.Vh - sb * ST));
     D4S red = {0, 0, 0, 0};
     if (i < g.Vh) {
       int c[4];
@@ -763,6 +764,25 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
   const double delta = p.delta > 0 ? p.delta : 0.1;
   const double floor2 = 4e-12;  // (2e-6)^2: inner FP32 target floor, relative to |b_inner|^2
 
+  // measurement of the dominant kernel (sloppy hopping term), when enabled
+  unsigned long long *prof = ctx->prof_on ? ctx->d_prof : nullptr;
+  if (ctx->prof_on) ctx->prof_prec = p.precision;
+  auto ev_begin = [&]() {
+    if (!ctx->prof_on) return;
+    while (ctx->prof_used + 2 > ctx->prof_ev.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) { ctx->prof_on = false; return; }
+      ctx->prof_ev.push_back(e);
+    }
+    cudaEventRecord(ctx->prof_ev[ctx->prof_used], st);
+  };
+  auto ev_end = [&]() {
+    if (!ctx->prof_on) return;
+    cudaEventRecord(ctx->prof_ev[ctx->prof_used + 1], st);
+    ctx->prof_used += 2;
+    ctx->prof_hop_launches++;
+  };
+
   SlopFields<S> F;
   F.r = make_sfield<S>(ss, 0, cap, vh);
   F.rhat = make_sfield<S>(ss, 1, cap, vh);
@@ -835,12 +855,12 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(unscale, hun.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sc, hs.data(), nrhs * sizeof(SState), cudaMemcpyHostToDevice, st));
     // inner right-hand side: b32 = scale (r_e + kappa H_eo r_o), o32 = scale r_o
-    k_cvt64to32<<<G, ST, 0, st>>>(g, 0, ss->r64, b32, scale, WL(cyc_list, counts + 2), nbx);
-    k_cvt64to32<<<G, ST, 0, st>>>(g, 1, ss->r64, o32, scale, WL(cyc_list, counts + 2), nbx);
-    k_hop_s<F32F, F32F, true, EPI_AXPY><<<G, ST, 0, st>>>(g, 0, ctx->U32, o32, b32, b32, b32, 1.f, 0.f, kappa,
-                                                            WL(cyc_list, counts + 2), nullptr, nbx);
-    k_blas_copy<S><<<G, ST, 0, st>>>(vh, b32, F.r, F.r, false, x32, true, WL(cyc_list, counts + 2), part, nbx);
-    k_sfin_init<<<ncyc, 32, 0, st>>>(sc, flags, WL(cyc_list, counts + 2), part, nbx);
+    KL k_cvt64to32<<<G, ST, 0, st>>>(g, 0, ss->r64, b32, scale, WL(cyc_list, counts + 2), nbx);
+    KL k_cvt64to32<<<G, ST, 0, st>>>(g, 1, ss->r64, o32, scale, WL(cyc_list, counts + 2), nbx);
+    KL k_hop_s<F32F, F32F, true, EPI_AXPY><<<G, ST, 0, st>>>(g, 0, ctx->U32, o32, b32, b32, b32, 1.f, 0.f, kappa,
+                                                            WL(cyc_list, counts + 2), nullptr, nbx, nullptr);
+    KL k_blas_copy<S><<<G, ST, 0, st>>>(vh, b32, F.r, F.r, false, x32, true, WL(cyc_list, counts + 2), part, nbx);
+    KL k_sfin_init<<<ncyc, 32, 0, st>>>(sc, flags, WL(cyc_list, counts + 2), part, nbx);
     // floor of the inner target relative to |b32|^2
     LQCD_LAUNCH_CHECK(ctx, "mixed: cycle setup");
     {
@@ -857,36 +877,44 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
       LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(flags, fl.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
       LQCD_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     }
-    k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, act_list, counts, ru_list, counts + 1);
+    KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, act_list, counts, ru_list, counts + 1);
     // ---------------------------------------------------------- inner loop
     bool any = true;
     while (any) {
       for (int it = 0; it < 4; ++it) {
-        k_blas_p<S><<<G, ST, 0, st>>>(vh, sc, F.r, F.rhat, F.p, F.v, WL(act_list, counts), nbx);
-        k_hop_s<S, S, false, EPI_PLAIN><<<G, ST, 0, st>>>(g, 1, ctx->U16, F.p, F.tmp, F.tmp, F.tmp, 0.f, 0.f, 1.f,
-                                                          WL(act_list, counts), nullptr, nbx);
-        k_hop_s<S, S, false, EPI_DOTR><<<G, ST, 0, st>>>(g, 0, ctx->U16, F.tmp, F.v, F.p, F.rhat, 1.f, 0.f, -k2,
-                                                         WL(act_list, counts), part, nbx);
-        k_sfin_alpha<<<nrhs, 32, 0, st>>>(sc, WL(act_list, counts), part, nbx);
-        k_blas_s<S><<<G, ST, 0, st>>>(vh, sc, F.r, F.v, F.s, WL(act_list, counts), nbx);
-        k_hop_s<S, S, false, EPI_PLAIN><<<G, ST, 0, st>>>(g, 1, ctx->U16, F.s, F.tmp, F.tmp, F.tmp, 0.f, 0.f, 1.f,
-                                                          WL(act_list, counts), nullptr, nbx);
-        k_hop_s<S, S, false, EPI_TS><<<G, ST, 0, st>>>(g, 0, ctx->U16, F.tmp, F.t, F.s, F.s, 1.f, 0.f, -k2,
-                                                       WL(act_list, counts), part, nbx);
-        k_sfin_omega<<<nrhs, 32, 0, st>>>(sc, WL(act_list, counts), part, nbx);
-        k_blas_xr<S><<<G, ST, 0, st>>>(vh, sc, x32, F.p, F.s, F.t, F.r, F.rhat, WL(act_list, counts), part, nbx);
-        k_sfin_conv<<<nrhs, 32, 0, st>>>(sc, flags, WL(act_list, counts), part, nbx, delta * delta, p.max_iter);
-        k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, act_list, counts, ru_list, counts + 1);
+        KL k_blas_p<S><<<G, ST, 0, st>>>(vh, sc, F.r, F.rhat, F.p, F.v, WL(act_list, counts), nbx);
+        ev_begin();
+        KL k_hop_s<S, S, false, EPI_PLAIN><<<G, ST, 0, st>>>(g, 1, ctx->U16, F.p, F.tmp, F.tmp, F.tmp, 0.f, 0.f, 1.f,
+                                                          WL(act_list, counts), nullptr, nbx, prof);
+        ev_end();
+        ev_begin();
+        KL k_hop_s<S, S, false, EPI_DOTR><<<G, ST, 0, st>>>(g, 0, ctx->U16, F.tmp, F.v, F.p, F.rhat, 1.f, 0.f, -k2,
+                                                         WL(act_list, counts), part, nbx, prof);
+        ev_end();
+        KL k_sfin_alpha<<<nrhs, 32, 0, st>>>(sc, WL(act_list, counts), part, nbx);
+        KL k_blas_s<S><<<G, ST, 0, st>>>(vh, sc, F.r, F.v, F.s, WL(act_list, counts), nbx);
+        ev_begin();
+        KL k_hop_s<S, S, false, EPI_PLAIN><<<G, ST, 0, st>>>(g, 1, ctx->U16, F.s, F.tmp, F.tmp, F.tmp, 0.f, 0.f, 1.f,
+                                                          WL(act_list, counts), nullptr, nbx, prof);
+        ev_end();
+        ev_begin();
+        KL k_hop_s<S, S, false, EPI_TS><<<G, ST, 0, st>>>(g, 0, ctx->U16, F.tmp, F.t, F.s, F.s, 1.f, 0.f, -k2,
+                                                       WL(act_list, counts), part, nbx, prof);
+        ev_end();
+        KL k_sfin_omega<<<nrhs, 32, 0, st>>>(sc, WL(act_list, counts), part, nbx);
+        KL k_blas_xr<S><<<G, ST, 0, st>>>(vh, sc, x32, F.p, F.s, F.t, F.r, F.rhat, WL(act_list, counts), part, nbx);
+        KL k_sfin_conv<<<nrhs, 32, 0, st>>>(sc, flags, WL(act_list, counts), part, nbx, delta * delta, p.max_iter);
+        KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, act_list, counts, ru_list, counts + 1);
         // reliable update in FP32: r32 = b32 - x32 + kappa^2 H_eo H_oe x32
-        k_hop_s<F32F, F32F, true, EPI_PLAIN><<<G, ST, 0, st>>>(g, 1, ctx->U32, x32, t32, t32, t32, 0.f, 0.f, 1.f,
-                                                               WL(ru_list, counts + 1), nullptr, nbx);
-        k_hop_s<F32F, F32F, true, EPI_RES><<<G, ST, 0, st>>>(g, 0, ctx->U32, t32, r32, b32, x32, 1.f, -1.f, k2,
-                                                             WL(ru_list, counts + 1), part, nbx);
-        k_sfin_ru<<<nrhs, 32, 0, st>>>(sc, flags, WL(ru_list, counts + 1), part, nbx, p.max_iter);
-        k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, act_list, counts, ru_list, counts + 1);
-        k_blas_copy<S><<<G, ST, 0, st>>>(vh, r32, F.r, F.rhat, true, x32, false, WL(ru_list, counts + 1), part, nbx);
-        k_sfin_ru2<<<nrhs, 32, 0, st>>>(sc, flags, WL(ru_list, counts + 1), part, nbx);
-        k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, act_list, counts, ru_list, counts + 1);
+        KL k_hop_s<F32F, F32F, true, EPI_PLAIN><<<G, ST, 0, st>>>(g, 1, ctx->U32, x32, t32, t32, t32, 0.f, 0.f, 1.f,
+                                                               WL(ru_list, counts + 1), nullptr, nbx, nullptr);
+        KL k_hop_s<F32F, F32F, true, EPI_RES><<<G, ST, 0, st>>>(g, 0, ctx->U32, t32, r32, b32, x32, 1.f, -1.f, k2,
+                                                             WL(ru_list, counts + 1), part, nbx, nullptr);
+        KL k_sfin_ru<<<nrhs, 32, 0, st>>>(sc, flags, WL(ru_list, counts + 1), part, nbx, p.max_iter);
+        KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, act_list, counts, ru_list, counts + 1);
+        KL k_blas_copy<S><<<G, ST, 0, st>>>(vh, r32, F.r, F.rhat, true, x32, false, WL(ru_list, counts + 1), part, nbx);
+        KL k_sfin_ru2<<<nrhs, 32, 0, st>>>(sc, flags, WL(ru_list, counts + 1), part, nbx);
+        KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, act_list, counts, ru_list, counts + 1);
       }
       LQCD_LAUNCH_CHECK(ctx, "mixed: iteration");
       LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(ss->h_counts, counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -898,10 +926,10 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
       }
     }
     // odd half of the correction: e_o = o32 + kappa H_oe x32; x += |r| e
-    k_hop_s<F32F, F32F, true, EPI_AXPY><<<G, ST, 0, st>>>(g, 1, ctx->U32, x32, o32, o32, o32, 1.f, 0.f, kappa,
-                                                            WL(cyc_list, counts + 2), nullptr, nbx);
-    k_accum64<<<G, ST, 0, st>>>(g, 0, x32, x, unscale, WL(cyc_list, counts + 2), nbx);
-    k_accum64<<<G, ST, 0, st>>>(g, 1, o32, x, unscale, WL(cyc_list, counts + 2), nbx);
+    KL k_hop_s<F32F, F32F, true, EPI_AXPY><<<G, ST, 0, st>>>(g, 1, ctx->U32, x32, o32, o32, o32, 1.f, 0.f, kappa,
+                                                            WL(cyc_list, counts + 2), nullptr, nbx, nullptr);
+    KL k_accum64<<<G, ST, 0, st>>>(g, 0, x32, x, unscale, WL(cyc_list, counts + 2), nbx);
+    KL k_accum64<<<G, ST, 0, st>>>(g, 1, o32, x, unscale, WL(cyc_list, counts + 2), nbx);
     LQCD_LAUNCH_CHECK(ctx, "mixed: correction");
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(hs.data(), sc, nrhs * sizeof(SState), cudaMemcpyDeviceToHost, st));
     LQCD_CUDA_TRY(ctx, cudaStreamSynchronize(st));

@@ -62,6 +62,14 @@ class lqcd_solve_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class lqcd_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("hop_launches", ctypes.c_longlong), ("hop_ms", ctypes.c_double),
+                ("hop_site_rhs", ctypes.c_double), ("hop_bytes", ctypes.c_double), ("hop_flops", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def solver_params(tol=1e-10, max_iter=20000, precision=LQCD_PREC_FP64, solver=LQCD_SOLVER_BICGSTAB, delta=0.1,
                   rhs_block=0, timeout_ms=0.0):
     return lqcd_solver_params(tol, max_iter, precision, solver, delta, rhs_block, timeout_ms)
@@ -85,6 +93,9 @@ _SIGS = {
     "lqcd_point_sources": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), _i, _vp, _vp]),
     "lqcd_noise_generate": (_i, [_u64, _u64, _u64, ctypes.POINTER(_i), _i, _i, _i, _vp, _vp]),
     "lqcd_loops_batch": (_i, [_vp, _vp, _vp, _i, _d, _vp, _vp, _vp]),
+    "lqcd_profile_begin": (_i, [_vp]),
+    "lqcd_profile_end": (_i, [_vp, ctypes.POINTER(lqcd_profile)]),
+    "lqcd_launch_count": (ctypes.c_longlong, []),
 }
 OPTIONAL_SIGS = {}
 
@@ -207,3 +218,17 @@ def lqcd_loops_batch(h, src, sol, weight=1.0, per_site=None, per_t=None):
     st = _stream(src)
     return _check(load().lqcd_loops_batch(h, _ptr(src), _ptr(sol), nrhs, float(weight), _ptr(per_site),
                                           _ptr(per_t), st), h)
+
+
+def lqcd_profile_begin(h):
+    return _check(load().lqcd_profile_begin(h), h)
+
+
+def lqcd_profile_end(h):
+    out = lqcd_profile()
+    _check(load().lqcd_profile_end(h, ctypes.byref(out)), h)
+    return out.as_dict()
+
+
+def lqcd_launch_count():
+    return int(load().lqcd_launch_count())
