@@ -177,7 +177,31 @@ int lqcd_noise_generate(uint64_t seed, uint64_t noise_stream, uint64_t noise_ind
 int lqcd_loops_batch(lqcd_ctx *ctx, const double *src, const double *sol, int nrhs,
                      double weight, double *per_site, double *per_t, lqcd_stream_t stream);
 
-/* ---- measurement (the paper has no counterpart: instrumentation) -------- */
+/* No-allocation variant of lqcd_loops_batch.  The paper has no counterpart:
+ * this exists for callers that cannot allocate device memory -- code that
+ * runs while a CUDA graph is being captured, where cudaMalloc/cudaFree are not
+ * allowed or would synchronise the device; frameworks whose caching allocator
+ * already holds the GPU's memory; latency-critical pipelines in which the
+ * implicit device synchronisation of cudaFree would stall other streams.  It
+ * needs no context (lqcd_create allocates) and calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *
+ * Same result as lqcd_loops_batch (accumulating into per_site / per_t) for the
+ * lattice dims (host array of 4 ints, all even).  All arrays must be device
+ * memory.  The per-time-slice partial sums use a fixed 768 KiB device array
+ * inside the library: each GPU that loads the library holds it until the
+ * process exits.  Limit: Lt * ceil(Lx*Ly*Lz / 128) <= 8192 when per_t is
+ * given (24^3 x 48 needs 5184); larger lattices are rejected with
+ * LQCD_ERR_INVALID.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  All calls on a device share the array, so
+ * calls whose work overlaps on the GPU (different streams, or host threads)
+ * race and must be serialised by the caller; every partial is rewritten by
+ * each call, so nothing needs clearing in between. */
+int lqcd_loops_batch_noalloc(const int dims[4], const double *src, const double *sol, int nrhs, double weight,
+                             double *per_site, double *per_t, lqcd_stream_t stream);
+
+/* ---- measurement (instrumentation, not part of the method) -------------- */
 
 /* Work of the dominant kernel, the reduced-precision Wilson hopping term of
  * the mixed solver, between lqcd_profile_begin and lqcd_profile_end. */

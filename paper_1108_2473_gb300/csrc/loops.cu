@@ -128,3 +128,86 @@ extern "C" int lqcd_loops_batch(lqcd_ctx *ctx, const double *src, const double *
   }
   return LQCD_OK;
 }
+
+// ===================================================== no-allocation variant
+// lqcd_loops_batch_noalloc: the same contraction kernels as lqcd_loops_batch,
+// for callers that must not allocate device memory.  The per-time-slice
+// partial sums, which lqcd_loops_batch keeps in a context workspace, live here
+// in one file-scope device array of fixed size instead.  That array exists on
+// every GPU that loads this library, from module load until process exit.
+#include <mutex>
+
+namespace lqcd {
+
+// Capacity in partial blocks: Lt * ceil(Lx*Ly*Lz / LOOP_THREADS) must not exceed it.
+// 8192 blocks x 6 complex128 = 768 KiB per device (e.g. 24^3 x 48 needs 5184).
+#define LQCD_NOALLOC_MAX_PARTIALS 8192
+static __device__ __align__(256) double2 g_noalloc_partials[LQCD_NOALLOC_MAX_PARTIALS * 6];
+
+// Host-side record of the array's device address, looked up once per device.
+// In host code the symbol g_noalloc_partials is only a host stand-in; a kernel
+// must be given the address returned by cudaGetSymbolAddress.
+static double2 *g_noalloc_addr[64];
+static std::mutex g_noalloc_mu;
+
+static int noalloc_scratch(double2 **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_error(nullptr, e, "lqcd_loops_batch_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= 64) return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_loops_batch_noalloc: device %d", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_partials);  // with device `dev` current
+    if (e != cudaSuccess || !p)
+      return cuda_error(nullptr, e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                        "lqcd_loops_batch_noalloc: cudaGetSymbolAddress");
+    g_noalloc_addr[dev] = (double2 *)p;
+  }
+  *out = g_noalloc_addr[dev];
+  return LQCD_OK;
+}
+
+}  // namespace lqcd
+
+extern "C" int lqcd_loops_batch_noalloc(const int dims[4], const double *src, const double *sol, int nrhs,
+                                        double weight, double *per_site, double *per_t, lqcd_stream_t stream) {
+  if (!dims || nrhs < 0 || (nrhs > 0 && (!src || !sol)))
+    return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_loops_batch_noalloc: bad argument");
+  for (int i = 0; i < 4; ++i)
+    if (dims[i] < 2 || (dims[i] & 1))
+      return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_loops_batch_noalloc: extent %d = %d must be even and >= 2",
+                       i, dims[i]);
+  Geom g = make_geom(dims);
+  int vs = g.L[0] * g.L[1] * g.L[2], lt = g.L[3];
+  int nbx = (vs + LOOP_THREADS - 1) / LOOP_THREADS;
+  long long need = (long long)lt * nbx;
+  if (per_t && need > LQCD_NOALLOC_MAX_PARTIALS)
+    return set_error(nullptr, LQCD_ERR_INVALID,
+                     "lqcd_loops_batch_noalloc: lattice needs %lld partial blocks (Lt * ceil(Lx*Ly*Lz/%d)); the fixed "
+                     "scratch holds %d -- use lqcd_loops_batch",
+                     need, LOOP_THREADS, LQCD_NOALLOC_MAX_PARTIALS);
+  if (nrhs == 0 || (!per_site && !per_t)) return LQCD_OK;
+  const void *ptrs[4] = {src, sol, per_site, per_t};
+  for (const void *q : ptrs)
+    if (q && !is_device_ptr(q))
+      return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_loops_batch_noalloc: all arrays must be device memory");
+  double2 *part = nullptr;
+  if (per_t) {
+    int rc = noalloc_scratch(&part);
+    if (rc) return rc;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // every partial read by k_loops_fin is written by k_loops in the same call,
+  // so the scratch needs no clearing
+  KL k_loops<<<dim3(nbx, lt), LOOP_THREADS, 0, st>>>(g, (const double2 *)src, (const double2 *)sol, nrhs, weight,
+                                                     (double2 *)per_site, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(nullptr, e, "lqcd_loops_batch_noalloc: k_loops");
+  if (per_t) {
+    KL k_loops_fin<<<lt, 32, 0, st>>>(nbx, part, (double2 *)per_t);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_error(nullptr, e, "lqcd_loops_batch_noalloc: k_loops_fin");
+  }
+  return LQCD_OK;
+}

@@ -93,6 +93,7 @@ _SIGS = {
     "lqcd_point_sources": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), _i, _vp, _vp]),
     "lqcd_noise_generate": (_i, [_u64, _u64, _u64, ctypes.POINTER(_i), _i, _i, _i, _vp, _vp]),
     "lqcd_loops_batch": (_i, [_vp, _vp, _vp, _i, _d, _vp, _vp, _vp]),
+    "lqcd_loops_batch_noalloc": (_i, [ctypes.POINTER(_i), _vp, _vp, _i, _d, _vp, _vp, _vp]),
     "lqcd_profile_begin": (_i, [_vp]),
     "lqcd_profile_end": (_i, [_vp, ctypes.POINTER(lqcd_profile)]),
     "lqcd_launch_count": (ctypes.c_longlong, []),
@@ -232,3 +233,16 @@ def lqcd_profile_end(h):
 
 def lqcd_launch_count():
     return int(load().lqcd_launch_count())
+
+
+def lqcd_loops_batch_noalloc(dims, src, sol, weight=1.0, per_site=None, per_t=None):
+    """Loop contraction that allocates no device memory (see include/lqcd.h).
+
+    For callers that cannot allocate: it needs no context and uses a fixed
+    device array inside the library for its partial sums.  All tensors must be
+    on the current CUDA device.
+    """
+    nrhs = src.shape[0]
+    rc = load().lqcd_loops_batch_noalloc(_dims(dims), _ptr(src), _ptr(sol), nrhs, float(weight), _ptr(per_site),
+                                         _ptr(per_t), _stream(src))
+    return _check(rc, None)
