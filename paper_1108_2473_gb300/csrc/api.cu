@@ -68,7 +68,7 @@ __device__ __forceinline__ double2 dmul(double2 a, double2 b) { return cmul(a, b
 
 // Check unitarity and unit determinant of every link; write the FP32 and FP16
 // reconstruct-12 copies (rows 0 and 1) in parity-split SoA order.
-__global__ void k_pack_gauge(const double2 *__restrict__ U, Geom g, float4 *U32, uint2 *U16, int *flag) {
+__global__ void k_pack_gauge(const double2 *__restrict__ U, Geom g, float4 *U32, uint4 *U16, int *flag) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.V * 4) return;
   int s = idx >> 2, mu = idx & 3;
@@ -103,16 +103,18 @@ __global__ void k_pack_gauge(const double2 *__restrict__ U, Geom g, float4 *U32,
     v[2 * k] = (float)m[k / 3][k % 3].x;
     v[2 * k + 1] = (float)m[k / 3][k % 3].y;
   }
+  // FP16 copy for the pair kernels: every real stored twice, (u, u), so one
+  // half2 -> float2 conversion gives the operand both members of a pair use
+  unsigned w[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    __half2 hh = __float2half2_rn(v[k]);
+    w[k] = *reinterpret_cast<unsigned *>(&hh);
+  }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     U32[base + (size_t)k * g.Vh] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-    __half2 h0 = __floats2half2_rn((float)m[(2 * k) / 3][(2 * k) % 3].x, (float)m[(2 * k) / 3][(2 * k) % 3].y);
-    __half2 h1 = __floats2half2_rn((float)m[(2 * k + 1) / 3][(2 * k + 1) % 3].x,
-                                   (float)m[(2 * k + 1) / 3][(2 * k + 1) % 3].y);
-    uint2 w;
-    w.x = *reinterpret_cast<unsigned *>(&h0);
-    w.y = *reinterpret_cast<unsigned *>(&h1);
-    U16[base + (size_t)k * g.Vh] = w;
+    U16[base + (size_t)k * g.Vh] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
   }
 }
 
@@ -236,7 +238,7 @@ int lqcd_set_gauge(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream) {
   if (!ctx->U64) {
     LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->U64, n64 * sizeof(double2)));
     LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->U32, (size_t)g.V * 4 * 3 * sizeof(float4)));
-    LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->U16, (size_t)g.V * 4 * 3 * sizeof(uint2)));
+    LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->U16, (size_t)g.V * 4 * 3 * sizeof(uint4)));
   }
   int st_ = LQCD_OK;
   double2 *stage = (double2 *)workspace(ctx, WS_STAGE_AUX, n64 * sizeof(double2), &st_);
@@ -408,7 +410,7 @@ int lqcd_profile_end(lqcd_ctx *ctx, lqcd_profile *out) {
     pairs += (double)h[e];
     bytes += (double)h[e] * operands[e] * spinor_bytes;
   }
-  bytes += (double)ctx->prof_hop_launches * ctx->geom.Vh * 8 * 24.0;  // FP16 recon-12 links once per launch
+  bytes += (double)ctx->prof_hop_launches * ctx->geom.Vh * 8 * 48.0;  // FP16 (u,u) recon-12 links once per launch
   out->launches = lqcd::g_launches.load() - ctx->prof_launch_base;
   out->hop_launches = ctx->prof_hop_launches;
   out->hop_ms = ms;

@@ -459,13 +459,52 @@ int fp64_true_residual(lqcd_ctx *ctx, const double2 *b, const double2 *x, int nr
   return LQCD_OK;
 }
 
-// res = b - D x (canonical FP64) and per-RHS |res|^2, |b|^2 (host arrays)
+// res = b - x + kappa H x at the sites of parity p (canonical layout), with
+// per-block partials of |res|^2 (.c) and |b|^2 (.d) at part[rhs][p * nblk + block]
+__global__ void __launch_bounds__(128) k_resid64(Geom g, int p_out, const double2 *__restrict__ U,
+                                                 const double2 *__restrict__ x, const double2 *__restrict__ b,
+                                                 double2 *res, double kappa, D4 *part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rhs = blockIdx.y;
+  const size_t stride = (size_t)g.V * 12;
+  D4 nrm = {0, 0, 0, 0};
+  if (i < g.Vh) {
+    int c[4];
+    coords_of(g, p_out, i, c);
+    int s = site_of(g, c);
+    double2 acc[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) acc[a][q] = make_double2(0.0, 0.0);
+    const double2 *xr = x + (size_t)rhs * stride;
+    hop_dir64<0, false, true>(g, c, s, xr, U, acc);
+    hop_dir64<1, false, true>(g, c, s, xr, U, acc);
+    hop_dir64<2, false, true>(g, c, s, xr, U, acc);
+    hop_dir64<3, false, true>(g, c, s, xr, U, acc);
+    size_t o = (size_t)rhs * stride + (size_t)s * 12;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double2 bk = b[o + k], xk = x[o + k];
+      double2 v = cadd(csub(bk, xk), cscale(acc[k / 3][k % 3], kappa));
+      res[o + k] = v;
+      nrm.c += v.x * v.x + v.y * v.y;
+      nrm.d += bk.x * bk.x + bk.y * bk.y;
+    }
+  }
+  D4 t = block_sum4(nrm);
+  if (threadIdx.x == 0) part[(size_t)rhs * 2 * gridDim.x + (size_t)p_out * gridDim.x + blockIdx.x] = t;
+}
+
+// res = b - D x (canonical FP64) and per-RHS |res|^2, |b|^2 (host arrays).
+// With x = null the residual is b itself: only the norms are computed.
 int fp64_residual_into(lqcd_ctx *ctx, const double2 *b, const double2 *x, double2 *res, int nrhs, double *rr,
                        double *bb, cudaStream_t st) {
   const Geom &g = ctx->geom;
   size_t stride = (size_t)g.V * 12;
   int rc = LQCD_OK;
-  int nb = red_blocks(stride);
+  int nblk = (g.Vh + 127) / 128;
+  int nb = x ? 2 * nblk : red_blocks(stride);
   Carver sizing(nullptr);
   sizing.take<D4>((size_t)nrhs * nb);
   sizing.take<double>(2 * (size_t)nrhs);
@@ -475,13 +514,15 @@ int fp64_residual_into(lqcd_ctx *ctx, const double2 *b, const double2 *x, double
   D4 *part = cv.take<D4>((size_t)nrhs * nb);
   double *d_rr = cv.take<double>(2 * (size_t)nrhs);
   double *d_bb = d_rr + nrhs;
-  for (int p = 0; p < 2; ++p) {
-    rc = launch_hop64(ctx, st, false, true, true, p, x, stride, res, stride, b, 1.0, x, -1.0, ctx->kappa, nullptr,
-                      nrhs);
-    if (rc) return rc;
+  if (x) {
+    for (int p = 0; p < 2; ++p) {
+      KL k_resid64<<<dim3(nblk, nrhs), 128, 0, st>>>(g, p, ctx->U64, x, b, res, ctx->kappa, part);
+      LQCD_LAUNCH_CHECK(ctx, "k_resid64");
+    }
+  } else {
+    KL k_norms64<<<dim3(nb, nrhs), RED_THREADS, 0, st>>>(stride, b, b, part);
+    LQCD_LAUNCH_CHECK(ctx, "k_norms64");
   }
-  KL k_norms64<<<dim3(nb, nrhs), RED_THREADS, 0, st>>>(stride, res, b, part);
-  LQCD_LAUNCH_CHECK(ctx, "k_norms64");
   KL k_fin_norms<<<nrhs, 32, 0, st>>>(part, nb, d_rr, d_bb);
   LQCD_LAUNCH_CHECK(ctx, "k_fin_norms");
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(rr, d_rr, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -133,13 +133,6 @@ __device__ __forceinline__ void su3_mul(const C u[3][3], const C h[2][3], C x[2]
   }
 }
 
-// Gamma insertion of a loop, Gamma order (1, g5, g1, g2, g3, g4):
-// (Gamma psi)_a = phase[g][a] * psi_{perm[g][a]}; phase index 0:+1 1:-1 2:+i 3:-i.
-static __constant__ const int kGammaPerm[6][4] = {
-    {0, 1, 2, 3}, {0, 1, 2, 3}, {3, 2, 1, 0}, {3, 2, 1, 0}, {2, 3, 0, 1}, {2, 3, 0, 1}};
-static __constant__ const int kGammaPhase[6][4] = {
-    {0, 0, 0, 0}, {0, 0, 1, 1}, {2, 2, 3, 3}, {1, 0, 0, 1}, {2, 3, 3, 2}, {0, 0, 0, 0}};
-
 // ------------------------------------------------------------------ context
 struct DevBuf {
   void *p = nullptr;
@@ -158,7 +151,7 @@ struct lqcd_ctx {
   bool have_gauge = false;
   double2 *U64 = nullptr;     // canonical [V][4][3][3]
   float4 *U32 = nullptr;      // recon-12 FP32  [2 parity][4 mu][3 float4][Vh]
-  uint2 *U16 = nullptr;       // recon-12 FP16  [2 parity][4 mu][3 uint2 (4 halves)][Vh]
+  uint4 *U16 = nullptr;       // recon-12 FP16, each real twice  [2 parity][4 mu][3 uint4][Vh]
   std::vector<lqcd::DevBuf> ws;  // named workspaces, grow-only
   lqcd::SloppyState *sloppy = nullptr;
   std::string err;

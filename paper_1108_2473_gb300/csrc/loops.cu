@@ -7,6 +7,19 @@
 
 namespace lqcd {
 
+// Gamma insertion of a loop, Gamma order (1, g5, g1, g2, g3, g4), DeGrand-Rossi:
+// row a of Gamma has its one non-zero entry in column gamma_col(g, a), equal to
+// +1, -1, +i, -i for gamma_ph(g, a) = 0, 1, 2, 3.  Compile-time after unrolling.
+__host__ __device__ constexpr int gamma_col(int g, int a) { return g < 2 ? a : (g < 4 ? 3 - a : (a + 2) & 3); }
+__host__ __device__ constexpr int gamma_ph(int g, int a) {
+  return g == 0 ? 0
+         : g == 1 ? (a < 2 ? 0 : 1)
+         : g == 2 ? (a < 2 ? 2 : 3)
+         : g == 3 ? ((a == 0 || a == 3) ? 1 : 0)
+         : g == 4 ? ((a == 0 || a == 3) ? 2 : 3)
+                  : 0;
+}
+
 __device__ __forceinline__ double2 gamma_phase(int ph, double2 v) {
   switch (ph) {
     case 0: return v;
@@ -31,6 +44,7 @@ __global__ void __launch_bounds__(LOOP_THREADS) k_loops(Geom g, const double2 *_
   for (int k = 0; k < 6; ++k) acc[k] = make_double2(0.0, 0.0);
   if (xs < vs) {
     size_t s = (size_t)t * vs + xs;
+#pragma unroll 2
     for (int i = 0; i < nrhs; ++i) {
       const double2 *a = src + ((size_t)i * g.V + s) * 12;
       const double2 *b = sol + ((size_t)i * g.V + s) * 12;
@@ -45,8 +59,8 @@ __global__ void __launch_bounds__(LOOP_THREADS) k_loops(Geom g, const double2 *_
         double2 sum = make_double2(0.0, 0.0);
 #pragma unroll
         for (int al = 0; al < 4; ++al) {
-          int be = kGammaPerm[gi][al];
-          int ph = kGammaPhase[gi][al];
+          const int be = gamma_col(gi, al);
+          const int ph = gamma_ph(gi, al);
 #pragma unroll
           for (int c = 0; c < 3; ++c) sum = cadd(sum, cmulc(ea[al * 3 + c], gamma_phase(ph, eb[be * 3 + c])));
         }

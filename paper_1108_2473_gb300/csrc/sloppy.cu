@@ -1,26 +1,36 @@
-// Mixed-precision many-RHS solver (Sec. II: QUDA-style mixed-precision
-// BiCGstab for the all-to-all inversions; Sec. III: stop on the true
-// relative residual |M x - b| / |b| of the full operator).
+// Mixed-precision many-RHS solver (Sec. II: mixed-precision BiCGstab for the
+// all-to-all inversions; Sec. III: stop on the true relative residual
+// |M x - b| / |b| of the full operator).
 //
 // Three precision levels:
-//   * sloppy  -- Krylov vectors stored as FP16 with one FP32 norm per site
-//               (values scaled into [-1, 1]) or as BF16; links as FP16
-//               reconstruct-12; all arithmetic in FP32;
+//   * sloppy  -- Krylov vectors stored as FP16 (with one FP32 norm per site
+//               and RHS, values scaled into [-1, 1]) or as BF16; links FP16;
+//               all arithmetic in FP32;
 //   * FP32    -- the iterate x and the reliable-update residual
 //               r = b - D_hat x, with FP32 reconstruct-12 links;
 //   * FP64    -- the outer defect correction: r = b - D x on the full lattice
 //               in FP64, inner solve D e = r, x += e, until |r| / |b| <= tol.
 //
-// Vectors are parity-compact, structure-of-arrays per RHS:
-//   sloppy: [rhs][3][Vh] uint4 (8 x 16-bit reals each) + [rhs][Vh] float norm
+// Sloppy vectors hold right-hand sides in pairs (RHS 2P and 2P+1): each
+// 16-bit pair is the same real of both members, so after conversion every
+// operation of the hopping term and of the BLAS updates is one packed FP32x2
+// instruction (fma.rn.f32x2 / add / mul) working on both members at once, and
+// a link load, its reconstruction and the neighbour indexing serve two RHS.
+// The sloppy links are FP16 reconstruct-12 with every real stored twice, so
+// that one conversion yields the (u, u) operand of the packed products.
+//
+// Layouts (parity-compact, per pair / per RHS):
+//   sloppy: [P][6][Vh] uint4 (24 16-bit pairs) + FP16 norms [P][Vh] float2
 //   FP32:   [rhs][6][Vh] float4
+//   links:  FP16 [2 parity][4 mu][3][Vh] uint4 (rows 0-1, duplicated);
+//           FP32 [2][4][3][Vh] float4 (rows 0-1)
 // A spinor's 24 reals are ordered ((spin * 3 + colour) * 2 + re/im).
 //
-// Kernels walk a device-side list of RHS: work item w = (list[w / nbx],
-// site block w % nbx), grid-stride over a fixed grid, so converged or idle
-// right-hand sides cost nothing.  Every reduction is written as one partial
-// per (RHS, site block) and summed by one warp per RHS in a fixed order, so a
-// right-hand side's arithmetic does not depend on which others share the batch.
+// Kernels walk device-side lists (of RHS or of pairs): work item w =
+// (list[w / nbx], site block w % nbx), grid-stride over a fixed grid, so
+// converged right-hand sides cost nothing.  Every reduction is written as one
+// partial per (RHS, site block) and summed by one warp per RHS in a fixed
+// order: a right-hand side's arithmetic does not depend on its batch mates.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -30,24 +40,36 @@
 
 namespace lqcd {
 
-// ============================================================ accessors
+// ============================================================ conversions
 __device__ __forceinline__ float2 h2f(unsigned w) {
   __half2 h = *reinterpret_cast<__half2 *>(&w);
   return __half22float2(h);
 }
-__device__ __forceinline__ unsigned f2h(float a, float b) {
-  __half2 h = __floats2half2_rn(a, b);
+__device__ __forceinline__ unsigned f2h(float2 v) {
+  __half2 h = __float22half2_rn(v);
   return *reinterpret_cast<unsigned *>(&h);
 }
 __device__ __forceinline__ float2 b2f(unsigned w) {
   // bf16 -> f32 is exact: the bf16 bits are the high half of the f32
   return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
 }
-__device__ __forceinline__ unsigned f2b(float a, float b) {
-  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+__device__ __forceinline__ unsigned f2b(float2 v) {
+  __nv_bfloat162 h = __float22bfloat162_rn(v);
   return *reinterpret_cast<unsigned *>(&h);
 }
 
+// packed FP32x2 arithmetic (one instruction for both members of a pair)
+__device__ __forceinline__ float2 A2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 M2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 F2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 S2(float2 a, float2 b) {  // a - b, rounded once
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 sel2(bool lo, bool hi, float2 a, float2 b) {  // per member: a where set
+  return make_float2(lo ? a.x : b.x, hi ? a.y : b.y);
+}
+
+// ============================================================ FP32 field
 __device__ __forceinline__ void F32F::load(int r, int i, float2 v[12]) const {
   const float4 *p = d + (size_t)r * 6 * vh + i;
 #pragma unroll
@@ -63,84 +85,114 @@ __device__ __forceinline__ void F32F::store(int r, int i, const float2 v[12]) co
   for (int k = 0; k < 6; ++k) p[(size_t)k * vh] = make_float4(v[2 * k].x, v[2 * k].y, v[2 * k + 1].x, v[2 * k + 1].y);
 }
 
-__device__ __forceinline__ void F16F::load(int r, int i, float2 v[12]) const {
-  const uint4 *p = d + (size_t)r * 3 * vh + i;
-  float s = n[(size_t)r * vh + i];
+// ============================================================ pair fields
+// raw (unscaled) pairs and the norm pair (1, 1 for BF16)
+__device__ __forceinline__ void load_raw(const F16P &f, int P, int i, float2 v[24], float2 &nrm) {
+  const uint4 *p = f.d + (size_t)P * 6 * f.vh + i;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    uint4 q = p[(size_t)k * vh];
-    float2 a = h2f(q.x), b = h2f(q.y), c = h2f(q.z), e = h2f(q.w);
-    v[4 * k] = make_float2(a.x * s, a.y * s);
-    v[4 * k + 1] = make_float2(b.x * s, b.y * s);
-    v[4 * k + 2] = make_float2(c.x * s, c.y * s);
-    v[4 * k + 3] = make_float2(e.x * s, e.y * s);
+  for (int k = 0; k < 6; ++k) {
+    uint4 q = p[(size_t)k * f.vh];
+    v[4 * k] = h2f(q.x);
+    v[4 * k + 1] = h2f(q.y);
+    v[4 * k + 2] = h2f(q.z);
+    v[4 * k + 3] = h2f(q.w);
   }
+  nrm = f.n[(size_t)P * f.vh + i];
 }
-__device__ __forceinline__ void F16F::store(int r, int i, const float2 v[12]) const {
-  float m = 0.0f;
+__device__ __forceinline__ void load_raw(const BF16P &f, int P, int i, float2 v[24], float2 &nrm) {
+  const uint4 *p = f.d + (size_t)P * 6 * f.vh + i;
 #pragma unroll
-  for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].x), fabsf(v[k].y)));
-  float inv = m > 0.0f ? 1.0f / m : 0.0f;
-  uint4 *p = d + (size_t)r * 3 * vh + i;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    uint4 q;
-    q.x = f2h(v[4 * k].x * inv, v[4 * k].y * inv);
-    q.y = f2h(v[4 * k + 1].x * inv, v[4 * k + 1].y * inv);
-    q.z = f2h(v[4 * k + 2].x * inv, v[4 * k + 2].y * inv);
-    q.w = f2h(v[4 * k + 3].x * inv, v[4 * k + 3].y * inv);
-    p[(size_t)k * vh] = q;
-  }
-  n[(size_t)r * vh + i] = m;
-}
-
-__device__ __forceinline__ void BF16F::load(int r, int i, float2 v[12]) const {
-  const uint4 *p = d + (size_t)r * 3 * vh + i;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    uint4 q = p[(size_t)k * vh];
+  for (int k = 0; k < 6; ++k) {
+    uint4 q = p[(size_t)k * f.vh];
     v[4 * k] = b2f(q.x);
     v[4 * k + 1] = b2f(q.y);
     v[4 * k + 2] = b2f(q.z);
     v[4 * k + 3] = b2f(q.w);
   }
+  nrm = make_float2(1.f, 1.f);
 }
-__device__ __forceinline__ void BF16F::store(int r, int i, const float2 v[12]) const {
-  uint4 *p = d + (size_t)r * 3 * vh + i;
+__device__ __forceinline__ void load_scaled(const F16P &f, int P, int i, float2 v[24]) {
+  float2 nrm;
+  load_raw(f, P, i, v, nrm);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    uint4 q;
-    q.x = f2b(v[4 * k].x, v[4 * k].y);
-    q.y = f2b(v[4 * k + 1].x, v[4 * k + 1].y);
-    q.z = f2b(v[4 * k + 2].x, v[4 * k + 2].y);
-    q.w = f2b(v[4 * k + 3].x, v[4 * k + 3].y);
-    p[(size_t)k * vh] = q;
-  }
+  for (int k = 0; k < 24; ++k) v[k] = M2(v[k], nrm);
+}
+__device__ __forceinline__ void load_scaled(const BF16P &f, int P, int i, float2 v[24]) {
+  float2 nrm;
+  load_raw(f, P, i, v, nrm);
 }
 
-// reconstruct-12 link: rows 0, 1 stored, row 2 = (row0 x row1)^*
-template <bool L32>
-__device__ __forceinline__ void load_link(const void *links, int p, int mu, int i, int vh, float2 u[3][3]) {
-  size_t base = ((size_t)(p * 4 + mu) * 3) * vh + i;
-  if (L32) {
-    const float4 *U = (const float4 *)links;
-    float4 q0 = U[base], q1 = U[base + vh], q2 = U[base + 2 * (size_t)vh];
-    u[0][0] = make_float2(q0.x, q0.y);
-    u[0][1] = make_float2(q0.z, q0.w);
-    u[0][2] = make_float2(q1.x, q1.y);
-    u[1][0] = make_float2(q1.z, q1.w);
-    u[1][1] = make_float2(q2.x, q2.y);
-    u[1][2] = make_float2(q2.z, q2.w);
-  } else {
-    const uint2 *U = (const uint2 *)links;
-    uint2 w0 = U[base], w1 = U[base + vh], w2 = U[base + 2 * (size_t)vh];
-    u[0][0] = h2f(w0.x);
-    u[0][1] = h2f(w0.y);
-    u[0][2] = h2f(w1.x);
-    u[1][0] = h2f(w1.y);
-    u[1][1] = h2f(w2.x);
-    u[1][2] = h2f(w2.y);
+// FP16: the words to store and the per-member norms
+__device__ __forceinline__ void encode(const F16P &, const float2 v[24], unsigned w[24], float2 &m) {
+  m = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < 24; ++k) {
+    m.x = fmaxf(m.x, fabsf(v[k].x));
+    m.y = fmaxf(m.y, fabsf(v[k].y));
   }
+  float2 inv = make_float2(m.x > 0.f ? 1.f / m.x : 0.f, m.y > 0.f ? 1.f / m.y : 0.f);
+#pragma unroll
+  for (int k = 0; k < 24; ++k) w[k] = f2h(M2(v[k], inv));
+}
+__device__ __forceinline__ void encode(const BF16P &, const float2 v[24], unsigned w[24], float2 &m) {
+  m = make_float2(1.f, 1.f);
+#pragma unroll
+  for (int k = 0; k < 24; ++k) w[k] = f2b(v[k]);
+}
+__device__ __forceinline__ void write_norm(const F16P &f, int P, int i, float2 m) { f.n[(size_t)P * f.vh + i] = m; }
+__device__ __forceinline__ void write_norm(const BF16P &, int, int, float2) {}
+__device__ __forceinline__ float2 read_norm(const F16P &f, int P, int i) { return f.n[(size_t)P * f.vh + i]; }
+__device__ __forceinline__ float2 read_norm(const BF16P &, int, int) { return make_float2(1.f, 1.f); }
+
+template <class SP>
+__device__ __forceinline__ void store_pair(const SP &f, int P, int i, const float2 v[24]) {
+  unsigned w[24];
+  float2 m;
+  encode(f, v, w, m);
+  uint4 *p = f.d + (size_t)P * 6 * f.vh + i;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) p[(size_t)k * f.vh] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+  write_norm(f, P, i, m);
+}
+
+// store only the members flagged in (lo, hi); the other member's bits are kept
+template <class SP>
+__device__ __forceinline__ void store_members(const SP &f, int P, int i, const float2 v[24], bool lo, bool hi) {
+  if (lo && hi) {
+    store_pair(f, P, i, v);
+    return;
+  }
+  if (!lo && !hi) return;
+  unsigned w[24];
+  float2 m;
+  encode(f, v, w, m);
+  const unsigned keep = lo ? 0xffff0000u : 0x0000ffffu;
+  uint4 *p = f.d + (size_t)P * 6 * f.vh + i;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    uint4 o = p[(size_t)k * f.vh];
+    uint4 q;
+    q.x = (o.x & keep) | (w[4 * k] & ~keep);
+    q.y = (o.y & keep) | (w[4 * k + 1] & ~keep);
+    q.z = (o.z & keep) | (w[4 * k + 2] & ~keep);
+    q.w = (o.w & keep) | (w[4 * k + 3] & ~keep);
+    p[(size_t)k * f.vh] = q;
+  }
+  float2 om = read_norm(f, P, i);
+  write_norm(f, P, i, make_float2(lo ? m.x : om.x, hi ? m.y : om.y));
+}
+
+// ======================================================= FP32 hopping term
+// reconstruct-12 FP32 link: rows 0, 1 stored, row 2 = (row0 x row1)^*
+__device__ __forceinline__ void load_link32(const float4 *U, int p, int mu, int i, int vh, float2 u[3][3]) {
+  size_t base = ((size_t)(p * 4 + mu) * 3) * vh + i;
+  float4 q0 = U[base], q1 = U[base + vh], q2 = U[base + 2 * (size_t)vh];
+  u[0][0] = make_float2(q0.x, q0.y);
+  u[0][1] = make_float2(q0.z, q0.w);
+  u[0][2] = make_float2(q1.x, q1.y);
+  u[1][0] = make_float2(q1.z, q1.w);
+  u[1][1] = make_float2(q2.x, q2.y);
+  u[1][2] = make_float2(q2.z, q2.w);
   float2 c0 = csub(cmul(u[0][1], u[1][2]), cmul(u[0][2], u[1][1]));
   float2 c1 = csub(cmul(u[0][2], u[1][0]), cmul(u[0][0], u[1][2]));
   float2 c2 = csub(cmul(u[0][0], u[1][1]), cmul(u[0][1], u[1][0]));
@@ -149,12 +201,10 @@ __device__ __forceinline__ void load_link(const void *links, int p, int mu, int 
   u[2][2] = make_float2(c2.x, -c2.y);
 }
 
-// ============================================================ hopping term
-template <int MU, class IN, bool L32>
-__device__ __forceinline__ void hop_dir_s(const Geom &g, int p_out, const int c[4], int i, const IN &in, int rhs,
-                                          const void *links, float2 acc[4][3]) {
-  float2 v[12], h[2][3], x[2][3], u[3][3];
-  float2 ps[4][3];
+template <int MU>
+__device__ __forceinline__ void hop_dir32(const Geom &g, int p_out, const int c[4], int i, const F32F &in, int rhs,
+                                          const float4 *links, float2 acc[4][3]) {
+  float2 v[12], h[2][3], x[2][3], u[3][3], ps[4][3];
   {  // forward: (1 - gamma_mu) U_mu(x) psi(x + mu)
     int cn[4] = {c[0], c[1], c[2], c[3]};
     cn[MU] = (c[MU] + 1 == g.L[MU]) ? 0 : c[MU] + 1;
@@ -162,7 +212,7 @@ __device__ __forceinline__ void hop_dir_s(const Geom &g, int p_out, const int c[
     in.load(rhs, sn >> 1, v);
 #pragma unroll
     for (int k = 0; k < 12; ++k) ps[k / 3][k % 3] = v[k];
-    load_link<L32>(links, p_out, MU, i, g.Vh, u);
+    load_link32(links, p_out, MU, i, g.Vh, u);
     spin_project<MU, -1>(ps, h);
     su3_mul<false>(u, h, x);
     if (MU == 3 && c[3] == g.L[3] - 1) {
@@ -180,7 +230,7 @@ __device__ __forceinline__ void hop_dir_s(const Geom &g, int p_out, const int c[
     in.load(rhs, sn >> 1, v);
 #pragma unroll
     for (int k = 0; k < 12; ++k) ps[k / 3][k % 3] = v[k];
-    load_link<L32>(links, 1 - p_out, MU, sn >> 1, g.Vh, u);
+    load_link32(links, 1 - p_out, MU, sn >> 1, g.Vh, u);
     spin_project<MU, +1>(ps, h);
     su3_mul<true>(u, h, x);
     if (MU == 3 && c[3] == 0) {
@@ -199,7 +249,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// fixed-order block reduction of a D4 (all ST threads participate)
+// fixed-order block reduction of one or two D4S (all ST threads participate)
 __device__ __forceinline__ void block_reduce_store(D4S v, D4S *dst) {
   __shared__ D4S sh[ST / 32];
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -222,19 +272,46 @@ __device__ __forceinline__ void block_reduce_store(D4S v, D4S *dst) {
   }
   __syncthreads();
 }
+__device__ __forceinline__ void block_reduce_store2(D4S v0, D4S v1, D4S *dst0, D4S *dst1) {
+  __shared__ D4S sh[2][ST / 32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v0.a = warp_sum_d(v0.a);
+  v0.b = warp_sum_d(v0.b);
+  v0.c = warp_sum_d(v0.c);
+  v0.d = warp_sum_d(v0.d);
+  v1.a = warp_sum_d(v1.a);
+  v1.b = warp_sum_d(v1.b);
+  v1.c = warp_sum_d(v1.c);
+  v1.d = warp_sum_d(v1.d);
+  if (lane == 0) {
+    sh[0][w] = v0;
+    sh[1][w] = v1;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    D4S t = sh[threadIdx.x][0];
+#pragma unroll
+    for (int k = 1; k < ST / 32; ++k) {
+      t.a += sh[threadIdx.x][k].a;
+      t.b += sh[threadIdx.x][k].b;
+      t.c += sh[threadIdx.x][k].c;
+      t.d += sh[threadIdx.x][k].d;
+    }
+    *(threadIdx.x ? dst1 : dst0) = t;
+  }
+  __syncthreads();
+}
 
-// out = cA A + cB B + cH (H in) at the sites of parity p_out.
-// EPI_PLAIN: A, B unused.  EPI_AXPY: B unused.  EPI_DOTR: partial <B, out>.
-// EPI_TS: partials <out, A> and |out|^2.  EPI_RES: partial |out|^2.
-template <class IN, class OUT, bool L32, int EPI>
-__global__ void __launch_bounds__(ST) k_hop_s(Geom g, int p_out, const void *links, IN in, OUT out, OUT A, OUT B,
-                                              float cA, float cB, float cH, const int *list, const int *count,
-                                              D4S *part, int nbx, unsigned long long *prof) {
+// FP32 hopping term: out = cA A + cB B + cH (H in) at the sites of parity p_out.
+// EPI_PLAIN: A, B unused.  EPI_AXPY: B unused.  EPI_RES: partial |out|^2.
+template <int EPI>
+__global__ void __launch_bounds__(ST) k_hop32(Geom g, int p_out, const float4 *links, F32F in, F32F out, F32F A,
+                                              F32F B, float cA, float cB, float cH, const int *list,
+                                              const int *count, D4S *part, int nbx) {
   const int n_items = *count * nbx;
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
     const int rhs = list[w / nbx], sb = w % nbx;
     const int i = sb * ST + threadIdx.x;
-    if (prof && threadIdx.x == 0) atomicAdd(prof + EPI, (unsigned long long)min(ST, g.Vh - sb * ST));
     D4S red = {0, 0, 0, 0};
     if (i < g.Vh) {
       int c[4];
@@ -244,15 +321,15 @@ __global__ void __launch_bounds__(ST) k_hop_s(Geom g, int p_out, const void *lin
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) acc[a][b] = make_float2(0.f, 0.f);
-      hop_dir_s<0, IN, L32>(g, p_out, c, i, in, rhs, links, acc);
-      hop_dir_s<1, IN, L32>(g, p_out, c, i, in, rhs, links, acc);
-      hop_dir_s<2, IN, L32>(g, p_out, c, i, in, rhs, links, acc);
-      hop_dir_s<3, IN, L32>(g, p_out, c, i, in, rhs, links, acc);
+      hop_dir32<0>(g, p_out, c, i, in, rhs, links, acc);
+      hop_dir32<1>(g, p_out, c, i, in, rhs, links, acc);
+      hop_dir32<2>(g, p_out, c, i, in, rhs, links, acc);
+      hop_dir32<3>(g, p_out, c, i, in, rhs, links, acc);
       float2 o[12];
 #pragma unroll
       for (int k = 0; k < 12; ++k) o[k] = make_float2(cH * acc[k / 3][k % 3].x, cH * acc[k / 3][k % 3].y);
-      float2 a[12];
       if (EPI != EPI_PLAIN) {
+        float2 a[12];
         A.load(rhs, i, a);
 #pragma unroll
         for (int k = 0; k < 12; ++k) o[k] = make_float2(fmaf(cA, a[k].x, o[k].x), fmaf(cA, a[k].y, o[k].y));
@@ -264,158 +341,416 @@ __global__ void __launch_bounds__(ST) k_hop_s(Geom g, int p_out, const void *lin
         for (int k = 0; k < 12; ++k) o[k] = make_float2(fmaf(cB, b[k].x, o[k].x), fmaf(cB, b[k].y, o[k].y));
       }
       out.store(rhs, i, o);
-      if (EPI == EPI_DOTR) {
-        float2 r[12];
-        B.load(rhs, i, r);
-        float re = 0.f, im = 0.f;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-          re += r[k].x * o[k].x + r[k].y * o[k].y;
-          im += r[k].x * o[k].y - r[k].y * o[k].x;
-        }
-        red.a = re;
-        red.b = im;
-      } else if (EPI == EPI_TS) {
-        float re = 0.f, im = 0.f, nn = 0.f;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-          re += o[k].x * a[k].x + o[k].y * a[k].y;
-          im += o[k].x * a[k].y - o[k].y * a[k].x;
-          nn += o[k].x * o[k].x + o[k].y * o[k].y;
-        }
-        red.a = re;
-        red.b = im;
-        red.d = nn;
-      } else if (EPI == EPI_RES) {
+      if (EPI == EPI_RES) {
         float nn = 0.f;
 #pragma unroll
         for (int k = 0; k < 12; ++k) nn += o[k].x * o[k].x + o[k].y * o[k].y;
         red.c = nn;
       }
     }
-    if (EPI == EPI_DOTR || EPI == EPI_TS || EPI == EPI_RES) block_reduce_store(red, part + (size_t)rhs * nbx + sb);
+    if (EPI == EPI_RES) block_reduce_store(red, part + (size_t)rhs * nbx + sb);
+  }
+}
+
+// ====================================================== pair hopping term
+// FP16 link for both members: rows 0-1 from memory as (u, u) pairs, row 2 =
+// (row0 x row1)^* rebuilt with packed arithmetic.
+__device__ __forceinline__ void load_link_pair(const uint4 *U, int p, int mu, int i, int vh, CP u[3][3]) {
+  size_t base = ((size_t)(p * 4 + mu) * 3) * vh + i;
+  uint4 q0 = U[base], q1 = U[base + vh], q2 = U[base + 2 * (size_t)vh];
+  u[0][0] = CP{h2f(q0.x), h2f(q0.y)};
+  u[0][1] = CP{h2f(q0.z), h2f(q0.w)};
+  u[0][2] = CP{h2f(q1.x), h2f(q1.y)};
+  u[1][0] = CP{h2f(q1.z), h2f(q1.w)};
+  u[1][1] = CP{h2f(q2.x), h2f(q2.y)};
+  u[1][2] = CP{h2f(q2.z), h2f(q2.w)};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const int k = (j + 1) % 3, l = (j + 2) % 3;
+    const CP &a = u[0][k], &b = u[1][l], &c = u[0][l], &d = u[1][k];
+    // (a b - c d)^*:  re = [a.re b.re + c.im d.im] - [a.im b.im + c.re d.re]
+    //                 im = [c.re d.im + c.im d.re] - [a.re b.im + a.im b.re]
+    u[2][j].re = S2(F2(a.re, b.re, M2(c.im, d.im)), F2(a.im, b.im, M2(c.re, d.re)));
+    u[2][j].im = S2(F2(c.re, d.im, M2(c.im, d.re)), F2(a.re, b.im, M2(a.im, b.re)));
+  }
+}
+
+// a + s i b and a + s b on pairs
+template <int S> __device__ __forceinline__ CP cp_addi(const CP &a, const CP &b) {
+  return S > 0 ? CP{S2(a.re, b.im), A2(a.im, b.re)} : CP{A2(a.re, b.im), S2(a.im, b.re)};
+}
+template <int S> __device__ __forceinline__ CP cp_addpm(const CP &a, const CP &b) {
+  return S > 0 ? CP{A2(a.re, b.re), A2(a.im, b.im)} : CP{S2(a.re, b.re), S2(a.im, b.im)};
+}
+
+// Spin projection (1 + SIGMA gamma_mu) of the neighbour spinor, as in
+// spin_project (internal.cuh) but on pairs; then the norm pair scales h.
+template <int MU, int SIGMA>
+__device__ __forceinline__ void project_pair(const float2 v[24], float2 nrm, CP h[2][3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const CP p0{v[(0 * 3 + c) * 2], v[(0 * 3 + c) * 2 + 1]};
+    const CP p1{v[(1 * 3 + c) * 2], v[(1 * 3 + c) * 2 + 1]};
+    const CP p2{v[(2 * 3 + c) * 2], v[(2 * 3 + c) * 2 + 1]};
+    const CP p3{v[(3 * 3 + c) * 2], v[(3 * 3 + c) * 2 + 1]};
+    CP h0, h1;
+    if (MU == 0) {
+      h0 = cp_addi<SIGMA>(p0, p3);
+      h1 = cp_addi<SIGMA>(p1, p2);
+    } else if (MU == 1) {
+      h0 = cp_addpm<-SIGMA>(p0, p3);
+      h1 = cp_addpm<SIGMA>(p1, p2);
+    } else if (MU == 2) {
+      h0 = cp_addi<SIGMA>(p0, p2);
+      h1 = cp_addi<-SIGMA>(p1, p3);
+    } else {
+      h0 = cp_addpm<SIGMA>(p0, p2);
+      h1 = cp_addpm<SIGMA>(p1, p3);
+    }
+    h[0][c] = CP{M2(h0.re, nrm), M2(h0.im, nrm)};
+    h[1][c] = CP{M2(h1.re, nrm), M2(h1.im, nrm)};
+  }
+}
+
+// (U h)_a or (U^+ h)_a for one spin row, packed
+template <bool DAG>
+__device__ __forceinline__ CP su3_row_pair(const CP u[3][3], const CP h[3], int a) {
+  CP r;
+  if (!DAG) {  // sum_b U[a][b] h[b]
+    float2 rr = M2(u[a][0].re, h[0].re), ii = M2(u[a][0].im, h[0].im);
+    rr = F2(u[a][1].re, h[1].re, rr);
+    ii = F2(u[a][1].im, h[1].im, ii);
+    rr = F2(u[a][2].re, h[2].re, rr);
+    ii = F2(u[a][2].im, h[2].im, ii);
+    r.re = S2(rr, ii);
+    float2 im = M2(u[a][0].re, h[0].im);
+    im = F2(u[a][0].im, h[0].re, im);
+    im = F2(u[a][1].re, h[1].im, im);
+    im = F2(u[a][1].im, h[1].re, im);
+    im = F2(u[a][2].re, h[2].im, im);
+    im = F2(u[a][2].im, h[2].re, im);
+    r.im = im;
+  } else {  // sum_b conj(U[b][a]) h[b]
+    float2 re = M2(u[0][a].re, h[0].re);
+    re = F2(u[0][a].im, h[0].im, re);
+    re = F2(u[1][a].re, h[1].re, re);
+    re = F2(u[1][a].im, h[1].im, re);
+    re = F2(u[2][a].re, h[2].re, re);
+    re = F2(u[2][a].im, h[2].im, re);
+    r.re = re;
+    float2 ri = M2(u[0][a].re, h[0].im), ir = M2(u[0][a].im, h[0].re);
+    ri = F2(u[1][a].re, h[1].im, ri);
+    ir = F2(u[1][a].im, h[1].re, ir);
+    ri = F2(u[2][a].re, h[2].im, ri);
+    ir = F2(u[2][a].im, h[2].re, ir);
+    r.im = S2(ri, ir);
+  }
+  return r;
+}
+
+// acc += spin reconstruction of (U h), colour by colour (see spin_accum)
+template <int MU, int SIGMA, bool DAG>
+__device__ __forceinline__ void su3_accum_pair(const CP u[3][3], const CP h[2][3], CP acc[4][3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const CP x0 = su3_row_pair<DAG>(u, h[0], a);
+    const CP x1 = su3_row_pair<DAG>(u, h[1], a);
+    acc[0][a] = cp_addpm<1>(acc[0][a], x0);
+    acc[1][a] = cp_addpm<1>(acc[1][a], x1);
+    if (MU == 0) {
+      acc[2][a] = cp_addi<-SIGMA>(acc[2][a], x1);
+      acc[3][a] = cp_addi<-SIGMA>(acc[3][a], x0);
+    } else if (MU == 1) {
+      acc[2][a] = cp_addpm<SIGMA>(acc[2][a], x1);
+      acc[3][a] = cp_addpm<-SIGMA>(acc[3][a], x0);
+    } else if (MU == 2) {
+      acc[2][a] = cp_addi<-SIGMA>(acc[2][a], x0);
+      acc[3][a] = cp_addi<SIGMA>(acc[3][a], x1);
+    } else {
+      acc[2][a] = cp_addpm<SIGMA>(acc[2][a], x0);
+      acc[3][a] = cp_addpm<SIGMA>(acc[3][a], x1);
+    }
+  }
+}
+
+template <int MU, class SP>
+__device__ __forceinline__ void hop_dir_pair(const Geom &g, int p_out, const int c[4], int i, const SP &in, int P,
+                                             const uint4 *links, CP acc[4][3]) {
+  float2 v[24], nrm;
+  CP h[2][3], u[3][3];
+  {  // forward: (1 - gamma_mu) U_mu(x) psi(x + mu); the t-boundary sign rides on the norm
+    int cn[4] = {c[0], c[1], c[2], c[3]};
+    cn[MU] = (c[MU] + 1 == g.L[MU]) ? 0 : c[MU] + 1;
+    const int sn = site_of(g, cn);
+    load_raw(in, P, sn >> 1, v, nrm);
+    if (MU == 3 && c[3] == g.L[3] - 1) nrm = make_float2(-nrm.x, -nrm.y);
+    project_pair<MU, -1>(v, nrm, h);
+    load_link_pair(links, p_out, MU, i, g.Vh, u);
+    su3_accum_pair<MU, -1, false>(u, h, acc);
+  }
+  {  // backward: (1 + gamma_mu) U_mu(x - mu)^+ psi(x - mu)
+    int cn[4] = {c[0], c[1], c[2], c[3]};
+    cn[MU] = (c[MU] == 0) ? g.L[MU] - 1 : c[MU] - 1;
+    const int sn = site_of(g, cn);
+    load_raw(in, P, sn >> 1, v, nrm);
+    if (MU == 3 && c[3] == 0) nrm = make_float2(-nrm.x, -nrm.y);
+    project_pair<MU, +1>(v, nrm, h);
+    load_link_pair(links, 1 - p_out, MU, sn >> 1, g.Vh, u);
+    su3_accum_pair<MU, +1, true>(u, h, acc);
+  }
+}
+
+// Sloppy hopping term on RHS pairs: out = cA A + cH (H in) at parity p_out.
+// EPI_PLAIN: out = cH H in.  EPI_DOTR: partial <B, out> per member.
+// EPI_TS: partials <out, A> and |out|^2 per member.
+template <class SP, int EPI>
+__global__ void __launch_bounds__(ST) k_hop_pair(Geom g, int p_out, const uint4 *links, SP in, SP out, SP A, SP B,
+                                                 float cA, float cH, const int *plist, const int *pcount, D4S *part,
+                                                 int nbx, int nrhs, unsigned long long *prof) {
+  const int n_items = *pcount * nbx;
+  const float2 cA2 = make_float2(cA, cA), cH2 = make_float2(cH, cH);
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int P = plist[w / nbx], sb = w % nbx;
+    const int i = sb * ST + threadIdx.x;
+    if (prof && threadIdx.x == 0)
+      atomicAdd(prof + EPI, (unsigned long long)min(ST, g.Vh - sb * ST) * (2 * P + 1 < nrhs ? 2 : 1));
+    D4S r0 = {0, 0, 0, 0}, r1 = {0, 0, 0, 0};
+    if (i < g.Vh) {
+      int c[4];
+      coords_of(g, p_out, i, c);
+      CP acc[4][3];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) acc[a][b] = CP{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      hop_dir_pair<0>(g, p_out, c, i, in, P, links, acc);
+      hop_dir_pair<1>(g, p_out, c, i, in, P, links, acc);
+      hop_dir_pair<2>(g, p_out, c, i, in, P, links, acc);
+      hop_dir_pair<3>(g, p_out, c, i, in, P, links, acc);
+      float2 o[24];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        o[2 * k] = M2(acc[k / 3][k % 3].re, cH2);
+        o[2 * k + 1] = M2(acc[k / 3][k % 3].im, cH2);
+      }
+      float2 a[24];
+      if (EPI != EPI_PLAIN) {
+        load_scaled(A, P, i, a);
+#pragma unroll
+        for (int k = 0; k < 24; ++k) o[k] = F2(cA2, a[k], o[k]);
+      }
+      store_pair(out, P, i, o);
+      if (EPI == EPI_DOTR) {  // <B, out> = sum conj(B) out
+        float2 rb[24];
+        load_scaled(B, P, i, rb);
+        float2 re = make_float2(0.f, 0.f), ip = re, im = re;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          re = F2(rb[2 * k], o[2 * k], re);
+          re = F2(rb[2 * k + 1], o[2 * k + 1], re);
+          ip = F2(rb[2 * k], o[2 * k + 1], ip);
+          im = F2(rb[2 * k + 1], o[2 * k], im);
+        }
+        const float2 imag = S2(ip, im);
+        r0 = D4S{re.x, imag.x, 0, 0};
+        r1 = D4S{re.y, imag.y, 0, 0};
+      } else if (EPI == EPI_TS) {  // <out, A> and |out|^2
+        float2 re = make_float2(0.f, 0.f), ip = re, im = re, nn = re;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          re = F2(o[2 * k], a[2 * k], re);
+          re = F2(o[2 * k + 1], a[2 * k + 1], re);
+          ip = F2(o[2 * k], a[2 * k + 1], ip);
+          im = F2(o[2 * k + 1], a[2 * k], im);
+          nn = F2(o[2 * k], o[2 * k], nn);
+          nn = F2(o[2 * k + 1], o[2 * k + 1], nn);
+        }
+        const float2 imag = S2(ip, im);
+        r0 = D4S{re.x, imag.x, 0, nn.x};
+        r1 = D4S{re.y, imag.y, 0, nn.y};
+      }
+    }
+    if (EPI == EPI_DOTR || EPI == EPI_TS)
+      block_reduce_store2(r0, r1, part + (size_t)(2 * P) * nbx + sb, part + (size_t)(2 * P + 1) * nbx + sb);
   }
 }
 
 // ============================================================ BLAS kernels
-__device__ __forceinline__ float2 f2(double2 a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ CP scal_pair(double2 a, double2 b) {
+  return CP{make_float2((float)a.x, (float)b.x), make_float2((float)a.y, (float)b.y)};
+}
+// (s * z) for complex pairs
+__device__ __forceinline__ CP cp_mul(const CP &s, const CP &z) {
+  return CP{S2(M2(s.re, z.re), M2(s.im, z.im)), F2(s.re, z.im, M2(s.im, z.re))};
+}
+// a + s * z and a - s * z
+__device__ __forceinline__ CP cp_fma(const CP &s, const CP &z, const CP &a) {
+  return CP{S2(F2(s.re, z.re, a.re), M2(s.im, z.im)), F2(s.re, z.im, F2(s.im, z.re, a.im))};
+}
+__device__ __forceinline__ CP cp_fms(const CP &s, const CP &z, const CP &a) {  // a - s z
+  return CP{F2(s.im, z.im, S2(a.re, M2(s.re, z.re))), S2(a.im, F2(s.re, z.im, M2(s.im, z.re)))};
+}
 
-// p = r + beta (p - omega v); on restart rhat = r, p = r.
-template <class S>
-__global__ void __launch_bounds__(ST) k_blas_p(int vh, const SState *sc, S r, S rhat, S p, S v, const int *list,
-                                               const int *count, int nbx) {
-  const int n_items = *count * nbx;
+// p = r + beta (p - omega v); members flagged for restart take rhat = r, p = r.
+template <class SP>
+__global__ void __launch_bounds__(ST) k_pair_p(int vh, const SState *sc, SP r, SP rhat, SP p, SP v,
+                                               const int *plist, const int *pcount, int nbx) {
+  const int n_items = *pcount * nbx;
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const int rhs = list[w / nbx];
+    const int P = plist[w / nbx];
     const int i = (w % nbx) * ST + threadIdx.x;
     if (i >= vh) continue;
-    float2 rv[12];
-    r.load(rhs, i, rv);
-    if (sc[rhs].restart) {
-      rhat.store(rhs, i, rv);
-      p.store(rhs, i, rv);
-    } else {
-      float2 be = f2(sc[rhs].beta), om = f2(sc[rhs].omega);
-      float2 pv[12], vv[12];
-      p.load(rhs, i, pv);
-      v.load(rhs, i, vv);
+    const bool re0 = sc[2 * P].restart, re1 = sc[2 * P + 1].restart;
+    float2 rv[24], pv[24];
+    load_scaled(r, P, i, rv);
+    if (!(re0 && re1)) {
+      float2 vv[24];
+      load_scaled(p, P, i, pv);
+      load_scaled(v, P, i, vv);
+      const CP be = scal_pair(sc[2 * P].beta, sc[2 * P + 1].beta);
+      const CP om = scal_pair(sc[2 * P].omega, sc[2 * P + 1].omega);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) pv[k] = cadd(rv[k], cmul(be, csub(pv[k], cmul(om, vv[k]))));
-      p.store(rhs, i, pv);
+      for (int k = 0; k < 12; ++k) {
+        CP t = cp_fms(om, CP{vv[2 * k], vv[2 * k + 1]}, CP{pv[2 * k], pv[2 * k + 1]});
+        CP n = cp_fma(be, t, CP{rv[2 * k], rv[2 * k + 1]});
+        pv[2 * k] = n.re;
+        pv[2 * k + 1] = n.im;
+      }
     }
+    if (re0 || re1) {
+#pragma unroll
+      for (int k = 0; k < 24; ++k) pv[k] = sel2(re0, re1, rv[k], pv[k]);
+      store_members(rhat, P, i, rv, re0, re1);
+    }
+    store_pair(p, P, i, pv);
   }
 }
 
 // s = r - alpha v
-template <class S>
-__global__ void __launch_bounds__(ST) k_blas_s(int vh, const SState *sc, S r, S v, S s, const int *list,
-                                               const int *count, int nbx) {
-  const int n_items = *count * nbx;
+template <class SP>
+__global__ void __launch_bounds__(ST) k_pair_s(int vh, const SState *sc, SP r, SP v, SP s, const int *plist,
+                                               const int *pcount, int nbx) {
+  const int n_items = *pcount * nbx;
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const int rhs = list[w / nbx];
+    const int P = plist[w / nbx];
     const int i = (w % nbx) * ST + threadIdx.x;
     if (i >= vh) continue;
-    float2 al = f2(sc[rhs].alpha);
-    float2 rv[12], vv[12];
-    r.load(rhs, i, rv);
-    v.load(rhs, i, vv);
+    const CP al = scal_pair(sc[2 * P].alpha, sc[2 * P + 1].alpha);
+    float2 rv[24], vv[24];
+    load_scaled(r, P, i, rv);
+    load_scaled(v, P, i, vv);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) rv[k] = csub(rv[k], cmul(al, vv[k]));
-    s.store(rhs, i, rv);
-  }
-}
-
-// x += alpha p + omega s (FP32 x); r = s - omega t; partials <rhat, r>, |r|^2
-template <class S>
-__global__ void __launch_bounds__(ST) k_blas_xr(int vh, const SState *sc, F32F x, S p, S s, S t, S r, S rhat,
-                                                const int *list, const int *count, D4S *part, int nbx) {
-  const int n_items = *count * nbx;
-  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const int rhs = list[w / nbx], sb = w % nbx;
-    const int i = sb * ST + threadIdx.x;
-    D4S red = {0, 0, 0, 0};
-    if (i < vh) {
-      float2 al = f2(sc[rhs].alpha), om = f2(sc[rhs].omega);
-      float2 xv[12], pv[12], sv[12], tv[12];
-      x.load(rhs, i, xv);
-      p.load(rhs, i, pv);
-      s.load(rhs, i, sv);
-      t.load(rhs, i, tv);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        xv[k] = cadd(xv[k], cadd(cmul(al, pv[k]), cmul(om, sv[k])));
-        sv[k] = csub(sv[k], cmul(om, tv[k]));
-      }
-      x.store(rhs, i, xv);
-      r.store(rhs, i, sv);
-      rhat.load(rhs, i, pv);
-      float re = 0.f, im = 0.f, nn = 0.f;
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        re += pv[k].x * sv[k].x + pv[k].y * sv[k].y;
-        im += pv[k].x * sv[k].y - pv[k].y * sv[k].x;
-        nn += sv[k].x * sv[k].x + sv[k].y * sv[k].y;
-      }
-      red.a = re;
-      red.b = im;
-      red.c = nn;
+    for (int k = 0; k < 12; ++k) {
+      CP n = cp_fms(al, CP{vv[2 * k], vv[2 * k + 1]}, CP{rv[2 * k], rv[2 * k + 1]});
+      rv[2 * k] = n.re;
+      rv[2 * k + 1] = n.im;
     }
-    block_reduce_store(red, part + (size_t)rhs * nbx + sb);
+    store_pair(s, P, i, rv);
   }
 }
 
-// r (sloppy) = src (FP32); optionally x = 0; partials <rhat, r>, |r|^2 (rhat may alias r)
-template <class S>
-__global__ void __launch_bounds__(ST) k_blas_copy(int vh, F32F src, S r, S rhat, bool use_rhat, F32F x, bool zero_x,
-                                                  const int *list, const int *count, D4S *part, int nbx) {
-  const int n_items = *count * nbx;
+// x += alpha p + omega s (FP32 x, active members only); r = s - omega t;
+// partials <rhat, r> and |r|^2 per member
+template <class SP>
+__global__ void __launch_bounds__(ST) k_pair_xr(int vh, const SState *sc, const int *flags, F32F x, SP p, SP s, SP t,
+                                                SP r, SP rhat, const int *plist, const int *pcount, D4S *part,
+                                                int nbx) {
+  const int n_items = *pcount * nbx;
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const int rhs = list[w / nbx], sb = w % nbx;
+    const int P = plist[w / nbx], sb = w % nbx;
     const int i = sb * ST + threadIdx.x;
-    D4S red = {0, 0, 0, 0};
+    D4S r0 = {0, 0, 0, 0}, r1 = {0, 0, 0, 0};
     if (i < vh) {
-      float2 v[12], h[12];
-      src.load(rhs, i, v);
-      r.store(rhs, i, v);
+      const bool a0 = flags[2 * P] & FLAG_ACTIVE, a1 = flags[2 * P + 1] & FLAG_ACTIVE;
+      const CP al = scal_pair(sc[2 * P].alpha, sc[2 * P + 1].alpha);
+      const CP om = scal_pair(sc[2 * P].omega, sc[2 * P + 1].omega);
+      float2 pv[24], sv[24], tv[24];
+      load_scaled(p, P, i, pv);
+      load_scaled(s, P, i, sv);
+      load_scaled(t, P, i, tv);
+      float2 x0[12], x1[12];
+      if (a0) x.load(2 * P, i, x0);
+      if (a1) x.load(2 * P + 1, i, x1);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        CP xk{make_float2(a0 ? x0[k].x : 0.f, a1 ? x1[k].x : 0.f), make_float2(a0 ? x0[k].y : 0.f, a1 ? x1[k].y : 0.f)};
+        xk = cp_fma(al, CP{pv[2 * k], pv[2 * k + 1]}, xk);
+        xk = cp_fma(om, CP{sv[2 * k], sv[2 * k + 1]}, xk);
+        x0[k] = make_float2(xk.re.x, xk.im.x);
+        x1[k] = make_float2(xk.re.y, xk.im.y);
+        CP rn = cp_fms(om, CP{tv[2 * k], tv[2 * k + 1]}, CP{sv[2 * k], sv[2 * k + 1]});
+        sv[2 * k] = rn.re;
+        sv[2 * k + 1] = rn.im;
+      }
+      if (a0) x.store(2 * P, i, x0);
+      if (a1) x.store(2 * P + 1, i, x1);
+      store_pair(r, P, i, sv);
+      load_scaled(rhat, P, i, pv);
+      float2 re = make_float2(0.f, 0.f), ip = re, im = re, nn = re;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        re = F2(pv[2 * k], sv[2 * k], re);
+        re = F2(pv[2 * k + 1], sv[2 * k + 1], re);
+        ip = F2(pv[2 * k], sv[2 * k + 1], ip);
+        im = F2(pv[2 * k + 1], sv[2 * k], im);
+        nn = F2(sv[2 * k], sv[2 * k], nn);
+        nn = F2(sv[2 * k + 1], sv[2 * k + 1], nn);
+      }
+      const float2 imag = S2(ip, im);
+      r0 = D4S{re.x, imag.x, nn.x, 0};
+      r1 = D4S{re.y, imag.y, nn.y, 0};
+    }
+    block_reduce_store2(r0, r1, part + (size_t)(2 * P) * nbx + sb, part + (size_t)(2 * P + 1) * nbx + sb);
+  }
+}
+
+// members flagged FLAG_RU: r = src (FP32), optionally x = 0; partials per
+// member of <rhat, r> (or <r, r>) and |r|^2
+template <class SP>
+__global__ void __launch_bounds__(ST) k_pair_copy(int vh, const int *flags, F32F src, SP r, SP rhat, bool use_rhat,
+                                                  F32F x, bool zero_x, const int *plist, const int *pcount, D4S *part,
+                                                  int nbx) {
+  const int n_items = *pcount * nbx;
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int P = plist[w / nbx], sb = w % nbx;
+    const int i = sb * ST + threadIdx.x;
+    D4S r0 = {0, 0, 0, 0}, r1 = {0, 0, 0, 0};
+    if (i < vh) {
+      const bool w0 = flags[2 * P] & FLAG_RU, w1 = flags[2 * P + 1] & FLAG_RU;
+      float2 s0[12], s1[12], v[24];
+      if (w0) src.load(2 * P, i, s0);
+      if (w1) src.load(2 * P + 1, i, s1);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        v[2 * k] = make_float2(w0 ? s0[k].x : 0.f, w1 ? s1[k].x : 0.f);
+        v[2 * k + 1] = make_float2(w0 ? s0[k].y : 0.f, w1 ? s1[k].y : 0.f);
+      }
+      store_members(r, P, i, v, w0, w1);
       if (zero_x) {
+        float2 z[12];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) h[k] = make_float2(0.f, 0.f);
-        x.store(rhs, i, h);
+        for (int k = 0; k < 12; ++k) z[k] = make_float2(0.f, 0.f);
+        if (w0) x.store(2 * P, i, z);
+        if (w1) x.store(2 * P + 1, i, z);
       }
-      if (use_rhat) rhat.load(rhs, i, h);
-      float re = 0.f, im = 0.f, nn = 0.f;
+      float2 q[24];
+      if (use_rhat) load_scaled(rhat, P, i, q);
+      float2 re = make_float2(0.f, 0.f), ip = re, im = re, nn = re;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        float2 q = use_rhat ? h[k] : v[k];
-        re += q.x * v[k].x + q.y * v[k].y;
-        im += q.x * v[k].y - q.y * v[k].x;
-        nn += v[k].x * v[k].x + v[k].y * v[k].y;
+        const float2 qr = use_rhat ? q[2 * k] : v[2 * k], qi = use_rhat ? q[2 * k + 1] : v[2 * k + 1];
+        re = F2(qr, v[2 * k], re);
+        re = F2(qi, v[2 * k + 1], re);
+        ip = F2(qr, v[2 * k + 1], ip);
+        im = F2(qi, v[2 * k], im);
+        nn = F2(v[2 * k], v[2 * k], nn);
+        nn = F2(v[2 * k + 1], v[2 * k + 1], nn);
       }
-      red.a = re;
-      red.b = im;
-      red.c = nn;
+      const float2 imag = S2(ip, im);
+      r0 = D4S{re.x, imag.x, nn.x, 0};
+      r1 = D4S{re.y, imag.y, nn.y, 0};
     }
-    block_reduce_store(red, part + (size_t)rhs * nbx + sb);
+    block_reduce_store2(r0, r1, part + (size_t)(2 * P) * nbx + sb, part + (size_t)(2 * P + 1) * nbx + sb);
   }
 }
 
@@ -461,7 +796,7 @@ __global__ void __launch_bounds__(ST) k_accum64(Geom g, int p, F32F src, double2
 // ============================================================ finalisers
 __device__ __forceinline__ D4S warp_total_s(const D4S *part, int nb) {
   D4S acc = {0, 0, 0, 0};
-  for (int k = threadIdx.x; k < nb; k += 32) {
+  for (int k = threadIdx.x & 31; k < nb; k += 32) {
     D4S v = part[k];
     acc.a += v.a;
     acc.b += v.b;
@@ -484,12 +819,15 @@ __device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
 }
 
 // after the inner right-hand side is loaded into r (partials: |r|^2 in .c)
-__global__ void k_sfin_init(SState *sc, int *flags, const int *list, const int *count, const D4S *part, int nb) {
+// target2 (set by the host from the outer tolerance) is floored at floor2 * |b_inner|^2
+__global__ void k_sfin_init(SState *sc, int *flags, const int *list, const int *count, const D4S *part, int nb,
+                            double floor2) {
   if (blockIdx.x >= *count) return;
   int rhs = list[blockIdx.x];
   D4S t = warp_total_s(part + (size_t)rhs * nb, nb);
   if (threadIdx.x) return;
   SState &s = sc[rhs];
+  s.target2 = fmax(s.target2, floor2 * t.c);
   s.rr = t.c;
   s.rmax = t.c;
   s.rr_ru = t.c;
@@ -508,33 +846,38 @@ __global__ void k_sfin_init(SState *sc, int *flags, const int *list, const int *
   flags[rhs] = f;
 }
 
-__global__ void k_sfin_alpha(SState *sc, const int *list, const int *count, const D4S *part, int nb) {
-  if (blockIdx.x >= *count) return;
-  int rhs = list[blockIdx.x];
+// One warp per member of a listed pair; members without FLAG_ACTIVE are skipped.
+#define PAIR_MEMBER(n)                                            \
+  if (blockIdx.x >= *pcount) return;                              \
+  const int rhs = 2 * plist[blockIdx.x] + (threadIdx.x >> 5);     \
+  if (rhs >= (n) || !(flags[rhs] & FLAG_ACTIVE)) return;
+
+__global__ void k_sfin_alpha(SState *sc, const int *flags, const int *plist, const int *pcount, const D4S *part,
+                             int nb, int n) {
+  PAIR_MEMBER(n)
   D4S t = warp_total_s(part + (size_t)rhs * nb, nb);
-  if (threadIdx.x) return;
+  if (threadIdx.x & 31) return;
   SState &s = sc[rhs];
   double2 rv = make_double2(t.a, t.b);
   s.alpha = (rv.x == 0.0 && rv.y == 0.0) ? make_double2(0.0, 0.0) : cdiv_d(s.rho, rv);
   s.restart = 0;
 }
 
-__global__ void k_sfin_omega(SState *sc, const int *list, const int *count, const D4S *part, int nb) {
-  if (blockIdx.x >= *count) return;
-  int rhs = list[blockIdx.x];
+__global__ void k_sfin_omega(SState *sc, const int *flags, const int *plist, const int *pcount, const D4S *part,
+                             int nb, int n) {
+  PAIR_MEMBER(n)
   D4S t = warp_total_s(part + (size_t)rhs * nb, nb);
-  if (threadIdx.x) return;
+  if (threadIdx.x & 31) return;
   SState &s = sc[rhs];
   s.omega = (t.d == 0.0) ? make_double2(0.0, 0.0) : make_double2(t.a / t.d, t.b / t.d);
 }
 
 // convergence / reliable-update decision after the x, r update
-__global__ void k_sfin_conv(SState *sc, int *flags, const int *list, const int *count, const D4S *part, int nb,
-                            double delta2, int max_iter) {
-  if (blockIdx.x >= *count) return;
-  int rhs = list[blockIdx.x];
+__global__ void k_sfin_conv(SState *sc, int *flags, const int *plist, const int *pcount, const D4S *part, int nb,
+                            int n, double delta2, int max_iter) {
+  PAIR_MEMBER(n)
   D4S t = warp_total_s(part + (size_t)rhs * nb, nb);
-  if (threadIdx.x) return;
+  if (threadIdx.x & 31) return;
   SState &s = sc[rhs];
   double2 rho_new = make_double2(t.a, t.b);
   s.rr = t.c;
@@ -601,35 +944,45 @@ __global__ void k_sfin_ru2(SState *sc, int *flags, const int *list, const int *c
   flags[rhs] = FLAG_ACTIVE;
 }
 
-// deterministic compaction of flags into the active and reliable-update lists
-__global__ void k_build_lists(int n, const int *flags, int *act_list, int *act_count, int *ru_list, int *ru_count) {
-  __shared__ int sa[1024], sr[1024];
+// Deterministic compaction of the per-RHS flags into: active pairs (either
+// member active), RHS needing a reliable update, and pairs containing one.
+__global__ void k_build_lists(int n, const int *flags, int *act_pairs, int *ru_list, int *ru_pairs, int *counts) {
+  __shared__ int sa[1024], sr[1024], sp[1024];
+  const int np = (n + 1) / 2;
   int tid = threadIdx.x, nt = blockDim.x;
-  int per = (n + nt - 1) / nt;
-  int b0 = tid * per, b1 = min(n, b0 + per);
-  int ca = 0, cr = 0;
-  for (int k = b0; k < b1; ++k) {
-    ca += (flags[k] & FLAG_ACTIVE) ? 1 : 0;
-    cr += (flags[k] & FLAG_RU) ? 1 : 0;
+  int per = (np + nt - 1) / nt;
+  int b0 = tid * per, b1 = min(np, b0 + per);
+  int ca = 0, cr = 0, cp = 0;
+  for (int P = b0; P < b1; ++P) {
+    int f0 = flags[2 * P], f1 = (2 * P + 1 < n) ? flags[2 * P + 1] : 0;
+    ca += ((f0 | f1) & FLAG_ACTIVE) ? 1 : 0;
+    cp += ((f0 | f1) & FLAG_RU) ? 1 : 0;
+    cr += ((f0 & FLAG_RU) ? 1 : 0) + ((f1 & FLAG_RU) ? 1 : 0);
   }
   sa[tid] = ca;
   sr[tid] = cr;
+  sp[tid] = cp;
   __syncthreads();
-  for (int off = 1; off < nt; off <<= 1) {  // inclusive scan
-    int va = tid >= off ? sa[tid - off] : 0, vr = tid >= off ? sr[tid - off] : 0;
+  for (int off = 1; off < nt; off <<= 1) {  // inclusive scans
+    int va = tid >= off ? sa[tid - off] : 0, vr = tid >= off ? sr[tid - off] : 0, vp = tid >= off ? sp[tid - off] : 0;
     __syncthreads();
     sa[tid] += va;
     sr[tid] += vr;
+    sp[tid] += vp;
     __syncthreads();
   }
-  int oa = sa[tid] - ca, orr = sr[tid] - cr;
-  for (int k = b0; k < b1; ++k) {
-    if (flags[k] & FLAG_ACTIVE) act_list[oa++] = k;
-    if (flags[k] & FLAG_RU) ru_list[orr++] = k;
+  int oa = sa[tid] - ca, orr = sr[tid] - cr, op = sp[tid] - cp;
+  for (int P = b0; P < b1; ++P) {
+    int f0 = flags[2 * P], f1 = (2 * P + 1 < n) ? flags[2 * P + 1] : 0;
+    if ((f0 | f1) & FLAG_ACTIVE) act_pairs[oa++] = P;
+    if ((f0 | f1) & FLAG_RU) ru_pairs[op++] = P;
+    if (f0 & FLAG_RU) ru_list[orr++] = 2 * P;
+    if (f1 & FLAG_RU) ru_list[orr++] = 2 * P + 1;
   }
   if (tid == nt - 1) {
-    *act_count = sa[tid];
-    *ru_count = sr[tid];
+    counts[0] = sa[tid];
+    counts[1] = sr[tid];
+    counts[3] = sp[tid];
   }
 }
 
@@ -639,13 +992,12 @@ __global__ void k_build_lists(int n, const int *flags, int *act_list, int *act_c
 namespace lqcd {
 
 struct SloppyState {
-  int cap = 0;
-  uint4 *sd = nullptr;  // 7 sloppy fields
-  float *sn = nullptr;  // their norms
-  float4 *f32 = nullptr;  // 5 FP32 fields
+  int cap = 0;             // RHS capacity (even)
+  uint4 *sd = nullptr;     // 7 sloppy pair fields
+  float2 *sn = nullptr;    // their FP16 norms
+  float4 *f32 = nullptr;   // 5 FP32 fields
   double2 *r64 = nullptr;  // canonical FP64 residual
   char *small = nullptr;
-  size_t small_bytes = 0;
   int *h_counts = nullptr;  // pinned
 };
 
@@ -677,7 +1029,7 @@ static int num_sms(int device) {
 // per-RHS state, flags, lists, scales and reduction partials in one buffer
 struct SmallBufs {
   SState *sc;
-  int *flags, *act_list, *ru_list, *cyc_list, *counts;
+  int *flags, *act_pairs, *ru_list, *ru_pairs, *cyc_list, *cyc_pairs, *counts;
   double *scale, *unscale;
   D4S *part;
   size_t bytes;
@@ -688,10 +1040,12 @@ static SmallBufs small_layout(void *base, int cap, int nbx) {
   SmallBufs b;
   b.sc = cv.take<SState>(cap);
   b.flags = cv.take<int>(cap);
-  b.act_list = cv.take<int>(cap);
+  b.act_pairs = cv.take<int>(cap / 2);
   b.ru_list = cv.take<int>(cap);
+  b.ru_pairs = cv.take<int>(cap / 2);
   b.cyc_list = cv.take<int>(cap);
-  b.counts = cv.take<int>(16);
+  b.cyc_pairs = cv.take<int>(cap / 2);
+  b.counts = cv.take<int>(16);  // [0] active pairs, [1] RU RHS, [2] cycle RHS, [3] RU pairs, [4] cycle pairs
   b.scale = cv.take<double>(cap);
   b.unscale = cv.take<double>(cap);
   b.part = cv.take<D4S>((size_t)cap * nbx);
@@ -702,8 +1056,8 @@ static SmallBufs small_layout(void *base, int cap, int nbx) {
 static int sloppy_alloc(lqcd_ctx *ctx, int nrhs) {
   if (!ctx->sloppy) ctx->sloppy = new SloppyState();
   SloppyState *s = ctx->sloppy;
-  if (s->cap >= nrhs) return LQCD_OK;
-  cudaStreamSynchronize(0);
+  const int cap = (nrhs + 1) & ~1;
+  if (s->cap >= cap) return LQCD_OK;
   cudaDeviceSynchronize();
   cudaFree(s->sd);
   cudaFree(s->sn);
@@ -713,43 +1067,32 @@ static int sloppy_alloc(lqcd_ctx *ctx, int nrhs) {
   s->sd = nullptr; s->sn = nullptr; s->f32 = nullptr; s->r64 = nullptr; s->small = nullptr;
   s->cap = 0;
   const Geom &g = ctx->geom;
-  size_t vh = g.Vh;
-  int nbx = (g.Vh + ST - 1) / ST;
-  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->sd, 7 * (size_t)nrhs * 3 * vh * sizeof(uint4)));
-  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->sn, 7 * (size_t)nrhs * vh * sizeof(float)));
-  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->f32, 5 * (size_t)nrhs * 6 * vh * sizeof(float4)));
-  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->r64, (size_t)nrhs * g.V * 12 * sizeof(double2)));
-  s->small_bytes = small_layout(nullptr, nrhs, nbx).size();
-  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->small, s->small_bytes));
+  const size_t vh = g.Vh, pairs = cap / 2;
+  const int nbx = (g.Vh + ST - 1) / ST;
+  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->sd, 7 * pairs * 6 * vh * sizeof(uint4)));
+  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->sn, 7 * pairs * vh * sizeof(float2)));
+  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->f32, 5 * (size_t)cap * 6 * vh * sizeof(float4)));
+  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->r64, (size_t)cap * g.V * 12 * sizeof(double2)));
+  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->small, small_layout(nullptr, cap, nbx).size()));
   if (!s->h_counts) LQCD_CUDA_TRY(ctx, cudaMallocHost(&s->h_counts, 16 * sizeof(int)));
-  s->cap = nrhs;
+  s->cap = cap;
   return LQCD_OK;
 }
 
 int fp64_residual_into(lqcd_ctx *ctx, const double2 *b, const double2 *x, double2 *res, int nrhs, double *rr,
                        double *bb, cudaStream_t st);
 
-template <class S>
-struct SlopFields {
-  S r, rhat, p, v, s, t, tmp;
-};
-
-template <class S> S make_sfield(SloppyState *st, int f, int cap, int vh);
-template <> F16F make_sfield<F16F>(SloppyState *st, int f, int cap, int vh) {
-  F16F x;
-  x.d = st->sd + (size_t)f * cap * 3 * vh;
-  x.n = st->sn + (size_t)f * cap * vh;
-  x.vh = vh;
-  return x;
+template <class SP> SP pair_field(SloppyState *st, int f, int vh);
+template <> F16P pair_field<F16P>(SloppyState *st, int f, int vh) {
+  size_t pairs = st->cap / 2;
+  return F16P{st->sd + (size_t)f * pairs * 6 * vh, st->sn + (size_t)f * pairs * vh, vh};
 }
-template <> BF16F make_sfield<BF16F>(SloppyState *st, int f, int cap, int vh) {
-  BF16F x;
-  x.d = st->sd + (size_t)f * cap * 3 * vh;
-  x.vh = vh;
-  return x;
+template <> BF16P pair_field<BF16P>(SloppyState *st, int f, int vh) {
+  size_t pairs = st->cap / 2;
+  return BF16P{st->sd + (size_t)f * pairs * 6 * vh, vh};
 }
 
-template <class S>
+template <class SP>
 static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const lqcd_solver_params &p,
                        lqcd_solve_stats *stats, cudaStream_t st, double t0) {
   int rc = sloppy_alloc(ctx, nrhs);
@@ -761,8 +1104,11 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
   const float kappa = (float)ctx->kappa;
   const float k2 = (float)(ctx->kappa * ctx->kappa);
   const int G = num_sms(ctx->device) * 8;
+  const int npairs = (nrhs + 1) / 2;
   const double delta = p.delta > 0 ? p.delta : 0.1;
   const double floor2 = 4e-12;  // (2e-6)^2: inner FP32 target floor, relative to |b_inner|^2
+  const uint4 *L16 = ctx->U16;
+  const float4 *L32 = ctx->U32;
 
   // measurement of the dominant kernel (sloppy hopping term), when enabled
   unsigned long long *prof = ctx->prof_on ? ctx->d_prof : nullptr;
@@ -783,41 +1129,35 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
     ctx->prof_hop_launches++;
   };
 
-  SlopFields<S> F;
-  F.r = make_sfield<S>(ss, 0, cap, vh);
-  F.rhat = make_sfield<S>(ss, 1, cap, vh);
-  F.p = make_sfield<S>(ss, 2, cap, vh);
-  F.v = make_sfield<S>(ss, 3, cap, vh);
-  F.s = make_sfield<S>(ss, 4, cap, vh);
-  F.t = make_sfield<S>(ss, 5, cap, vh);
-  F.tmp = make_sfield<S>(ss, 6, cap, vh);
+  const SP r = pair_field<SP>(ss, 0, vh), rhat = pair_field<SP>(ss, 1, vh), pp = pair_field<SP>(ss, 2, vh);
+  const SP v = pair_field<SP>(ss, 3, vh), s = pair_field<SP>(ss, 4, vh), t = pair_field<SP>(ss, 5, vh);
+  const SP tmp = pair_field<SP>(ss, 6, vh);
   auto f32 = [&](int k) { F32F f; f.d = ss->f32 + (size_t)k * cap * 6 * vh; f.vh = vh; return f; };
-  F32F x32 = f32(0), b32 = f32(1), r32 = f32(2), t32 = f32(3), o32 = f32(4);
+  const F32F x32 = f32(0), b32 = f32(1), r32 = f32(2), t32 = f32(3), o32 = f32(4);
 
   SmallBufs sb = small_layout(ss->small, cap, nbx);
   SState *sc = sb.sc;
-  int *flags = sb.flags, *act_list = sb.act_list, *ru_list = sb.ru_list, *cyc_list = sb.cyc_list;
-  int *counts = sb.counts;  // [0] active, [1] reliable update, [2] this cycle
-  double *scale = sb.scale, *unscale = sb.unscale;
+  int *flags = sb.flags, *counts = sb.counts;
   D4S *part = sb.part;
 
   std::vector<double> rr(nrhs), bb(nrhs), prev_rel(nrhs, 1e300);
-  std::vector<SState> hs(nrhs);
-  std::vector<int> hl, bad(nrhs, 0);
-  std::vector<double> hscale(nrhs), hun(nrhs);
-  for (int k = 0; k < nrhs; ++k) {
-    hs[k] = SState{};
-    stats[k] = lqcd_solve_stats{0, LQCD_OK, 0.0, 0, 0};
-  }
+  std::vector<SState> hs(cap);
+  std::vector<int> hl, hp, bad(nrhs, 0), hflags(cap, 0);
+  std::vector<double> hscale(cap, 0.0), hun(cap, 0.0);
+  for (int k = 0; k < cap; ++k) hs[k] = SState{};
+  for (int k = 0; k < nrhs; ++k) stats[k] = lqcd_solve_stats{0, LQCD_OK, 0.0, 0, 0};
   LQCD_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, (size_t)nrhs * g.V * 12 * sizeof(double2), st));
   const int max_cycles = 10;
   bool timed_out = false;
 
-#define WL(list_ptr, count_ptr) list_ptr, count_ptr
   for (int cycle = 0; cycle <= max_cycles; ++cycle) {
-    rc = fp64_residual_into(ctx, b, x, ss->r64, nrhs, rr.data(), bb.data(), st);
+    // at x = 0 the residual is b itself: only its norm is needed
+    const double2 *r64 = cycle == 0 ? b : ss->r64;
+    rc = fp64_residual_into(ctx, b, cycle == 0 ? nullptr : x, ss->r64, nrhs, rr.data(), bb.data(), st);
     if (rc) return rc;
     hl.clear();
+    hp.clear();
+    std::fill(hflags.begin(), hflags.end(), 0);
     for (int k = 0; k < nrhs; ++k) {
       double rel = bb[k] > 0 ? std::sqrt(rr[k] / bb[k]) : 0.0;
       stats[k].true_rel_residual = rel;
@@ -829,92 +1169,78 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
       if (status == LQCD_OK && rel > p.tol) {
         if (timed_out) status = LQCD_ERR_TIMEOUT;
         else if (cycle == max_cycles || hs[k].iters >= p.max_iter) status = LQCD_ERR_NOT_CONVERGED;
-        else if (rel > 0.5 * prev_rel[k]) {
-          if (++bad[k] >= 3) status = LQCD_ERR_NOT_CONVERGED;  // refinement no longer reduces the residual
-        }
+        else if (rel > 0.5 * prev_rel[k] && ++bad[k] >= 3) status = LQCD_ERR_NOT_CONVERGED;
       }
       prev_rel[k] = rel;
       stats[k].status = status;
       hs[k].status = status;
+      hscale[k] = hun[k] = 0.0;
       if (status == LQCD_OK && rel > p.tol) {
         hl.push_back(k);
+        if (hp.empty() || hp.back() != k / 2) hp.push_back(k / 2);
         hscale[k] = 1.0 / std::sqrt(rr[k]);
         hun[k] = std::sqrt(rr[k]);
         hs[k].target2 = 0.25 * p.tol * p.tol * bb[k] / rr[k];
-        hs[k].ru_count = hs[k].ru_count;
-      } else {
-        hscale[k] = 0.0;
-        hun[k] = 0.0;
+        hflags[k] = FLAG_RU;  // marks the members whose inner source is loaded below
       }
     }
     if (hl.empty() || timed_out) break;
-    int ncyc = (int)hl.size();
-    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(cyc_list, hl.data(), ncyc * sizeof(int), cudaMemcpyHostToDevice, st));
-    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(counts + 2, &ncyc, sizeof(int), cudaMemcpyHostToDevice, st));
-    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(scale, hscale.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
-    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(unscale, hun.data(), nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
-    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sc, hs.data(), nrhs * sizeof(SState), cudaMemcpyHostToDevice, st));
+    int hc[5] = {0, 0, (int)hl.size(), 0, (int)hp.size()};
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.cyc_list, hl.data(), hl.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.cyc_pairs, hp.data(), hp.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(counts, hc, sizeof(hc), cudaMemcpyHostToDevice, st));
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.scale, hscale.data(), cap * sizeof(double), cudaMemcpyHostToDevice, st));
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.unscale, hun.data(), cap * sizeof(double), cudaMemcpyHostToDevice, st));
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sc, hs.data(), cap * sizeof(SState), cudaMemcpyHostToDevice, st));
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(flags, hflags.data(), cap * sizeof(int), cudaMemcpyHostToDevice, st));
     // inner right-hand side: b32 = scale (r_e + kappa H_eo r_o), o32 = scale r_o
-    KL k_cvt64to32<<<G, ST, 0, st>>>(g, 0, ss->r64, b32, scale, WL(cyc_list, counts + 2), nbx);
-    KL k_cvt64to32<<<G, ST, 0, st>>>(g, 1, ss->r64, o32, scale, WL(cyc_list, counts + 2), nbx);
-    KL k_hop_s<F32F, F32F, true, EPI_AXPY><<<G, ST, 0, st>>>(g, 0, ctx->U32, o32, b32, b32, b32, 1.f, 0.f, kappa,
-                                                            WL(cyc_list, counts + 2), nullptr, nbx, nullptr);
-    KL k_blas_copy<S><<<G, ST, 0, st>>>(vh, b32, F.r, F.r, false, x32, true, WL(cyc_list, counts + 2), part, nbx);
-    KL k_sfin_init<<<ncyc, 32, 0, st>>>(sc, flags, WL(cyc_list, counts + 2), part, nbx);
-    // floor of the inner target relative to |b32|^2
+    KL k_cvt64to32<<<G, ST, 0, st>>>(g, 0, r64, b32, sb.scale, sb.cyc_list, counts + 2, nbx);
+    KL k_cvt64to32<<<G, ST, 0, st>>>(g, 1, r64, o32, sb.scale, sb.cyc_list, counts + 2, nbx);
+    KL k_hop32<EPI_AXPY><<<G, ST, 0, st>>>(g, 0, L32, o32, b32, b32, b32, 1.f, 0.f, kappa, sb.cyc_list, counts + 2,
+                                           nullptr, nbx);
+    KL k_pair_copy<SP><<<G, ST, 0, st>>>(vh, flags, b32, r, r, false, x32, true, sb.cyc_pairs, counts + 4, part, nbx);
+    KL k_sfin_init<<<(int)hl.size(), 32, 0, st>>>(sc, flags, sb.cyc_list, counts + 2, part, nbx, floor2);
+    KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
     LQCD_LAUNCH_CHECK(ctx, "mixed: cycle setup");
-    {
-      // apply the floor: target2 = max(target2, floor2 * |b32|^2)
-      std::vector<SState> tmp(nrhs);
-      LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(tmp.data(), sc, nrhs * sizeof(SState), cudaMemcpyDeviceToHost, st));
-      LQCD_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-      std::vector<int> fl(nrhs, 0);
-      for (int k : hl) {
-        tmp[k].target2 = std::max(tmp[k].target2, floor2 * tmp[k].rr);
-        fl[k] = (tmp[k].status == LQCD_OK && tmp[k].rr > tmp[k].target2) ? FLAG_ACTIVE : 0;
-      }
-      LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sc, tmp.data(), nrhs * sizeof(SState), cudaMemcpyHostToDevice, st));
-      LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(flags, fl.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
-      LQCD_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-    }
-    KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, act_list, counts, ru_list, counts + 1);
     // ---------------------------------------------------------- inner loop
     bool any = true;
     while (any) {
       for (int it = 0; it < 4; ++it) {
-        KL k_blas_p<S><<<G, ST, 0, st>>>(vh, sc, F.r, F.rhat, F.p, F.v, WL(act_list, counts), nbx);
+        KL k_pair_p<SP><<<G, ST, 0, st>>>(vh, sc, r, rhat, pp, v, sb.act_pairs, counts, nbx);
         ev_begin();
-        KL k_hop_s<S, S, false, EPI_PLAIN><<<G, ST, 0, st>>>(g, 1, ctx->U16, F.p, F.tmp, F.tmp, F.tmp, 0.f, 0.f, 1.f,
-                                                          WL(act_list, counts), nullptr, nbx, prof);
+        KL k_hop_pair<SP, EPI_PLAIN><<<G, ST, 0, st>>>(g, 1, L16, pp, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
+                                                       nullptr, nbx, nrhs, prof);
         ev_end();
         ev_begin();
-        KL k_hop_s<S, S, false, EPI_DOTR><<<G, ST, 0, st>>>(g, 0, ctx->U16, F.tmp, F.v, F.p, F.rhat, 1.f, 0.f, -k2,
-                                                         WL(act_list, counts), part, nbx, prof);
+        KL k_hop_pair<SP, EPI_DOTR><<<G, ST, 0, st>>>(g, 0, L16, tmp, v, pp, rhat, 1.f, -k2, sb.act_pairs, counts,
+                                                      part, nbx, nrhs, prof);
         ev_end();
-        KL k_sfin_alpha<<<nrhs, 32, 0, st>>>(sc, WL(act_list, counts), part, nbx);
-        KL k_blas_s<S><<<G, ST, 0, st>>>(vh, sc, F.r, F.v, F.s, WL(act_list, counts), nbx);
+        KL k_sfin_alpha<<<npairs, 64, 0, st>>>(sc, flags, sb.act_pairs, counts, part, nbx, nrhs);
+        KL k_pair_s<SP><<<G, ST, 0, st>>>(vh, sc, r, v, s, sb.act_pairs, counts, nbx);
         ev_begin();
-        KL k_hop_s<S, S, false, EPI_PLAIN><<<G, ST, 0, st>>>(g, 1, ctx->U16, F.s, F.tmp, F.tmp, F.tmp, 0.f, 0.f, 1.f,
-                                                          WL(act_list, counts), nullptr, nbx, prof);
+        KL k_hop_pair<SP, EPI_PLAIN><<<G, ST, 0, st>>>(g, 1, L16, s, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
+                                                       nullptr, nbx, nrhs, prof);
         ev_end();
         ev_begin();
-        KL k_hop_s<S, S, false, EPI_TS><<<G, ST, 0, st>>>(g, 0, ctx->U16, F.tmp, F.t, F.s, F.s, 1.f, 0.f, -k2,
-                                                       WL(act_list, counts), part, nbx, prof);
+        KL k_hop_pair<SP, EPI_TS><<<G, ST, 0, st>>>(g, 0, L16, tmp, t, s, s, 1.f, -k2, sb.act_pairs, counts, part,
+                                                    nbx, nrhs, prof);
         ev_end();
-        KL k_sfin_omega<<<nrhs, 32, 0, st>>>(sc, WL(act_list, counts), part, nbx);
-        KL k_blas_xr<S><<<G, ST, 0, st>>>(vh, sc, x32, F.p, F.s, F.t, F.r, F.rhat, WL(act_list, counts), part, nbx);
-        KL k_sfin_conv<<<nrhs, 32, 0, st>>>(sc, flags, WL(act_list, counts), part, nbx, delta * delta, p.max_iter);
-        KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, act_list, counts, ru_list, counts + 1);
+        KL k_sfin_omega<<<npairs, 64, 0, st>>>(sc, flags, sb.act_pairs, counts, part, nbx, nrhs);
+        KL k_pair_xr<SP><<<G, ST, 0, st>>>(vh, sc, flags, x32, pp, s, t, r, rhat, sb.act_pairs, counts, part, nbx);
+        KL k_sfin_conv<<<npairs, 64, 0, st>>>(sc, flags, sb.act_pairs, counts, part, nbx, nrhs, delta * delta,
+                                              p.max_iter);
+        KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
         // reliable update in FP32: r32 = b32 - x32 + kappa^2 H_eo H_oe x32
-        KL k_hop_s<F32F, F32F, true, EPI_PLAIN><<<G, ST, 0, st>>>(g, 1, ctx->U32, x32, t32, t32, t32, 0.f, 0.f, 1.f,
-                                                               WL(ru_list, counts + 1), nullptr, nbx, nullptr);
-        KL k_hop_s<F32F, F32F, true, EPI_RES><<<G, ST, 0, st>>>(g, 0, ctx->U32, t32, r32, b32, x32, 1.f, -1.f, k2,
-                                                             WL(ru_list, counts + 1), part, nbx, nullptr);
-        KL k_sfin_ru<<<nrhs, 32, 0, st>>>(sc, flags, WL(ru_list, counts + 1), part, nbx, p.max_iter);
-        KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, act_list, counts, ru_list, counts + 1);
-        KL k_blas_copy<S><<<G, ST, 0, st>>>(vh, r32, F.r, F.rhat, true, x32, false, WL(ru_list, counts + 1), part, nbx);
-        KL k_sfin_ru2<<<nrhs, 32, 0, st>>>(sc, flags, WL(ru_list, counts + 1), part, nbx);
-        KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, act_list, counts, ru_list, counts + 1);
+        KL k_hop32<EPI_PLAIN><<<G, ST, 0, st>>>(g, 1, L32, x32, t32, t32, t32, 0.f, 0.f, 1.f, sb.ru_list, counts + 1,
+                                                nullptr, nbx);
+        KL k_hop32<EPI_RES><<<G, ST, 0, st>>>(g, 0, L32, t32, r32, b32, x32, 1.f, -1.f, k2, sb.ru_list, counts + 1,
+                                              part, nbx);
+        KL k_sfin_ru<<<nrhs, 32, 0, st>>>(sc, flags, sb.ru_list, counts + 1, part, nbx, p.max_iter);
+        KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
+        KL k_pair_copy<SP><<<G, ST, 0, st>>>(vh, flags, r32, r, rhat, true, x32, false, sb.ru_pairs, counts + 3, part,
+                                             nbx);
+        KL k_sfin_ru2<<<nrhs, 32, 0, st>>>(sc, flags, sb.ru_list, counts + 1, part, nbx);
+        KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
       }
       LQCD_LAUNCH_CHECK(ctx, "mixed: iteration");
       LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(ss->h_counts, counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -926,17 +1252,18 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
       }
     }
     // odd half of the correction: e_o = o32 + kappa H_oe x32; x += |r| e
-    KL k_hop_s<F32F, F32F, true, EPI_AXPY><<<G, ST, 0, st>>>(g, 1, ctx->U32, x32, o32, o32, o32, 1.f, 0.f, kappa,
-                                                            WL(cyc_list, counts + 2), nullptr, nbx, nullptr);
-    KL k_accum64<<<G, ST, 0, st>>>(g, 0, x32, x, unscale, WL(cyc_list, counts + 2), nbx);
-    KL k_accum64<<<G, ST, 0, st>>>(g, 1, o32, x, unscale, WL(cyc_list, counts + 2), nbx);
+    KL k_hop32<EPI_AXPY><<<G, ST, 0, st>>>(g, 1, L32, x32, o32, o32, o32, 1.f, 0.f, kappa, sb.cyc_list, counts + 2,
+                                           nullptr, nbx);
+    KL k_accum64<<<G, ST, 0, st>>>(g, 0, x32, x, sb.unscale, sb.cyc_list, counts + 2, nbx);
+    KL k_accum64<<<G, ST, 0, st>>>(g, 1, o32, x, sb.unscale, sb.cyc_list, counts + 2, nbx);
     LQCD_LAUNCH_CHECK(ctx, "mixed: correction");
-    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(hs.data(), sc, nrhs * sizeof(SState), cudaMemcpyDeviceToHost, st));
+    std::vector<int> keep_status(nrhs);
+    for (int k = 0; k < nrhs; ++k) keep_status[k] = hs[k].status;
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(hs.data(), sc, cap * sizeof(SState), cudaMemcpyDeviceToHost, st));
     LQCD_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     for (int k = 0; k < nrhs; ++k)
-      if (std::find(hl.begin(), hl.end(), k) == hl.end()) hs[k].status = stats[k].status;
+      if (!std::binary_search(hl.begin(), hl.end(), k)) hs[k].status = keep_status[k];
   }
-#undef WL
   return LQCD_OK;
 }
 
@@ -950,8 +1277,8 @@ int mixed_solve(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const lqc
   for (int k0 = 0; k0 < nrhs; k0 += blk) {
     int nk = std::min(blk, nrhs - k0);
     int rc = p.precision == LQCD_PREC_MIXED_FP16
-                 ? mixed_block<F16F>(ctx, b + k0 * full, x + k0 * full, nk, p, stats + k0, st, t0)
-                 : mixed_block<BF16F>(ctx, b + k0 * full, x + k0 * full, nk, p, stats + k0, st, t0);
+                 ? mixed_block<F16P>(ctx, b + k0 * full, x + k0 * full, nk, p, stats + k0, st, t0)
+                 : mixed_block<BF16P>(ctx, b + k0 * full, x + k0 * full, nk, p, stats + k0, st, t0);
     if (rc) return rc;
     for (int k = 0; k < nk; ++k)
       if (worst == LQCD_OK && stats[k0 + k].status != LQCD_OK) worst = stats[k0 + k].status;
