@@ -123,6 +123,14 @@ const char *lqcd_last_error(const lqcd_ctx *ctx);
  * from unitarity or unit determinant by more than 1e-12 (nothing is kept). */
 int lqcd_set_gauge(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream);
 
+/* As lqcd_set_gauge but for arbitrary complex 3x3 links (no SU(3) check).
+ * The operator D is defined for any links; only the FP64 path can use such a
+ * field (the reduced-precision copies rely on reconstruct-12, valid for SU(3)
+ * only), and mixed-precision solves then fail with LQCD_ERR_INVALID.  Exists so
+ * that gradients can be checked entry by entry (finite differences leave
+ * SU(3)); the paper has no counterpart. */
+int lqcd_set_gauge_general(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream);
+
 /* Set the hopping parameter kappa of D (Sec. II: kappa = 0.157 for SESAM). */
 int lqcd_set_kappa(lqcd_ctx *ctx, double kappa);
 
@@ -176,6 +184,26 @@ int lqcd_noise_generate(uint64_t seed, uint64_t noise_stream, uint64_t noise_ind
  * order (bit-reproducible). */
 int lqcd_loops_batch(lqcd_ctx *ctx, const double *src, const double *sol, int nrhs,
                      double weight, double *per_site, double *per_t, lqcd_stream_t stream);
+
+/* Gradient of a real loss of the per-time-slice loops by adjoint solves (the
+ * paper computes no gradients; this is the derivative of its stochastic loop
+ * estimator, Eq. loop stochastic, for fixed noise).
+ *   src, sol: [nrhs][V][4][3] complex128 device -- the noise pieces xi_d and
+ *             their forward solutions phi_d = D^{-1} xi_d (from lqcd_solve_batch).
+ *   coef:     host [Lt][6] complex128, c[t][g] = d loss / d Re L_g(t)
+ *             + i d loss / d Im L_g(t) for the loops L_g(t) = sum_{x in t}
+ *             sum_d xi_d(x)^+ Gamma_g phi_d(x) (Gamma order 1, g5, g1..g4).
+ * Solves D y_d = gamma5 M^+ xi_d with M(x) = sum_g conj(c[t(x)][g]) Gamma_g
+ * (params as for lqcd_solve_batch; D^+ = gamma5 D gamma5 makes chi_d = gamma5 y_d
+ * the adjoint solution), then accumulates
+ *   *dkappa (host, may be NULL) += weight * Re sum_d chi_d^+ H phi_d   (= d loss / d kappa)
+ *   dU (device [V][4][3][3] complex128, may be NULL) += weight * d loss / d U
+ * in the convention d loss = Re sum conj(dU_ij) dU_ij (torch's for complex
+ * leaves), FP64 accumulation in a fixed order.  stats (host, nrhs) report the
+ * adjoint solves; the return value is that of the adjoint solves. */
+int lqcd_gradient(lqcd_ctx *ctx, const double *src, const double *sol, int nrhs, const double *coef, double weight,
+                  const lqcd_solver_params *params, double *dkappa, double *dU, lqcd_solve_stats *stats,
+                  lqcd_stream_t stream);
 
 /* No-allocation variant of lqcd_loops_batch.  The paper has no counterpart:
  * this exists for callers that cannot allocate device memory -- code that

@@ -229,7 +229,17 @@ int lqcd_destroy(lqcd_ctx *ctx) {
 
 const char *lqcd_last_error(const lqcd_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }
 
+static int set_gauge_impl(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream, bool require_su3);
+
 int lqcd_set_gauge(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream) {
+  return set_gauge_impl(ctx, U, stream, true);
+}
+
+int lqcd_set_gauge_general(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream) {
+  return set_gauge_impl(ctx, U, stream, false);
+}
+
+static int set_gauge_impl(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream, bool require_su3) {
   if (!ctx || !U) return set_error(ctx, LQCD_ERR_INVALID, "lqcd_set_gauge: null argument");
   cudaSetDevice(ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -252,12 +262,13 @@ int lqcd_set_gauge(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream) {
   int flag = 0;
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   LQCD_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-  if (flag) {
+  if (flag && require_su3) {
     ctx->have_gauge = false;
     return set_error(ctx, LQCD_ERR_NOT_SU3, "lqcd_set_gauge: a link is not SU(3) within 1e-12");
   }
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->U64, stage, n64 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   ctx->have_gauge = true;
+  ctx->gauge_su3 = !flag;
   int rc = pack_gauge_sloppy(ctx, st);
   if (rc != LQCD_OK) return rc;
   LQCD_CUDA_TRY(ctx, cudaStreamSynchronize(st));

@@ -149,6 +149,7 @@ struct lqcd_ctx {
   lqcd::Geom geom;
   double kappa = 0.0;
   bool have_gauge = false;
+  bool gauge_su3 = false;     // links checked SU(3): reconstruct-12 copies are valid
   double2 *U64 = nullptr;     // canonical [V][4][3][3]
   float4 *U32 = nullptr;      // recon-12 FP32  [2 parity][4 mu][3 float4][Vh]
   uint4 *U16 = nullptr;       // recon-12 FP16, each real twice  [2 parity][4 mu][3 uint4][Vh]

@@ -1269,6 +1269,10 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
 
 int mixed_solve(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const lqcd_solver_params &p,
                 lqcd_solve_stats *stats, cudaStream_t st) {
+  if (!ctx->gauge_su3)
+    return set_error(ctx, LQCD_ERR_INVALID,
+                     "mixed precision needs SU(3) links (reconstruct-12); this gauge field was set with "
+                     "lqcd_set_gauge_general: use LQCD_PREC_FP64");
   int blk = p.rhs_block > 0 ? p.rhs_block : nrhs;
   if (blk > 4096) blk = 4096;
   double t0 = wall_ms();

@@ -85,6 +85,7 @@ _SIGS = {
     "lqcd_destroy": (_i, [_vp]),
     "lqcd_last_error": (ctypes.c_char_p, [_vp]),
     "lqcd_set_gauge": (_i, [_vp, _vp, _vp]),
+    "lqcd_set_gauge_general": (_i, [_vp, _vp, _vp]),
     "lqcd_set_kappa": (_i, [_vp, _d]),
     "lqcd_plaquette": (_i, [_vp, ctypes.POINTER(_d), _vp]),
     "lqcd_apply_dirac": (_i, [_vp, _vp, _vp, _i, _i, _vp]),
@@ -93,6 +94,8 @@ _SIGS = {
     "lqcd_point_sources": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), _i, _vp, _vp]),
     "lqcd_noise_generate": (_i, [_u64, _u64, _u64, ctypes.POINTER(_i), _i, _i, _i, _vp, _vp]),
     "lqcd_loops_batch": (_i, [_vp, _vp, _vp, _i, _d, _vp, _vp, _vp]),
+    "lqcd_gradient": (_i, [_vp, _vp, _vp, _i, _vp, _d, ctypes.POINTER(lqcd_solver_params), ctypes.POINTER(_d), _vp,
+                           ctypes.POINTER(lqcd_solve_stats), _vp]),
     "lqcd_loops_batch_noalloc": (_i, [ctypes.POINTER(_i), _vp, _vp, _i, _d, _vp, _vp, _vp]),
     "lqcd_profile_begin": (_i, [_vp]),
     "lqcd_profile_end": (_i, [_vp, ctypes.POINTER(lqcd_profile)]),
@@ -174,6 +177,11 @@ def lqcd_set_gauge(h, U):
     return _check(load().lqcd_set_gauge(h, _ptr(U), _stream(U)), h)
 
 
+def lqcd_set_gauge_general(h, U):
+    """Arbitrary complex links (no SU(3) check; FP64 solves only)."""
+    return _check(load().lqcd_set_gauge_general(h, _ptr(U), _stream(U)), h)
+
+
 def lqcd_set_kappa(h, kappa):
     return _check(load().lqcd_set_kappa(h, float(kappa)), h)
 
@@ -246,3 +254,21 @@ def lqcd_loops_batch_noalloc(dims, src, sol, weight=1.0, per_site=None, per_t=No
     rc = load().lqcd_loops_batch_noalloc(_dims(dims), _ptr(src), _ptr(sol), nrhs, float(weight), _ptr(per_site),
                                          _ptr(per_t), _stream(src))
     return _check(rc, None)
+
+
+def lqcd_gradient(h, src, sol, coef, params, weight=1.0, dU=None):
+    """Adjoint-solve gradient of a real loss of the per-time-slice loops.
+
+    coef: complex128 host tensor/array [Lt, 6] (d loss / d Re L + i d loss / d Im L).
+    Returns (d loss / d kappa, status, stats); d loss / d U is accumulated into dU.
+    """
+    import numpy as np
+    c = np.ascontiguousarray(np.asarray(coef.cpu() if hasattr(coef, "cpu") else coef, dtype=np.complex128))
+    nrhs = src.shape[0]
+    stats = (lqcd_solve_stats * max(nrhs, 1))()
+    dk = ctypes.c_double(0.0)
+    rc = load().lqcd_gradient(h, _ptr(src), _ptr(sol), nrhs, c.ctypes.data_as(ctypes.c_void_p), float(weight),
+                              ctypes.byref(params), ctypes.byref(dk), _ptr(dU), stats, _stream(src))
+    if rc in (LQCD_ERR_INVALID, LQCD_ERR_CUDA, LQCD_ERR_NO_GAUGE, LQCD_ERR_OOM):
+        raise LqcdError(rc, _err(h))
+    return dk.value, rc, [stats[k].as_dict() for k in range(nrhs)]
