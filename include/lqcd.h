@@ -156,6 +156,30 @@ int lqcd_solve_batch(lqcd_ctx *ctx, const double *b, double *x, int nrhs,
                      const lqcd_solver_params *params, lqcd_solve_stats *stats,
                      lqcd_stream_t stream);
 
+/* Uneven batch: several lattices (each its own context: dims, gauge field and
+ * kappa) solved together (Sec. II: all inversions on the GPU; here several
+ * configurations / kappas at once).  lqcd_batch_add registers b, x ([nrhs][V]
+ * [4][3] complex128, device) of one context (one entry per context, all on one
+ * device).  lqcd_batch_run solves every entry with *params: in mixed precision
+ * the inner iterations of all lattices are captured into one CUDA graph (one
+ * branch per lattice) on `stream`, which must be a created stream (not the
+ * legacy default); one graph launch advances every lattice by four iterations,
+ * and each lattice's outer FP64 refinement runs between launches.  FP64 solves
+ * the entries one after another.  stats: host array with one record per RHS in
+ * the order of lqcd_batch_add.  Returns LQCD_OK only if every RHS converged. */
+int lqcd_batch_create(lqcd_batch **out);
+int lqcd_batch_add(lqcd_batch *batch, lqcd_ctx *ctx, const double *b, double *x, int nrhs);
+int lqcd_batch_run(lqcd_batch *batch, const lqcd_solver_params *params, lqcd_solve_stats *stats,
+                   lqcd_stream_t stream);
+int lqcd_batch_destroy(lqcd_batch *batch);
+
+/* Autotuner: time the reduced-precision hopping term for nrhs right-hand
+ * sides of `precision` on this context over the candidate launch grids
+ * (2, 4, 8, 16 blocks of 128 sites per SM) and keep the fastest for later
+ * solves of that (nrhs, precision); *best_blocks_per_sm (host, may be NULL)
+ * receives it.  Needs a gauge field.  Synchronises the device. */
+int lqcd_autotune(lqcd_ctx *ctx, int nrhs, int precision, int *best_blocks_per_sm);
+
 /* Point sources e_{x,spin,colour} (Sec. II: exact all-to-all propagator from
  * one inversion per site, spin and colour).  sites: host array of n_sites
  * site indices; out: [12 n_sites][V][4][3] complex128 (device), source
@@ -184,6 +208,36 @@ int lqcd_noise_generate(uint64_t seed, uint64_t noise_stream, uint64_t noise_ind
  * order (bit-reproducible). */
 int lqcd_loops_batch(lqcd_ctx *ctx, const double *src, const double *sol, int nrhs,
                      double weight, double *per_site, double *per_t, lqcd_stream_t stream);
+
+/* Stochastic loops with dilution and the truncated solver method (Sec. II,
+ * Eq. loop stochastic; TSM after Bali, Collins, Schafer):
+ *   L += (1/n_lp) sum_{r<n_lp} sum_d xi_{r,d}^+ Gamma phi^{LP}_{r,d}
+ *      + (1/n_hp) sum_{r<n_hp} sum_d eta_{r,d}^+ Gamma (phi^{HP}_{r,d} - phi^{LP}_{r,d})
+ * xi: noise vectors first_noise .. of stream LQCD_STREAM_LP, eta: vectors
+ * first_noise .. of stream LQCD_STREAM_HP, each split into its dilution pieces
+ * d; phi^{LP} solved to tol_lp, phi^{HP} to tol_hp (true FP64 residual), both
+ * with the same solver settings, so phi^{LP} of a HP vector is exactly what the
+ * LP solver gives it.  n_hp = 0 gives the plain diluted estimator at tol_lp. */
+typedef struct {
+  uint64_t seed;
+  uint64_t first_noise;
+  int dilution;   /* LQCD_DILUTE_*                                        */
+  int n_lp;       /* vectors of the low-precision (or plain) set, >= 1     */
+  int n_hp;       /* vectors of the high-precision correction set, >= 0   */
+  double tol_lp;  /* relative residual of the LP (or plain) solves         */
+  double tol_hp;  /* relative residual of the HP solves                    */
+  int chunk;      /* dilution pieces solved together; 0 = automatic        */
+} lqcd_stochastic_params;
+
+/* Runs the estimator above end to end on the device (noise generation,
+ * batched solves with *solver's precision / iteration cap / reliable-update
+ * settings, contraction) and accumulates into per_site ([V][6] complex128,
+ * device, may be NULL) and per_t ([Lt][6] complex128, device or host, may be
+ * NULL).  summary (host, may be NULL): [0] the LP solves, [1] the HP solves --
+ * largest iteration count and true residual, worst status.  Returns LQCD_OK
+ * only if every solve converged.  Synchronises stream. */
+int lqcd_loops_stochastic(lqcd_ctx *ctx, const lqcd_stochastic_params *sp, const lqcd_solver_params *solver,
+                          double *per_site, double *per_t, lqcd_solve_stats *summary, lqcd_stream_t stream);
 
 /* Gradient of a real loss of the per-time-slice loops by adjoint solves (the
  * paper computes no gradients; this is the derivative of its stochastic loop

@@ -114,6 +114,7 @@ int launch_hop64(lqcd_ctx *ctx, cudaStream_t st, bool dag, bool in_canon, bool o
   HOP64_CASE(false, true, false)
   HOP64_CASE(false, false, true)
   HOP64_CASE(true, true, true)
+  HOP64_CASE(true, false, false)
 #undef HOP64_CASE
   return set_error(ctx, LQCD_ERR_INVALID, "launch_hop64: unsupported layout combination");
 }
@@ -662,6 +663,226 @@ static int fp64_solve_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrh
   return LQCD_OK;
 }
 
+// ------------------------------------------------------------ CG (CGNR)
+// CG on the normal equations of the Schur operator A = D_hat:
+// A^+ A x = A^+ b_hat, with A^+ = gamma5 A gamma5 (the dagger hopping term),
+// stopping on the Schur residual s = b_hat - A x (tracked by the recursion and
+// checked against the true full-lattice FP64 residual afterwards).
+struct SCG {
+  double alpha, beta, rr, ss, target2;
+  int iters, status, pad;
+};
+
+__global__ void k_cg_fin_init(SCG *sc, int *active, const D4 *part_r, const D4 *part_s, int nb, int max_iter) {
+  int rhs = blockIdx.x;
+  if (!active[rhs]) return;
+  D4 tr = warp_total(part_r + (size_t)rhs * nb, nb);
+  D4 ts = warp_total(part_s + (size_t)rhs * nb, nb);
+  if (threadIdx.x) return;
+  SCG &c = sc[rhs];
+  c.rr = tr.c;
+  c.ss = ts.c;
+  if (!isfinite(tr.c) || !isfinite(ts.c)) {
+    c.status = LQCD_ERR_NONFINITE;
+    active[rhs] = 0;
+  } else if (ts.c <= c.target2 || tr.c == 0.0) {
+    active[rhs] = 0;
+  } else if (c.iters >= max_iter) {
+    c.status = LQCD_ERR_NOT_CONVERGED;
+    active[rhs] = 0;
+  }
+}
+
+__global__ void k_cg_fin_alpha(SCG *sc, const int *active, const D4 *part, int nb) {
+  int rhs = blockIdx.x;
+  if (!active[rhs]) return;
+  D4 t = warp_total(part + (size_t)rhs * nb, nb);  // |A p|^2 in .c
+  if (threadIdx.x) return;
+  sc[rhs].alpha = t.c > 0.0 ? sc[rhs].rr / t.c : 0.0;
+}
+
+// x += alpha p; s -= alpha q; partial |s|^2
+__global__ void __launch_bounds__(RED_THREADS) k_cg_xs(size_t n, const SCG *sc, const int *active, double2 *x,
+                                                       const double2 *p, double2 *s, const double2 *q, D4 *part) {
+  int rhs = blockIdx.y;
+  if (!active[rhs]) return;
+  double a = sc[rhs].alpha;
+  size_t off = (size_t)rhs * n;
+  D4 acc = {0, 0, 0, 0};
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    x[off + k] = cadd(x[off + k], cscale(p[off + k], a));
+    double2 v = csub(s[off + k], cscale(q[off + k], a));
+    s[off + k] = v;
+    acc.c += v.x * v.x + v.y * v.y;
+  }
+  D4 r = block_sum4(acc);
+  if (threadIdx.x == 0) part[(size_t)rhs * gridDim.x + blockIdx.x] = r;
+}
+
+__global__ void k_cg_fin_ss(SCG *sc, int *active, const D4 *part, int nb, int max_iter) {
+  int rhs = blockIdx.x;
+  if (!active[rhs]) return;
+  D4 t = warp_total(part + (size_t)rhs * nb, nb);
+  if (threadIdx.x) return;
+  SCG &c = sc[rhs];
+  c.ss = t.c;
+  c.iters += 1;
+  if (!isfinite(t.c)) {
+    c.status = LQCD_ERR_NONFINITE;
+    active[rhs] = 0;
+  } else if (t.c <= c.target2) {
+    active[rhs] = 0;
+  } else if (c.iters >= max_iter) {
+    c.status = LQCD_ERR_NOT_CONVERGED;
+    active[rhs] = 0;
+  }
+}
+
+__global__ void k_cg_fin_beta(SCG *sc, const int *active, const D4 *part, int nb) {
+  int rhs = blockIdx.x;
+  if (!active[rhs]) return;
+  D4 t = warp_total(part + (size_t)rhs * nb, nb);
+  if (threadIdx.x) return;
+  SCG &c = sc[rhs];
+  c.beta = c.rr > 0.0 ? t.c / c.rr : 0.0;
+  c.rr = t.c;
+}
+
+// p = r + beta p (beta = 0 on the first use)
+__global__ void __launch_bounds__(RED_THREADS) k_cg_p(size_t n, const SCG *sc, const int *active, const double2 *r,
+                                                      double2 *p) {
+  int rhs = blockIdx.y;
+  if (!active[rhs]) return;
+  double b = sc[rhs].beta;
+  size_t off = (size_t)rhs * n;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+    p[off + k] = cadd(r[off + k], cscale(p[off + k], b));
+}
+
+static int fp64_cg_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const lqcd_solver_params &p,
+                         lqcd_solve_stats *stats, cudaStream_t st, double t_start) {
+  const Geom &g = ctx->geom;
+  const double kappa = ctx->kappa, k2 = kappa * kappa;
+  size_t n = (size_t)g.Vh * 12;
+  int rc = LQCD_OK;
+  double2 *vec = (double2 *)workspace(ctx, WS_F64_VECS, (size_t)9 * nrhs * n * sizeof(double2), &rc);
+  if (!vec) return rc;
+  double2 *xe = vec, *s = vec + (size_t)nrhs * n, *r = s + (size_t)nrhs * n, *pp = r + (size_t)nrhs * n;
+  double2 *q = pp + (size_t)nrhs * n, *tmp = q + (size_t)nrhs * n, *bo = tmp + (size_t)nrhs * n;
+  double2 *bhat = bo + (size_t)nrhs * n, *be = bhat + (size_t)nrhs * n;
+  int nb = red_blocks(n);
+  Carver sizing(nullptr);
+  sizing.take<SCG>(nrhs);
+  sizing.take<int>(nrhs);
+  sizing.take<D4>((size_t)nrhs * nb);
+  sizing.take<D4>((size_t)nrhs * nb);
+  char *sw = (char *)workspace(ctx, WS_F64_SCAL, sizing.size(), &rc);
+  if (!sw) return rc;
+  Carver cv(sw);
+  SCG *sc = cv.take<SCG>(nrhs);
+  int *active = cv.take<int>(nrhs);
+  D4 *part = cv.take<D4>((size_t)nrhs * nb);
+  D4 *part2 = cv.take<D4>((size_t)nrhs * nb);
+  std::vector<double> rr(nrhs), bb(nrhs);
+  std::vector<SCG> hs(nrhs);
+  std::vector<int> hact(nrhs, 1);
+  dim3 gv((g.Vh + 127) / 128, nrhs), gr(nb, nrhs);
+  LQCD_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, (size_t)nrhs * g.V * 12 * sizeof(double2), st));
+  rc = fp64_true_residual(ctx, b, x, nrhs, rr.data(), bb.data(), st);  // |b|^2
+  if (rc) return rc;
+  KL k_split64<<<gv, 128, 0, st>>>(g, 1, b, bo);
+  KL k_split64<<<gv, 128, 0, st>>>(g, 0, b, be);
+  rc = launch_hop64(ctx, st, false, false, false, 0, bo, n, bhat, n, be, 1.0, nullptr, 0.0, kappa, nullptr, nrhs);
+  if (rc) return rc;
+  LQCD_CUDA_TRY(ctx, cudaMemsetAsync(xe, 0, (size_t)nrhs * n * sizeof(double2), st));
+  for (int k = 0; k < nrhs; ++k) {
+    hs[k] = SCG{};
+    hs[k].target2 = 0.25 * p.tol * p.tol * bb[k];
+  }
+  LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sc, hs.data(), nrhs * sizeof(SCG), cudaMemcpyHostToDevice, st));
+  const int max_restarts = 6;
+  for (int restart = 0; restart <= max_restarts; ++restart) {
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(active, hact.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+    // s = b_hat - A x_e ; r = A^+ s ; p = r
+    launch_hop64(ctx, st, false, false, false, 1, xe, n, tmp, n, nullptr, 0.0, nullptr, 0.0, 1.0, active, nrhs);
+    launch_hop64(ctx, st, false, false, false, 0, tmp, n, s, n, bhat, 1.0, xe, -1.0, k2, active, nrhs);
+    launch_hop64(ctx, st, true, false, false, 1, s, n, tmp, n, nullptr, 0.0, nullptr, 0.0, 1.0, active, nrhs);
+    launch_hop64(ctx, st, true, false, false, 0, tmp, n, r, n, s, 1.0, nullptr, 0.0, -k2, active, nrhs);
+    KL k_dot64<<<gr, RED_THREADS, 0, st>>>(n, active, r, r, part);
+    KL k_dot64<<<gr, RED_THREADS, 0, st>>>(n, active, s, s, part2);
+    KL k_cg_fin_init<<<nrhs, 32, 0, st>>>(sc, active, part, part2, nb, p.max_iter);
+    LQCD_CUDA_TRY(ctx, cudaMemsetAsync(pp, 0, (size_t)nrhs * n * sizeof(double2), st));
+    {  // beta = 0 for the first direction
+      std::vector<SCG> tmp_h(nrhs);
+      LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(tmp_h.data(), sc, nrhs * sizeof(SCG), cudaMemcpyDeviceToHost, st));
+      LQCD_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+      for (auto &c : tmp_h) c.beta = 0.0;
+      LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sc, tmp_h.data(), nrhs * sizeof(SCG), cudaMemcpyHostToDevice, st));
+    }
+    KL k_cg_p<<<gr, RED_THREADS, 0, st>>>(n, sc, active, r, pp);
+    bool any = true, timed_out = false;
+    while (any) {
+      for (int it = 0; it < 4; ++it) {
+        // q = A p
+        launch_hop64(ctx, st, false, false, false, 1, pp, n, tmp, n, nullptr, 0.0, nullptr, 0.0, 1.0, active, nrhs);
+        launch_hop64(ctx, st, false, false, false, 0, tmp, n, q, n, pp, 1.0, nullptr, 0.0, -k2, active, nrhs);
+        KL k_dot64<<<gr, RED_THREADS, 0, st>>>(n, active, q, q, part);
+        KL k_cg_fin_alpha<<<nrhs, 32, 0, st>>>(sc, active, part, nb);
+        KL k_cg_xs<<<gr, RED_THREADS, 0, st>>>(n, sc, active, xe, pp, s, q, part);
+        KL k_cg_fin_ss<<<nrhs, 32, 0, st>>>(sc, active, part, nb, p.max_iter);
+        // r = A^+ s
+        launch_hop64(ctx, st, true, false, false, 1, s, n, tmp, n, nullptr, 0.0, nullptr, 0.0, 1.0, active, nrhs);
+        launch_hop64(ctx, st, true, false, false, 0, tmp, n, r, n, s, 1.0, nullptr, 0.0, -k2, active, nrhs);
+        KL k_dot64<<<gr, RED_THREADS, 0, st>>>(n, active, r, r, part);
+        KL k_cg_fin_beta<<<nrhs, 32, 0, st>>>(sc, active, part, nb);
+        KL k_cg_p<<<gr, RED_THREADS, 0, st>>>(n, sc, active, r, pp);
+      }
+      LQCD_LAUNCH_CHECK(ctx, "cg iteration");
+      LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(hact.data(), active, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
+      LQCD_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+      any = false;
+      for (int k = 0; k < nrhs; ++k) any = any || hact[k];
+      if (any && p.timeout_ms > 0 && wall_ms() - t_start > p.timeout_ms) {
+        timed_out = true;
+        break;
+      }
+    }
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(hs.data(), sc, nrhs * sizeof(SCG), cudaMemcpyDeviceToHost, st));
+    rc = launch_hop64(ctx, st, false, false, false, 1, xe, n, tmp, n, bo, 1.0, nullptr, 0.0, kappa, nullptr, nrhs);
+    if (rc) return rc;
+    KL k_merge64<<<gv, 128, 0, st>>>(g, 0, xe, x, nullptr);
+    KL k_merge64<<<gv, 128, 0, st>>>(g, 1, tmp, x, nullptr);
+    LQCD_LAUNCH_CHECK(ctx, "k_merge64");
+    rc = fp64_true_residual(ctx, b, x, nrhs, rr.data(), bb.data(), st);
+    if (rc) return rc;
+    bool again = false;
+    for (int k = 0; k < nrhs; ++k) {
+      double rel = bb[k] > 0 ? std::sqrt(rr[k] / bb[k]) : 0.0;
+      stats[k].iterations = hs[k].iters;
+      stats[k].true_rel_residual = rel;
+      stats[k].reliable_updates = 0;
+      stats[k].restarts = restart;
+      int status = hs[k].status;
+      if (timed_out && status == LQCD_OK && !(rel <= p.tol)) status = LQCD_ERR_TIMEOUT;
+      if (status == LQCD_OK && !std::isfinite(rel)) status = LQCD_ERR_NONFINITE;
+      stats[k].status = status;
+      hact[k] = 0;
+      if (status == LQCD_OK && rel > p.tol) {
+        if (restart == max_restarts) {
+          stats[k].status = LQCD_ERR_NOT_CONVERGED;
+        } else {
+          hact[k] = 1;
+          again = true;
+          hs[k].target2 *= 0.01;
+        }
+      }
+    }
+    if (!again || timed_out) break;
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sc, hs.data(), nrhs * sizeof(SCG), cudaMemcpyHostToDevice, st));
+  }
+  return LQCD_OK;
+}
+
 int fp64_solve(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const lqcd_solver_params &p,
                lqcd_solve_stats *stats, cudaStream_t st) {
   int blk = p.rhs_block > 0 ? p.rhs_block : 1;  // the plain solver: one RHS at a time
@@ -671,7 +892,8 @@ int fp64_solve(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const lqcd
   int worst = LQCD_OK;
   for (int k0 = 0; k0 < nrhs; k0 += blk) {
     int nk = nrhs - k0 < blk ? nrhs - k0 : blk;
-    int rc = fp64_solve_block(ctx, b + k0 * full, x + k0 * full, nk, p, stats + k0, st, t0);
+    int rc = p.solver == LQCD_SOLVER_CG ? fp64_cg_block(ctx, b + k0 * full, x + k0 * full, nk, p, stats + k0, st, t0)
+                                        : fp64_solve_block(ctx, b + k0 * full, x + k0 * full, nk, p, stats + k0, st, t0);
     if (rc) return rc;
     for (int k = 0; k < nk; ++k)
       if (worst == LQCD_OK && stats[k0 + k].status != LQCD_OK) worst = stats[k0 + k].status;

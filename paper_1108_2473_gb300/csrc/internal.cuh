@@ -165,6 +165,8 @@ struct lqcd_ctx {
   long long prof_hop_launches = 0;
   long long prof_launch_base = 0;
   int prof_prec = 0;
+  // autotuned launch grid (blocks per SM) per (nrhs, precision)
+  std::vector<std::pair<long long, int>> tuned;
 };
 
 namespace lqcd {

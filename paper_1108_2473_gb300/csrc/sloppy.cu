@@ -999,6 +999,9 @@ struct SloppyState {
   double2 *r64 = nullptr;  // canonical FP64 residual
   char *small = nullptr;
   int *h_counts = nullptr;  // pinned
+  // captured graph of four inner iterations, valid while graph_key matches
+  cudaGraphExec_t graph = nullptr;
+  std::vector<double> graph_key;
 };
 
 void sloppy_free(lqcd_ctx *ctx) {
@@ -1010,6 +1013,7 @@ void sloppy_free(lqcd_ctx *ctx) {
   cudaFree(s->r64);
   cudaFree(s->small);
   if (s->h_counts) cudaFreeHost(s->h_counts);
+  if (s->graph) cudaGraphExecDestroy(s->graph);
   delete s;
   ctx->sloppy = nullptr;
 }
@@ -1059,6 +1063,11 @@ static int sloppy_alloc(lqcd_ctx *ctx, int nrhs) {
   const int cap = (nrhs + 1) & ~1;
   if (s->cap >= cap) return LQCD_OK;
   cudaDeviceSynchronize();
+  if (s->graph) {
+    cudaGraphExecDestroy(s->graph);
+    s->graph = nullptr;
+    s->graph_key.clear();
+  }
   cudaFree(s->sd);
   cudaFree(s->sn);
   cudaFree(s->f32);
@@ -1092,68 +1101,91 @@ template <> BF16P pair_field<BF16P>(SloppyState *st, int f, int vh) {
   return BF16P{st->sd + (size_t)f * pairs * 6 * vh, vh};
 }
 
+static int tuned_blocks_per_sm(const lqcd_ctx *ctx, int nrhs, int precision) {
+  long long key = (long long)nrhs * 8 + precision;
+  for (auto &kv : ctx->tuned)
+    if (kv.first == key) return kv.second;
+  return 8;
+}
+
+// One lattice's mixed-precision solve as a resumable state machine:
+//   cycle_start()    FP64 residual b - D x, per-RHS decisions, inner source
+//   launch_iters()   a fixed sequence of inner BiCGstab iterations (capturable:
+//                    every kernel reads its work list and counts from device memory)
+//   poll()           after the stream has drained: is the inner solve over?
+//   cycle_end()      odd reconstruction and x += |r| e in FP64
 template <class SP>
-static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const lqcd_solver_params &p,
-                       lqcd_solve_stats *stats, cudaStream_t st, double t0) {
-  int rc = sloppy_alloc(ctx, nrhs);
-  if (rc) return rc;
-  SloppyState *ss = ctx->sloppy;
-  const Geom &g = ctx->geom;
-  const int vh = g.Vh, cap = ss->cap;
-  const int nbx = (vh + ST - 1) / ST;
-  const float kappa = (float)ctx->kappa;
-  const float k2 = (float)(ctx->kappa * ctx->kappa);
-  const int G = num_sms(ctx->device) * 8;
-  const int npairs = (nrhs + 1) / 2;
-  const double delta = p.delta > 0 ? p.delta : 0.1;
-  const double floor2 = 4e-12;  // (2e-6)^2: inner FP32 target floor, relative to |b_inner|^2
-  const uint4 *L16 = ctx->U16;
-  const float4 *L32 = ctx->U32;
-
-  // measurement of the dominant kernel (sloppy hopping term), when enabled
-  unsigned long long *prof = ctx->prof_on ? ctx->d_prof : nullptr;
-  if (ctx->prof_on) ctx->prof_prec = p.precision;
-  auto ev_begin = [&]() {
-    if (!ctx->prof_on) return;
-    while (ctx->prof_used + 2 > ctx->prof_ev.size()) {
-      cudaEvent_t e;
-      if (cudaEventCreate(&e) != cudaSuccess) { ctx->prof_on = false; return; }
-      ctx->prof_ev.push_back(e);
-    }
-    cudaEventRecord(ctx->prof_ev[ctx->prof_used], st);
-  };
-  auto ev_end = [&]() {
-    if (!ctx->prof_on) return;
-    cudaEventRecord(ctx->prof_ev[ctx->prof_used + 1], st);
-    ctx->prof_used += 2;
-    ctx->prof_hop_launches++;
-  };
-
-  const SP r = pair_field<SP>(ss, 0, vh), rhat = pair_field<SP>(ss, 1, vh), pp = pair_field<SP>(ss, 2, vh);
-  const SP v = pair_field<SP>(ss, 3, vh), s = pair_field<SP>(ss, 4, vh), t = pair_field<SP>(ss, 5, vh);
-  const SP tmp = pair_field<SP>(ss, 6, vh);
-  auto f32 = [&](int k) { F32F f; f.d = ss->f32 + (size_t)k * cap * 6 * vh; f.vh = vh; return f; };
-  const F32F x32 = f32(0), b32 = f32(1), r32 = f32(2), t32 = f32(3), o32 = f32(4);
-
-  SmallBufs sb = small_layout(ss->small, cap, nbx);
-  SState *sc = sb.sc;
-  int *flags = sb.flags, *counts = sb.counts;
-  D4S *part = sb.part;
-
-  std::vector<double> rr(nrhs), bb(nrhs), prev_rel(nrhs, 1e300);
-  std::vector<SState> hs(cap);
-  std::vector<int> hl, hp, bad(nrhs, 0), hflags(cap, 0);
-  std::vector<double> hscale(cap, 0.0), hun(cap, 0.0);
-  for (int k = 0; k < cap; ++k) hs[k] = SState{};
-  for (int k = 0; k < nrhs; ++k) stats[k] = lqcd_solve_stats{0, LQCD_OK, 0.0, 0, 0};
-  LQCD_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, (size_t)nrhs * g.V * 12 * sizeof(double2), st));
+struct MixedRun {
+  lqcd_ctx *ctx;
+  const double2 *b;
+  double2 *x;
+  int nrhs;
+  lqcd_solver_params p;
+  lqcd_solve_stats *stats;
+  cudaStream_t st;
+  double t0;
+  SloppyState *ss = nullptr;
+  Geom g;
+  int vh = 0, cap = 0, nbx = 0, G = 0, npairs = 0;
+  float kappa = 0.f, k2 = 0.f;
+  double delta = 0.1, floor2 = 4e-12;  // (2e-6)^2: inner FP32 target floor, relative to |b_inner|^2
+  SP r, rhat, pp, v, s, t, tmp;
+  F32F x32, b32, r32, t32, o32;
+  SmallBufs sb;
+  std::vector<double> rr, bb, prev_rel, hscale, hun;
+  std::vector<SState> hs;
+  std::vector<int> hl, hp, bad, hflags, keep_status;
+  int cycle = 0;
   const int max_cycles = 10;
-  bool timed_out = false;
+  bool timed_out = false, done = false, inner = false;
 
-  for (int cycle = 0; cycle <= max_cycles; ++cycle) {
-    // at x = 0 the residual is b itself: only its norm is needed
-    const double2 *r64 = cycle == 0 ? b : ss->r64;
-    rc = fp64_residual_into(ctx, b, cycle == 0 ? nullptr : x, ss->r64, nrhs, rr.data(), bb.data(), st);
+  int init() {
+    int rc = sloppy_alloc(ctx, nrhs);
+    if (rc) return rc;
+    ss = ctx->sloppy;
+    g = ctx->geom;
+    vh = g.Vh;
+    cap = ss->cap;
+    nbx = (vh + ST - 1) / ST;
+    kappa = (float)ctx->kappa;
+    k2 = (float)(ctx->kappa * ctx->kappa);
+    G = num_sms(ctx->device) * tuned_blocks_per_sm(ctx, nrhs, p.precision);
+    npairs = (nrhs + 1) / 2;
+    delta = p.delta > 0 ? p.delta : 0.1;
+    r = pair_field<SP>(ss, 0, vh);
+    rhat = pair_field<SP>(ss, 1, vh);
+    pp = pair_field<SP>(ss, 2, vh);
+    v = pair_field<SP>(ss, 3, vh);
+    s = pair_field<SP>(ss, 4, vh);
+    t = pair_field<SP>(ss, 5, vh);
+    tmp = pair_field<SP>(ss, 6, vh);
+    auto f32 = [&](int k) { F32F f; f.d = ss->f32 + (size_t)k * cap * 6 * vh; f.vh = vh; return f; };
+    x32 = f32(0); b32 = f32(1); r32 = f32(2); t32 = f32(3); o32 = f32(4);
+    sb = small_layout(ss->small, cap, nbx);
+    rr.assign(nrhs, 0.0);
+    bb.assign(nrhs, 0.0);
+    prev_rel.assign(nrhs, 1e300);
+    hscale.assign(cap, 0.0);
+    hun.assign(cap, 0.0);
+    hs.assign(cap, SState{});
+    bad.assign(nrhs, 0);
+    hflags.assign(cap, 0);
+    keep_status.assign(nrhs, 0);
+    for (int k = 0; k < nrhs; ++k) stats[k] = lqcd_solve_stats{0, LQCD_OK, 0.0, 0, 0};
+    LQCD_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, (size_t)nrhs * g.V * 12 * sizeof(double2), st));
+    return LQCD_OK;
+  }
+
+  // key of the captured iteration graph: everything its kernels capture by value
+  std::vector<double> graph_key() const {
+    return {(double)nrhs, (double)p.precision, (double)p.max_iter, delta, (double)kappa, (double)G,
+            (double)(uintptr_t)ss->sd, (double)(uintptr_t)ss->f32, (double)(uintptr_t)ss->small,
+            (double)(uintptr_t)ctx->U16, (double)(uintptr_t)ctx->U32};
+  }
+
+  int cycle_start() {
+    const double2 *r64 = cycle == 0 ? b : ss->r64;  // at x = 0 the residual is b itself
+    int rc = fp64_residual_into(ctx, b, cycle == 0 ? nullptr : x, ss->r64, nrhs, rr.data(), bb.data(), st);
     if (rc) return rc;
     hl.clear();
     hp.clear();
@@ -1184,91 +1216,257 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
         hflags[k] = FLAG_RU;  // marks the members whose inner source is loaded below
       }
     }
-    if (hl.empty() || timed_out) break;
+    if (hl.empty() || timed_out) {
+      done = true;
+      return LQCD_OK;
+    }
+    int *counts = sb.counts;
     int hc[5] = {0, 0, (int)hl.size(), 0, (int)hp.size()};
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.cyc_list, hl.data(), hl.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.cyc_pairs, hp.data(), hp.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(counts, hc, sizeof(hc), cudaMemcpyHostToDevice, st));
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.scale, hscale.data(), cap * sizeof(double), cudaMemcpyHostToDevice, st));
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.unscale, hun.data(), cap * sizeof(double), cudaMemcpyHostToDevice, st));
-    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sc, hs.data(), cap * sizeof(SState), cudaMemcpyHostToDevice, st));
-    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(flags, hflags.data(), cap * sizeof(int), cudaMemcpyHostToDevice, st));
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.sc, hs.data(), cap * sizeof(SState), cudaMemcpyHostToDevice, st));
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.flags, hflags.data(), cap * sizeof(int), cudaMemcpyHostToDevice, st));
     // inner right-hand side: b32 = scale (r_e + kappa H_eo r_o), o32 = scale r_o
     KL k_cvt64to32<<<G, ST, 0, st>>>(g, 0, r64, b32, sb.scale, sb.cyc_list, counts + 2, nbx);
     KL k_cvt64to32<<<G, ST, 0, st>>>(g, 1, r64, o32, sb.scale, sb.cyc_list, counts + 2, nbx);
-    KL k_hop32<EPI_AXPY><<<G, ST, 0, st>>>(g, 0, L32, o32, b32, b32, b32, 1.f, 0.f, kappa, sb.cyc_list, counts + 2,
-                                           nullptr, nbx);
-    KL k_pair_copy<SP><<<G, ST, 0, st>>>(vh, flags, b32, r, r, false, x32, true, sb.cyc_pairs, counts + 4, part, nbx);
-    KL k_sfin_init<<<(int)hl.size(), 32, 0, st>>>(sc, flags, sb.cyc_list, counts + 2, part, nbx, floor2);
-    KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
+    KL k_hop32<EPI_AXPY><<<G, ST, 0, st>>>(g, 0, ctx->U32, o32, b32, b32, b32, 1.f, 0.f, kappa, sb.cyc_list,
+                                           counts + 2, nullptr, nbx);
+    KL k_pair_copy<SP><<<G, ST, 0, st>>>(vh, sb.flags, b32, r, r, false, x32, true, sb.cyc_pairs, counts + 4, sb.part,
+                                         nbx);
+    KL k_sfin_init<<<(int)hl.size(), 32, 0, st>>>(sb.sc, sb.flags, sb.cyc_list, counts + 2, sb.part, nbx, floor2);
+    KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, sb.flags, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
     LQCD_LAUNCH_CHECK(ctx, "mixed: cycle setup");
-    // ---------------------------------------------------------- inner loop
-    bool any = true;
-    while (any) {
-      for (int it = 0; it < 4; ++it) {
-        KL k_pair_p<SP><<<G, ST, 0, st>>>(vh, sc, r, rhat, pp, v, sb.act_pairs, counts, nbx);
-        ev_begin();
-        KL k_hop_pair<SP, EPI_PLAIN><<<G, ST, 0, st>>>(g, 1, L16, pp, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
-                                                       nullptr, nbx, nrhs, prof);
-        ev_end();
-        ev_begin();
-        KL k_hop_pair<SP, EPI_DOTR><<<G, ST, 0, st>>>(g, 0, L16, tmp, v, pp, rhat, 1.f, -k2, sb.act_pairs, counts,
-                                                      part, nbx, nrhs, prof);
-        ev_end();
-        KL k_sfin_alpha<<<npairs, 64, 0, st>>>(sc, flags, sb.act_pairs, counts, part, nbx, nrhs);
-        KL k_pair_s<SP><<<G, ST, 0, st>>>(vh, sc, r, v, s, sb.act_pairs, counts, nbx);
-        ev_begin();
-        KL k_hop_pair<SP, EPI_PLAIN><<<G, ST, 0, st>>>(g, 1, L16, s, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
-                                                       nullptr, nbx, nrhs, prof);
-        ev_end();
-        ev_begin();
-        KL k_hop_pair<SP, EPI_TS><<<G, ST, 0, st>>>(g, 0, L16, tmp, t, s, s, 1.f, -k2, sb.act_pairs, counts, part,
-                                                    nbx, nrhs, prof);
-        ev_end();
-        KL k_sfin_omega<<<npairs, 64, 0, st>>>(sc, flags, sb.act_pairs, counts, part, nbx, nrhs);
-        KL k_pair_xr<SP><<<G, ST, 0, st>>>(vh, sc, flags, x32, pp, s, t, r, rhat, sb.act_pairs, counts, part, nbx);
-        KL k_sfin_conv<<<npairs, 64, 0, st>>>(sc, flags, sb.act_pairs, counts, part, nbx, nrhs, delta * delta,
-                                              p.max_iter);
-        KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
-        // reliable update in FP32: r32 = b32 - x32 + kappa^2 H_eo H_oe x32
-        KL k_hop32<EPI_PLAIN><<<G, ST, 0, st>>>(g, 1, L32, x32, t32, t32, t32, 0.f, 0.f, 1.f, sb.ru_list, counts + 1,
-                                                nullptr, nbx);
-        KL k_hop32<EPI_RES><<<G, ST, 0, st>>>(g, 0, L32, t32, r32, b32, x32, 1.f, -1.f, k2, sb.ru_list, counts + 1,
-                                              part, nbx);
-        KL k_sfin_ru<<<nrhs, 32, 0, st>>>(sc, flags, sb.ru_list, counts + 1, part, nbx, p.max_iter);
-        KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
-        KL k_pair_copy<SP><<<G, ST, 0, st>>>(vh, flags, r32, r, rhat, true, x32, false, sb.ru_pairs, counts + 3, part,
-                                             nbx);
-        KL k_sfin_ru2<<<nrhs, 32, 0, st>>>(sc, flags, sb.ru_list, counts + 1, part, nbx);
-        KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, flags, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
+    inner = true;
+    return LQCD_OK;
+  }
+
+  // Enqueue k inner iterations on stream q (RHS that finish simply drop out of the lists).
+  void launch_iters(cudaStream_t q, int k) {
+    int *counts = sb.counts;
+    const uint4 *L16 = ctx->U16;
+    const float4 *L32 = ctx->U32;
+    unsigned long long *prof = ctx->prof_on ? ctx->d_prof : nullptr;
+    if (ctx->prof_on) ctx->prof_prec = p.precision;
+    auto ev_begin = [&]() {
+      if (!ctx->prof_on) return;
+      while (ctx->prof_used + 2 > ctx->prof_ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { ctx->prof_on = false; return; }
+        ctx->prof_ev.push_back(e);
       }
-      LQCD_LAUNCH_CHECK(ctx, "mixed: iteration");
-      LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(ss->h_counts, counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-      LQCD_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-      any = ss->h_counts[0] > 0;
-      if (any && p.timeout_ms > 0 && wall_ms() - t0 > p.timeout_ms) {
-        timed_out = true;
-        break;
-      }
+      cudaEventRecord(ctx->prof_ev[ctx->prof_used], q);
+    };
+    auto ev_end = [&]() {
+      if (!ctx->prof_on) return;
+      cudaEventRecord(ctx->prof_ev[ctx->prof_used + 1], q);
+      ctx->prof_used += 2;
+      ctx->prof_hop_launches++;
+    };
+    for (int it = 0; it < k; ++it) {
+      KL k_pair_p<SP><<<G, ST, 0, q>>>(vh, sb.sc, r, rhat, pp, v, sb.act_pairs, counts, nbx);
+      ev_begin();
+      KL k_hop_pair<SP, EPI_PLAIN><<<G, ST, 0, q>>>(g, 1, L16, pp, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
+                                                    nullptr, nbx, nrhs, prof);
+      ev_end();
+      ev_begin();
+      KL k_hop_pair<SP, EPI_DOTR><<<G, ST, 0, q>>>(g, 0, L16, tmp, v, pp, rhat, 1.f, -k2, sb.act_pairs, counts,
+                                                   sb.part, nbx, nrhs, prof);
+      ev_end();
+      KL k_sfin_alpha<<<npairs, 64, 0, q>>>(sb.sc, sb.flags, sb.act_pairs, counts, sb.part, nbx, nrhs);
+      KL k_pair_s<SP><<<G, ST, 0, q>>>(vh, sb.sc, r, v, s, sb.act_pairs, counts, nbx);
+      ev_begin();
+      KL k_hop_pair<SP, EPI_PLAIN><<<G, ST, 0, q>>>(g, 1, L16, s, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
+                                                    nullptr, nbx, nrhs, prof);
+      ev_end();
+      ev_begin();
+      KL k_hop_pair<SP, EPI_TS><<<G, ST, 0, q>>>(g, 0, L16, tmp, t, s, s, 1.f, -k2, sb.act_pairs, counts, sb.part,
+                                                 nbx, nrhs, prof);
+      ev_end();
+      KL k_sfin_omega<<<npairs, 64, 0, q>>>(sb.sc, sb.flags, sb.act_pairs, counts, sb.part, nbx, nrhs);
+      KL k_pair_xr<SP><<<G, ST, 0, q>>>(vh, sb.sc, sb.flags, x32, pp, s, t, r, rhat, sb.act_pairs, counts, sb.part,
+                                        nbx);
+      KL k_sfin_conv<<<npairs, 64, 0, q>>>(sb.sc, sb.flags, sb.act_pairs, counts, sb.part, nbx, nrhs,
+                                           delta * delta, p.max_iter);
+      KL k_build_lists<<<1, 1024, 0, q>>>(nrhs, sb.flags, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
+      // reliable update in FP32: r32 = b32 - x32 + kappa^2 H_eo H_oe x32
+      KL k_hop32<EPI_PLAIN><<<G, ST, 0, q>>>(g, 1, L32, x32, t32, t32, t32, 0.f, 0.f, 1.f, sb.ru_list, counts + 1,
+                                             nullptr, nbx);
+      KL k_hop32<EPI_RES><<<G, ST, 0, q>>>(g, 0, L32, t32, r32, b32, x32, 1.f, -1.f, k2, sb.ru_list, counts + 1,
+                                           sb.part, nbx);
+      KL k_sfin_ru<<<nrhs, 32, 0, q>>>(sb.sc, sb.flags, sb.ru_list, counts + 1, sb.part, nbx, p.max_iter);
+      KL k_build_lists<<<1, 1024, 0, q>>>(nrhs, sb.flags, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
+      KL k_pair_copy<SP><<<G, ST, 0, q>>>(vh, sb.flags, r32, r, rhat, true, x32, false, sb.ru_pairs, counts + 3,
+                                          sb.part, nbx);
+      KL k_sfin_ru2<<<nrhs, 32, 0, q>>>(sb.sc, sb.flags, sb.ru_list, counts + 1, sb.part, nbx);
+      KL k_build_lists<<<1, 1024, 0, q>>>(nrhs, sb.flags, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
     }
+  }
+
+  // enqueue the read-back of the active count (after the iterations on q)
+  int request_count(cudaStream_t q) {
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(ss->h_counts, sb.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, q));
+    return LQCD_OK;
+  }
+
+  // with the stream drained: finish the cycle if no RHS is active any more
+  int poll() {
+    bool any = ss->h_counts[0] > 0;
+    if (any && p.timeout_ms > 0 && wall_ms() - t0 > p.timeout_ms) {
+      timed_out = true;
+      any = false;
+    }
+    if (!any) return cycle_end();
+    return LQCD_OK;
+  }
+
+  int cycle_end() {
+    int *counts = sb.counts;
     // odd half of the correction: e_o = o32 + kappa H_oe x32; x += |r| e
-    KL k_hop32<EPI_AXPY><<<G, ST, 0, st>>>(g, 1, L32, x32, o32, o32, o32, 1.f, 0.f, kappa, sb.cyc_list, counts + 2,
-                                           nullptr, nbx);
+    KL k_hop32<EPI_AXPY><<<G, ST, 0, st>>>(g, 1, ctx->U32, x32, o32, o32, o32, 1.f, 0.f, kappa, sb.cyc_list,
+                                           counts + 2, nullptr, nbx);
     KL k_accum64<<<G, ST, 0, st>>>(g, 0, x32, x, sb.unscale, sb.cyc_list, counts + 2, nbx);
     KL k_accum64<<<G, ST, 0, st>>>(g, 1, o32, x, sb.unscale, sb.cyc_list, counts + 2, nbx);
     LQCD_LAUNCH_CHECK(ctx, "mixed: correction");
-    std::vector<int> keep_status(nrhs);
     for (int k = 0; k < nrhs; ++k) keep_status[k] = hs[k].status;
-    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(hs.data(), sc, cap * sizeof(SState), cudaMemcpyDeviceToHost, st));
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(hs.data(), sb.sc, cap * sizeof(SState), cudaMemcpyDeviceToHost, st));
     LQCD_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     for (int k = 0; k < nrhs; ++k)
       if (!std::binary_search(hl.begin(), hl.end(), k)) hs[k].status = keep_status[k];
+    inner = false;
+    ++cycle;
+    return LQCD_OK;
+  }
+};
+
+// capture `body(stream)` into an executable graph on stream st
+template <class F>
+static cudaError_t capture_graph(cudaStream_t st, F body, cudaGraphExec_t *exec) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  body(st);
+  e = cudaStreamEndCapture(st, &graph);
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(exec, graph, 0);
+  cudaGraphDestroy(graph);
+  return e;
+}
+
+constexpr int ITERS_PER_POLL = 4;
+
+// Single lattice: the four-iteration sequence is captured once into a CUDA
+// graph and replayed (launched directly while profiling, so every hop launch
+// gets its own events).
+template <class SP>
+static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const lqcd_solver_params &p,
+                       lqcd_solve_stats *stats, cudaStream_t st, double t0) {
+  MixedRun<SP> run{ctx, b, x, nrhs, p, stats, st, t0};
+  int rc = run.init();
+  if (rc) return rc;
+  SloppyState *ss = ctx->sloppy;
+  // the legacy default stream cannot be captured: launch directly there
+  const bool use_graph = !ctx->prof_on && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+  while (!run.done) {
+    if (!run.inner) {
+      rc = run.cycle_start();
+      if (rc) return rc;
+      continue;
+    }
+    if (use_graph) {
+      std::vector<double> key = run.graph_key();
+      if (!ss->graph || ss->graph_key != key) {
+        if (ss->graph) cudaGraphExecDestroy(ss->graph);
+        ss->graph = nullptr;
+        cudaError_t e = capture_graph(st, [&](cudaStream_t q) { run.launch_iters(q, ITERS_PER_POLL); }, &ss->graph);
+        if (e != cudaSuccess) return cuda_error(ctx, e, "mixed: capture of the iteration graph");
+        ss->graph_key = key;
+      }
+      LQCD_CUDA_TRY(ctx, cudaGraphLaunch(ss->graph, st));
+    } else {
+      run.launch_iters(st, ITERS_PER_POLL);
+      LQCD_LAUNCH_CHECK(ctx, "mixed: iteration");
+    }
+    rc = run.request_count(st);
+    if (rc) return rc;
+    LQCD_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    rc = run.poll();
+    if (rc) return rc;
+  }
+  return LQCD_OK;
+}
+
+// Uneven batch: all lattices' iterations in one captured graph (one branch
+// per lattice); one graph launch advances every lattice by four iterations.
+template <class SP>
+static int mixed_batch(std::vector<lqcd_ctx *> &ctxs, std::vector<const double2 *> &bs, std::vector<double2 *> &xs,
+                       std::vector<int> &ns, const lqcd_solver_params &p, std::vector<lqcd_solve_stats *> &stats,
+                       cudaStream_t st, std::vector<cudaStream_t> &side, cudaGraphExec_t *gexec,
+                       std::vector<double> *gkey) {
+  const size_t nl = ctxs.size();
+  const double t0 = wall_ms();
+  std::vector<MixedRun<SP>> runs;
+  runs.reserve(nl);
+  for (size_t l = 0; l < nl; ++l) runs.push_back(MixedRun<SP>{ctxs[l], bs[l], xs[l], ns[l], p, stats[l], st, t0});
+  for (auto &r : runs) {
+    int rc = r.init();
+    if (rc) return rc;
+  }
+  for (;;) {
+    bool any = false;
+    for (auto &r : runs) {
+      while (!r.done && !r.inner) {
+        int rc = r.cycle_start();
+        if (rc) return rc;
+      }
+      any = any || !r.done;
+    }
+    if (!any) break;
+    std::vector<double> key;
+    for (auto &r : runs) {
+      std::vector<double> k = r.graph_key();
+      key.insert(key.end(), k.begin(), k.end());
+    }
+    if (!*gexec || *gkey != key) {
+      if (*gexec) cudaGraphExecDestroy(*gexec);
+      *gexec = nullptr;
+      std::vector<cudaEvent_t> ev(nl + 1);
+      for (auto &e : ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+      cudaError_t e = capture_graph(st, [&](cudaStream_t q) {
+        cudaEventRecord(ev[nl], q);
+        for (size_t l = 0; l < nl; ++l) {
+          cudaStreamWaitEvent(side[l], ev[nl], 0);
+          runs[l].launch_iters(side[l], ITERS_PER_POLL);
+          cudaEventRecord(ev[l], side[l]);
+          cudaStreamWaitEvent(q, ev[l], 0);
+        }
+      }, gexec);
+      for (auto &ee : ev) cudaEventDestroy(ee);
+      if (e != cudaSuccess) return cuda_error(ctxs[0], e, "batch: capture of the iteration graph");
+      *gkey = key;
+    }
+    LQCD_CUDA_TRY(ctxs[0], cudaGraphLaunch(*gexec, st));
+    for (auto &r : runs)
+      if (!r.done) {
+        int rc = r.request_count(st);
+        if (rc) return rc;
+      }
+    LQCD_CUDA_TRY(ctxs[0], cudaStreamSynchronize(st));
+    for (auto &r : runs)
+      if (!r.done && r.inner) {
+        int rc = r.poll();
+        if (rc) return rc;
+      }
   }
   return LQCD_OK;
 }
 
 int mixed_solve(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const lqcd_solver_params &p,
                 lqcd_solve_stats *stats, cudaStream_t st) {
+  if (p.solver != LQCD_SOLVER_BICGSTAB)
+    return set_error(ctx, LQCD_ERR_INVALID, "the CG solver is available with LQCD_PREC_FP64 only");
   if (!ctx->gauge_su3)
     return set_error(ctx, LQCD_ERR_INVALID,
                      "mixed precision needs SU(3) links (reconstruct-12); this gauge field was set with "
@@ -1292,3 +1490,186 @@ int mixed_solve(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const lqc
 }
 
 }  // namespace lqcd
+
+// ================================================================ batch ABI
+struct lqcd_batch {
+  struct Entry {
+    lqcd_ctx *ctx;
+    const double2 *b;
+    double2 *x;
+    int nrhs;
+  };
+  std::vector<Entry> entries;
+  std::vector<cudaStream_t> side;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<double> graph_key;
+  std::string err;
+};
+
+using namespace lqcd;
+
+extern "C" {
+
+int lqcd_batch_create(lqcd_batch **out) {
+  if (!out) return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_batch_create: null argument");
+  *out = new lqcd_batch();
+  return LQCD_OK;
+}
+
+int lqcd_batch_destroy(lqcd_batch *batch) {
+  if (!batch) return LQCD_OK;
+  if (batch->graph) cudaGraphExecDestroy(batch->graph);
+  for (cudaStream_t s : batch->side) cudaStreamDestroy(s);
+  delete batch;
+  return LQCD_OK;
+}
+
+int lqcd_batch_add(lqcd_batch *batch, lqcd_ctx *ctx, const double *b, double *x, int nrhs) {
+  if (!batch || !ctx || nrhs <= 0 || !b || !x) return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_batch_add: bad argument");
+  if (!is_device_ptr(b) || !is_device_ptr(x))
+    return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_batch_add: b and x must be device memory");
+  for (auto &e : batch->entries)
+    if (e.ctx == ctx) return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_batch_add: one entry per context");
+  if (!batch->entries.empty() && batch->entries[0].ctx->device != ctx->device)
+    return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_batch_add: all lattices must be on one device");
+  batch->entries.push_back({ctx, (const double2 *)b, (double2 *)x, nrhs});
+  return LQCD_OK;
+}
+
+int lqcd_batch_run(lqcd_batch *batch, const lqcd_solver_params *params, lqcd_solve_stats *stats,
+                   lqcd_stream_t stream) {
+  if (!batch || !params || !stats) return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_batch_run: null argument");
+  if (batch->entries.empty()) return LQCD_OK;
+  const lqcd_solver_params &p = *params;
+  if (!(p.tol > 0.0) || p.max_iter <= 0 || p.precision < LQCD_PREC_FP64 || p.precision > LQCD_PREC_MIXED_BF16)
+    return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_batch_run: bad solver parameters");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(batch->entries[0].ctx->device);
+  std::vector<lqcd_ctx *> ctxs;
+  std::vector<const double2 *> bs;
+  std::vector<double2 *> xs;
+  std::vector<int> ns;
+  std::vector<lqcd_solve_stats *> sts;
+  size_t off = 0;
+  for (auto &e : batch->entries) {
+    if (!e.ctx->have_gauge) return set_error(e.ctx, LQCD_ERR_NO_GAUGE, "lqcd_batch_run: no gauge field");
+    ctxs.push_back(e.ctx);
+    bs.push_back(e.b);
+    xs.push_back(e.x);
+    ns.push_back(e.nrhs);
+    sts.push_back(stats + off);
+    off += e.nrhs;
+  }
+  int rc = LQCD_OK;
+  if (p.precision == LQCD_PREC_FP64) {
+    for (size_t l = 0; l < ctxs.size() && rc == LQCD_OK; ++l) {
+      rc = fp64_solve(ctxs[l], bs[l], xs[l], ns[l], p, sts[l], st);
+      if (rc == LQCD_ERR_NOT_CONVERGED || rc == LQCD_ERR_NONFINITE || rc == LQCD_ERR_TIMEOUT ||
+          rc == LQCD_ERR_BREAKDOWN)
+        rc = LQCD_OK;  // per-RHS statuses are reported in stats
+    }
+  } else {
+    if (p.solver != LQCD_SOLVER_BICGSTAB)
+      return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_batch_run: CG is available with LQCD_PREC_FP64 only");
+    for (auto *c : ctxs)
+      if (!c->gauge_su3)
+        return set_error(c, LQCD_ERR_INVALID, "lqcd_batch_run: mixed precision needs SU(3) links");
+    if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread)
+      return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_batch_run: pass a created stream (the graph is captured on it)");
+    while (batch->side.size() < ctxs.size()) {
+      cudaStream_t s;
+      LQCD_CUDA_TRY(ctxs[0], cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+      batch->side.push_back(s);
+    }
+    rc = p.precision == LQCD_PREC_MIXED_FP16
+             ? mixed_batch<F16P>(ctxs, bs, xs, ns, p, sts, st, batch->side, &batch->graph, &batch->graph_key)
+             : mixed_batch<BF16P>(ctxs, bs, xs, ns, p, sts, st, batch->side, &batch->graph, &batch->graph_key);
+  }
+  if (rc) {
+    set_error(nullptr, rc, "lqcd_batch_run: %s", lqcd_last_error(ctxs[0]));
+    return rc;
+  }
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(nullptr, e, "lqcd_batch_run: sync");
+  int worst = LQCD_OK;
+  for (size_t k = 0; k < off; ++k)
+    if (worst == LQCD_OK && stats[k].status != LQCD_OK) worst = stats[k].status;
+  return worst;
+}
+
+}  // extern "C"
+
+// ================================================================ autotuner
+namespace lqcd {
+
+template <class SP>
+static int autotune_hop(lqcd_ctx *ctx, int nrhs, int precision, int *best) {
+  int rc = sloppy_alloc(ctx, nrhs);
+  if (rc) return rc;
+  SloppyState *ss = ctx->sloppy;
+  const Geom &g = ctx->geom;
+  const int vh = g.Vh, cap = ss->cap, nbx = (vh + ST - 1) / ST, npairs = (nrhs + 1) / 2;
+  SmallBufs sb = small_layout(ss->small, cap, nbx);
+  SP in = pair_field<SP>(ss, 2, vh), out = pair_field<SP>(ss, 6, vh);
+  // zero data: timing does not depend on the values
+  LQCD_CUDA_TRY(ctx, cudaMemset(ss->sd, 0, 7 * (size_t)(cap / 2) * 6 * vh * sizeof(uint4)));
+  LQCD_CUDA_TRY(ctx, cudaMemset(ss->sn, 0, 7 * (size_t)(cap / 2) * vh * sizeof(float2)));
+  std::vector<int> pl(npairs);
+  for (int k = 0; k < npairs; ++k) pl[k] = k;
+  LQCD_CUDA_TRY(ctx, cudaMemcpy(sb.act_pairs, pl.data(), npairs * sizeof(int), cudaMemcpyHostToDevice));
+  LQCD_CUDA_TRY(ctx, cudaMemcpy(sb.counts, &npairs, sizeof(int), cudaMemcpyHostToDevice));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int cand[4] = {2, 4, 8, 16};
+  float best_ms = 1e30f;
+  int best_b = 8;
+  const int nsm = num_sms(ctx->device);
+  for (int c : cand) {
+    const int G = nsm * c;
+    for (int rep = 0; rep < 2; ++rep)  // warm-up
+      KL k_hop_pair<SP, EPI_PLAIN><<<G, ST>>>(g, 1, ctx->U16, in, out, out, out, 0.f, 1.f, sb.act_pairs, sb.counts,
+                                              nullptr, nbx, nrhs, nullptr);
+    cudaEventRecord(e0);
+    for (int rep = 0; rep < 5; ++rep)
+      KL k_hop_pair<SP, EPI_PLAIN><<<G, ST>>>(g, 1, ctx->U16, in, out, out, out, 0.f, 1.f, sb.act_pairs, sb.counts,
+                                              nullptr, nbx, nrhs, nullptr);
+    cudaEventRecord(e1);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cuda_error(ctx, e, "lqcd_autotune");
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_b = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  long long key = (long long)nrhs * 8 + precision;
+  bool found = false;
+  for (auto &kv : ctx->tuned)
+    if (kv.first == key) {
+      kv.second = best_b;
+      found = true;
+    }
+  if (!found) ctx->tuned.push_back({key, best_b});
+  if (best) *best = best_b;
+  return LQCD_OK;
+}
+
+}  // namespace lqcd
+
+extern "C" int lqcd_autotune(lqcd_ctx *ctx, int nrhs, int precision, int *best_blocks_per_sm) {
+  if (!ctx || nrhs <= 0 || nrhs > 4096) return set_error(ctx, LQCD_ERR_INVALID, "lqcd_autotune: bad argument");
+  if (!ctx->have_gauge || !ctx->gauge_su3) return set_error(ctx, LQCD_ERR_NO_GAUGE, "lqcd_autotune: needs an SU(3) gauge field");
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (precision == LQCD_PREC_MIXED_FP16) return autotune_hop<F16P>(ctx, nrhs, precision, best_blocks_per_sm);
+  if (precision == LQCD_PREC_MIXED_BF16) return autotune_hop<BF16P>(ctx, nrhs, precision, best_blocks_per_sm);
+  return set_error(ctx, LQCD_ERR_INVALID, "lqcd_autotune: only the mixed-precision paths are tuned");
+}

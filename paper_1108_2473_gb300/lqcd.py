@@ -70,6 +70,17 @@ class lqcd_profile(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class lqcd_stochastic_params(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("first_noise", ctypes.c_uint64), ("dilution", ctypes.c_int),
+                ("n_lp", ctypes.c_int), ("n_hp", ctypes.c_int), ("tol_lp", ctypes.c_double),
+                ("tol_hp", ctypes.c_double), ("chunk", ctypes.c_int)]
+
+
+def stochastic_params(seed, n_lp, n_hp=0, tol_lp=1e-10, tol_hp=1e-10, dilution=LQCD_DILUTE_TSC, first_noise=0,
+                      chunk=0):
+    return lqcd_stochastic_params(seed, first_noise, dilution, n_lp, n_hp, tol_lp, tol_hp, chunk)
+
+
 def solver_params(tol=1e-10, max_iter=20000, precision=LQCD_PREC_FP64, solver=LQCD_SOLVER_BICGSTAB, delta=0.1,
                   rhs_block=0, timeout_ms=0.0):
     return lqcd_solver_params(tol, max_iter, precision, solver, delta, rhs_block, timeout_ms)
@@ -94,6 +105,13 @@ _SIGS = {
     "lqcd_point_sources": (_i, [_vp, ctypes.POINTER(ctypes.c_int64), _i, _vp, _vp]),
     "lqcd_noise_generate": (_i, [_u64, _u64, _u64, ctypes.POINTER(_i), _i, _i, _i, _vp, _vp]),
     "lqcd_loops_batch": (_i, [_vp, _vp, _vp, _i, _d, _vp, _vp, _vp]),
+    "lqcd_batch_create": (_i, [ctypes.POINTER(_vp)]),
+    "lqcd_batch_add": (_i, [_vp, _vp, _vp, _vp, _i]),
+    "lqcd_batch_run": (_i, [_vp, ctypes.POINTER(lqcd_solver_params), ctypes.POINTER(lqcd_solve_stats), _vp]),
+    "lqcd_batch_destroy": (_i, [_vp]),
+    "lqcd_autotune": (_i, [_vp, _i, _i, ctypes.POINTER(_i)]),
+    "lqcd_loops_stochastic": (_i, [_vp, ctypes.POINTER(lqcd_stochastic_params), ctypes.POINTER(lqcd_solver_params),
+                                   _vp, _vp, ctypes.POINTER(lqcd_solve_stats), _vp]),
     "lqcd_gradient": (_i, [_vp, _vp, _vp, _i, _vp, _d, ctypes.POINTER(lqcd_solver_params), ctypes.POINTER(_d), _vp,
                            ctypes.POINTER(lqcd_solve_stats), _vp]),
     "lqcd_loops_batch_noalloc": (_i, [ctypes.POINTER(_i), _vp, _vp, _i, _d, _vp, _vp, _vp]),
@@ -272,3 +290,47 @@ def lqcd_gradient(h, src, sol, coef, params, weight=1.0, dU=None):
     if rc in (LQCD_ERR_INVALID, LQCD_ERR_CUDA, LQCD_ERR_NO_GAUGE, LQCD_ERR_OOM):
         raise LqcdError(rc, _err(h))
     return dk.value, rc, [stats[k].as_dict() for k in range(nrhs)]
+
+
+def lqcd_loops_stochastic(h, sparams, solver, per_site=None, per_t=None):
+    """Plain diluted or truncated-solver-method loops, accumulated into per_site / per_t.
+
+    Returns (status, [LP summary, HP summary]); argument and CUDA errors raise.
+    """
+    summ = (lqcd_solve_stats * 2)()
+    st = _stream(per_site) if per_site is not None else _stream(per_t)
+    rc = load().lqcd_loops_stochastic(h, ctypes.byref(sparams), ctypes.byref(solver), _ptr(per_site), _ptr(per_t),
+                                      summ, st)
+    if rc in (LQCD_ERR_INVALID, LQCD_ERR_CUDA, LQCD_ERR_NO_GAUGE, LQCD_ERR_OOM):
+        raise LqcdError(rc, _err(h))
+    return rc, [summ[0].as_dict(), summ[1].as_dict()]
+
+
+def lqcd_batch_create():
+    h = ctypes.c_void_p()
+    _check(load().lqcd_batch_create(ctypes.byref(h)), None)
+    return h
+
+
+def lqcd_batch_add(batch, ctx, b, x):
+    return _check(load().lqcd_batch_add(batch, ctx, _ptr(b), _ptr(x), b.shape[0]), None)
+
+
+def lqcd_batch_run(batch, params, total_rhs, stream=None):
+    """Solve every registered entry; returns (status, [stats dicts in add order])."""
+    stats = (lqcd_solve_stats * max(total_rhs, 1))()
+    st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else _stream()
+    rc = load().lqcd_batch_run(batch, ctypes.byref(params), stats, st)
+    if rc in (LQCD_ERR_INVALID, LQCD_ERR_CUDA, LQCD_ERR_NO_GAUGE, LQCD_ERR_OOM):
+        raise LqcdError(rc, _err(None))
+    return rc, [stats[k].as_dict() for k in range(total_rhs)]
+
+
+def lqcd_batch_destroy(batch):
+    return load().lqcd_batch_destroy(batch)
+
+
+def lqcd_autotune(h, nrhs, precision):
+    best = ctypes.c_int(0)
+    _check(load().lqcd_autotune(h, int(nrhs), int(precision), ctypes.byref(best)), h)
+    return best.value
