@@ -68,7 +68,7 @@ __device__ __forceinline__ double2 dmul(double2 a, double2 b) { return cmul(a, b
 
 // Check unitarity and unit determinant of every link; write the FP32 and FP16
 // reconstruct-12 copies (rows 0 and 1) in parity-split SoA order.
-__global__ void k_pack_gauge(const double2 *__restrict__ U, Geom g, float4 *U32, uint4 *U16, int *flag) {
+__global__ void k_pack_gauge(const double2 *__restrict__ U, Geom g, float4 *U32, uint4 *U16, float4 *Udf, int *flag) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.V * 4) return;
   int s = idx >> 2, mu = idx & 3;
@@ -77,7 +77,13 @@ __global__ void k_pack_gauge(const double2 *__restrict__ U, Geom g, float4 *U32,
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) m[a][b] = u[a * 3 + b];
+    for (int b = 0; b < 3; ++b) {
+      m[a][b] = u[a * 3 + b];
+      // double-float copy for the residual: hi = fl32(v), lo = fl32(v - hi)
+      float hx = (float)m[a][b].x, hy = (float)m[a][b].y;
+      Udf[(size_t)idx * 9 + a * 3 + b] =
+          make_float4(hx, hy, (float)(m[a][b].x - (double)hx), (float)(m[a][b].y - (double)hy));
+    }
   double dev = 0.0;
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) {
@@ -220,6 +226,7 @@ int lqcd_destroy(lqcd_ctx *ctx) {
   cudaFree(ctx->U64);
   cudaFree(ctx->U32);
   cudaFree(ctx->U16);
+  cudaFree(ctx->Udf);
   cudaFree(ctx->d_flag);
   cudaFree(ctx->d_prof);
   for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
@@ -249,6 +256,7 @@ static int set_gauge_impl(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream, 
     LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->U64, n64 * sizeof(double2)));
     LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->U32, (size_t)g.V * 4 * 3 * sizeof(float4)));
     LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->U16, (size_t)g.V * 4 * 3 * sizeof(uint4)));
+    LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->Udf, n64 * sizeof(float4)));
   }
   int st_ = LQCD_OK;
   double2 *stage = (double2 *)workspace(ctx, WS_STAGE_AUX, n64 * sizeof(double2), &st_);
@@ -257,7 +265,7 @@ static int set_gauge_impl(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream, 
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(stage, U, n64 * sizeof(double2), kind, st));
   LQCD_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));
   int threads = 256, blocks = (g.V * 4 + threads - 1) / threads;
-  KL k_pack_gauge<<<blocks, threads, 0, st>>>(stage, g, ctx->U32, ctx->U16, ctx->d_flag);
+  KL k_pack_gauge<<<blocks, threads, 0, st>>>(stage, g, ctx->U32, ctx->U16, ctx->Udf, ctx->d_flag);
   LQCD_LAUNCH_CHECK(ctx, "k_pack_gauge");
   int flag = 0;
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));

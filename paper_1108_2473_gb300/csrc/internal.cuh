@@ -152,6 +152,7 @@ struct lqcd_ctx {
   bool gauge_su3 = false;     // links checked SU(3): reconstruct-12 copies are valid
   double2 *U64 = nullptr;     // canonical [V][4][3][3]
   float4 *U32 = nullptr;      // recon-12 FP32  [2 parity][4 mu][3 float4][Vh]
+  float4 *Udf = nullptr;      // double-float copy  [V][4][3][3] (hi.re, hi.im, lo.re, lo.im)
   uint4 *U16 = nullptr;       // recon-12 FP16, each real twice  [2 parity][4 mu][3 uint4][Vh]
   std::vector<lqcd::DevBuf> ws;  // named workspaces, grow-only
   lqcd::SloppyState *sloppy = nullptr;
@@ -220,6 +221,10 @@ enum WsSlot {
 int launch_hop64(lqcd_ctx *ctx, cudaStream_t st, bool dag, bool in_canon, bool out_canon, int p_out,
                  const double2 *in, size_t in_stride, double2 *out, size_t out_stride, const double2 *A, double cA,
                  const double2 *B, double cB, double cH, const int *active, int nrhs);
+int df_split(lqcd_ctx *ctx, const double2 *in, float4 *out, size_t n, cudaStream_t st);
+int df_join(lqcd_ctx *ctx, const float4 *in, double2 *out, size_t n, cudaStream_t st);
+int df_residual(lqcd_ctx *ctx, const float4 *x, const float4 *b, float2 *r, int nrhs, double *rr, double *bb,
+                cudaStream_t st);
 int fp64_true_residual(lqcd_ctx *ctx, const double2 *b, const double2 *x, int nrhs, double *rr, double *bb,
                        cudaStream_t st);
 int fp64_apply_dirac(lqcd_ctx *ctx, const double2 *in, double2 *out, int nrhs, bool dagger,

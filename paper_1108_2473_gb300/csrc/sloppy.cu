@@ -36,6 +36,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "df.cuh"
 #include "sloppy.cuh"
 
 namespace lqcd {
@@ -774,6 +775,51 @@ __global__ void __launch_bounds__(ST) k_cvt64to32(Geom g, int p, const double2 *
   }
 }
 
+// dst (FP32 parity field) = scale[rhs] * src (canonical FP32 [rhs][V][12]) on parity p
+__global__ void __launch_bounds__(ST) k_cvt32to32(Geom g, int p, const float2 *__restrict__ src, F32F dst,
+                                                  const double *scale, const int *list, const int *count, int nbx) {
+  const int n_items = *count * nbx;
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int rhs = list[w / nbx];
+    const int i = (w % nbx) * ST + threadIdx.x;
+    if (i >= g.Vh) continue;
+    int c[4];
+    coords_of(g, p, i, c);
+    const float2 *q = src + ((size_t)rhs * g.V + site_of(g, c)) * 12;
+    const float sc = (float)scale[rhs];
+    float2 v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = make_float2(q[k].x * sc, q[k].y * sc);
+    dst.store(rhs, i, v);
+  }
+}
+
+// x (double-float canonical) += scale[rhs] * src (FP32 parity field) on parity p
+__global__ void __launch_bounds__(ST) k_accum_df(Geom g, int p, F32F src, float4 *x, const double *scale,
+                                                 const int *list, const int *count, int nbx) {
+  const int n_items = *count * nbx;
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int rhs = list[w / nbx];
+    const int i = (w % nbx) * ST + threadIdx.x;
+    if (i >= g.Vh) continue;
+    int c[4];
+    coords_of(g, p, i, c);
+    float4 *q = x + ((size_t)rhs * g.V + site_of(g, c)) * 12;
+    const double scd = scale[rhs];
+    const float sh = (float)scd;
+    const dfl sc{sh, (float)(scd - (double)sh)};
+    float2 v[12];
+    src.load(rhs, i, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      float4 o = q[k];
+      dfl re = df_norm(dfl{o.x, o.z} + sc * dfl{v[k].x, 0.f});
+      dfl im = df_norm(dfl{o.y, o.w} + sc * dfl{v[k].y, 0.f});
+      q[k] = make_float4(re.h, im.h, re.l, im.l);
+    }
+  }
+}
+
 // x (canonical FP64) += scale[rhs] * src (FP32 parity field) on parity p
 __global__ void __launch_bounds__(ST) k_accum64(Geom g, int p, F32F src, double2 *x, const double *scale,
                                                 const int *list, const int *count, int nbx) {
@@ -996,7 +1042,9 @@ struct SloppyState {
   uint4 *sd = nullptr;     // 7 sloppy pair fields
   float2 *sn = nullptr;    // their FP16 norms
   float4 *f32 = nullptr;   // 5 FP32 fields
-  double2 *r64 = nullptr;  // canonical FP64 residual
+  float4 *xdf = nullptr;   // the iterate, double-float canonical [cap][V][12]
+  float4 *bdf = nullptr;   // the source, double-float canonical
+  float2 *r32 = nullptr;   // residual b - D x, FP32 canonical (seeds the next inner solve)
   char *small = nullptr;
   int *h_counts = nullptr;  // pinned
   // captured graph of four inner iterations, valid while graph_key matches
@@ -1010,7 +1058,9 @@ void sloppy_free(lqcd_ctx *ctx) {
   cudaFree(s->sd);
   cudaFree(s->sn);
   cudaFree(s->f32);
-  cudaFree(s->r64);
+  cudaFree(s->xdf);
+  cudaFree(s->bdf);
+  cudaFree(s->r32);
   cudaFree(s->small);
   if (s->h_counts) cudaFreeHost(s->h_counts);
   if (s->graph) cudaGraphExecDestroy(s->graph);
@@ -1071,9 +1121,12 @@ static int sloppy_alloc(lqcd_ctx *ctx, int nrhs) {
   cudaFree(s->sd);
   cudaFree(s->sn);
   cudaFree(s->f32);
-  cudaFree(s->r64);
+  cudaFree(s->xdf);
+  cudaFree(s->bdf);
+  cudaFree(s->r32);
   cudaFree(s->small);
-  s->sd = nullptr; s->sn = nullptr; s->f32 = nullptr; s->r64 = nullptr; s->small = nullptr;
+  s->sd = nullptr; s->sn = nullptr; s->f32 = nullptr; s->xdf = nullptr; s->bdf = nullptr; s->r32 = nullptr;
+  s->small = nullptr;
   s->cap = 0;
   const Geom &g = ctx->geom;
   const size_t vh = g.Vh, pairs = cap / 2;
@@ -1081,7 +1134,9 @@ static int sloppy_alloc(lqcd_ctx *ctx, int nrhs) {
   LQCD_CUDA_TRY(ctx, cudaMalloc(&s->sd, 7 * pairs * 6 * vh * sizeof(uint4)));
   LQCD_CUDA_TRY(ctx, cudaMalloc(&s->sn, 7 * pairs * vh * sizeof(float2)));
   LQCD_CUDA_TRY(ctx, cudaMalloc(&s->f32, 5 * (size_t)cap * 6 * vh * sizeof(float4)));
-  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->r64, (size_t)cap * g.V * 12 * sizeof(double2)));
+  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->xdf, (size_t)cap * g.V * 12 * sizeof(float4)));
+  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->bdf, (size_t)cap * g.V * 12 * sizeof(float4)));
+  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->r32, (size_t)cap * g.V * 12 * sizeof(float2)));
   LQCD_CUDA_TRY(ctx, cudaMalloc(&s->small, small_layout(nullptr, cap, nbx).size()));
   if (!s->h_counts) LQCD_CUDA_TRY(ctx, cudaMallocHost(&s->h_counts, 16 * sizeof(int)));
   s->cap = cap;
@@ -1172,20 +1227,25 @@ struct MixedRun {
     hflags.assign(cap, 0);
     keep_status.assign(nrhs, 0);
     for (int k = 0; k < nrhs; ++k) stats[k] = lqcd_solve_stats{0, LQCD_OK, 0.0, 0, 0};
-    LQCD_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, (size_t)nrhs * g.V * 12 * sizeof(double2), st));
-    return LQCD_OK;
+    const size_t n = (size_t)nrhs * g.V * 12;
+    LQCD_CUDA_TRY(ctx, cudaMemsetAsync(ss->xdf, 0, n * sizeof(float4), st));
+    return df_split(ctx, b, ss->bdf, n, st);
   }
+
+  // the FP64 solution from the double-float iterate
+  int finish() { return df_join(ctx, ss->xdf, x, (size_t)nrhs * g.V * 12, st); }
 
   // key of the captured iteration graph: everything its kernels capture by value
   std::vector<double> graph_key() const {
     return {(double)nrhs, (double)p.precision, (double)p.max_iter, delta, (double)kappa, (double)G,
             (double)(uintptr_t)ss->sd, (double)(uintptr_t)ss->f32, (double)(uintptr_t)ss->small,
-            (double)(uintptr_t)ctx->U16, (double)(uintptr_t)ctx->U32};
+            (double)(uintptr_t)ctx->U16, (double)(uintptr_t)ctx->U32, (double)(uintptr_t)ss->xdf};
   }
 
   int cycle_start() {
-    const double2 *r64 = cycle == 0 ? b : ss->r64;  // at x = 0 the residual is b itself
-    int rc = fp64_residual_into(ctx, b, cycle == 0 ? nullptr : x, ss->r64, nrhs, rr.data(), bb.data(), st);
+    // at x = 0 the residual is b itself (FP64 norms only); later: double-float b - D x
+    int rc = cycle == 0 ? fp64_residual_into(ctx, b, nullptr, nullptr, nrhs, rr.data(), bb.data(), st)
+                        : df_residual(ctx, ss->xdf, ss->bdf, ss->r32, nrhs, rr.data(), bb.data(), st);
     if (rc) return rc;
     hl.clear();
     hp.clear();
@@ -1230,8 +1290,13 @@ struct MixedRun {
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.sc, hs.data(), cap * sizeof(SState), cudaMemcpyHostToDevice, st));
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.flags, hflags.data(), cap * sizeof(int), cudaMemcpyHostToDevice, st));
     // inner right-hand side: b32 = scale (r_e + kappa H_eo r_o), o32 = scale r_o
-    KL k_cvt64to32<<<G, ST, 0, st>>>(g, 0, r64, b32, sb.scale, sb.cyc_list, counts + 2, nbx);
-    KL k_cvt64to32<<<G, ST, 0, st>>>(g, 1, r64, o32, sb.scale, sb.cyc_list, counts + 2, nbx);
+    if (cycle == 0) {
+      KL k_cvt64to32<<<G, ST, 0, st>>>(g, 0, b, b32, sb.scale, sb.cyc_list, counts + 2, nbx);
+      KL k_cvt64to32<<<G, ST, 0, st>>>(g, 1, b, o32, sb.scale, sb.cyc_list, counts + 2, nbx);
+    } else {
+      KL k_cvt32to32<<<G, ST, 0, st>>>(g, 0, ss->r32, b32, sb.scale, sb.cyc_list, counts + 2, nbx);
+      KL k_cvt32to32<<<G, ST, 0, st>>>(g, 1, ss->r32, o32, sb.scale, sb.cyc_list, counts + 2, nbx);
+    }
     KL k_hop32<EPI_AXPY><<<G, ST, 0, st>>>(g, 0, ctx->U32, o32, b32, b32, b32, 1.f, 0.f, kappa, sb.cyc_list,
                                            counts + 2, nullptr, nbx);
     KL k_pair_copy<SP><<<G, ST, 0, st>>>(vh, sb.flags, b32, r, r, false, x32, true, sb.cyc_pairs, counts + 4, sb.part,
@@ -1327,8 +1392,8 @@ struct MixedRun {
     // odd half of the correction: e_o = o32 + kappa H_oe x32; x += |r| e
     KL k_hop32<EPI_AXPY><<<G, ST, 0, st>>>(g, 1, ctx->U32, x32, o32, o32, o32, 1.f, 0.f, kappa, sb.cyc_list,
                                            counts + 2, nullptr, nbx);
-    KL k_accum64<<<G, ST, 0, st>>>(g, 0, x32, x, sb.unscale, sb.cyc_list, counts + 2, nbx);
-    KL k_accum64<<<G, ST, 0, st>>>(g, 1, o32, x, sb.unscale, sb.cyc_list, counts + 2, nbx);
+    KL k_accum_df<<<G, ST, 0, st>>>(g, 0, x32, ss->xdf, sb.unscale, sb.cyc_list, counts + 2, nbx);
+    KL k_accum_df<<<G, ST, 0, st>>>(g, 1, o32, ss->xdf, sb.unscale, sb.cyc_list, counts + 2, nbx);
     LQCD_LAUNCH_CHECK(ctx, "mixed: correction");
     for (int k = 0; k < nrhs; ++k) keep_status[k] = hs[k].status;
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(hs.data(), sb.sc, cap * sizeof(SState), cudaMemcpyDeviceToHost, st));
@@ -1395,7 +1460,7 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
     rc = run.poll();
     if (rc) return rc;
   }
-  return LQCD_OK;
+  return run.finish();
 }
 
 // Uneven batch: all lattices' iterations in one captured graph (one branch
@@ -1459,6 +1524,10 @@ static int mixed_batch(std::vector<lqcd_ctx *> &ctxs, std::vector<const double2 
         int rc = r.poll();
         if (rc) return rc;
       }
+  }
+  for (auto &r : runs) {
+    int rc = r.finish();
+    if (rc) return rc;
   }
   return LQCD_OK;
 }
