@@ -109,19 +109,24 @@ __global__ void k_pack_gauge(const double2 *__restrict__ U, Geom g, float4 *U32,
     v[2 * k] = (float)m[k / 3][k % 3].x;
     v[2 * k + 1] = (float)m[k / 3][k % 3].y;
   }
-  // FP16 copy for the pair kernels: every real stored twice, (u, u), so one
-  // half2 -> float2 conversion gives the operand both members of a pair use
-  unsigned w[12];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    __half2 hh = __float2half2_rn(v[k]);
+  for (int k = 0; k < 3; ++k)
+    U32[base + (size_t)k * g.Vh] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+  // FP16 copy for the pair kernels: all 18 reals, each stored twice (u, u), so
+  // one half2 -> float2 conversion gives the operand both members of a pair use;
+  // layout [2 parity][4 mu][5][Vh] uint4 (the fifth uint4 half used)
+  unsigned w[20];
+#pragma unroll
+  for (int k = 0; k < 18; ++k) {
+    const double val = (k & 1) ? m[(k / 2) / 3][(k / 2) % 3].y : m[(k / 2) / 3][(k / 2) % 3].x;
+    __half2 hh = __float2half2_rn((float)val);
     w[k] = *reinterpret_cast<unsigned *>(&hh);
   }
+  w[18] = w[19] = 0u;
+  const size_t base16 = ((size_t)(p * 4 + mu) * 5) * g.Vh + i;
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    U32[base + (size_t)k * g.Vh] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-    U16[base + (size_t)k * g.Vh] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
-  }
+  for (int k = 0; k < 5; ++k)
+    U16[base16 + (size_t)k * g.Vh] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
 }
 
 // Plaquette partial sums: one double per block.
@@ -255,7 +260,7 @@ static int set_gauge_impl(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream, 
   if (!ctx->U64) {
     LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->U64, n64 * sizeof(double2)));
     LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->U32, (size_t)g.V * 4 * 3 * sizeof(float4)));
-    LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->U16, (size_t)g.V * 4 * 3 * sizeof(uint4)));
+    LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->U16, (size_t)g.Vh * 2 * 4 * 5 * sizeof(uint4)));
     LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->Udf, n64 * sizeof(float4)));
   }
   int st_ = LQCD_OK;
@@ -429,7 +434,7 @@ int lqcd_profile_end(lqcd_ctx *ctx, lqcd_profile *out) {
     pairs += (double)h[e];
     bytes += (double)h[e] * operands[e] * spinor_bytes;
   }
-  bytes += (double)ctx->prof_hop_launches * ctx->geom.Vh * 8 * 48.0;  // FP16 (u,u) recon-12 links once per launch
+  bytes += (double)ctx->prof_hop_launches * ctx->geom.Vh * 8 * 72.0;  // FP16 (u,u) links, 18 reals, once per launch
   out->launches = lqcd::g_launches.load() - ctx->prof_launch_base;
   out->hop_launches = ctx->prof_hop_launches;
   out->hop_ms = ms;

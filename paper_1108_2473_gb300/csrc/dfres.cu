@@ -66,6 +66,64 @@ __device__ __forceinline__ void hop_dir_df(const Geom &g, const int c[4], int s,
   }
 }
 
+// One output colour row a of the hop for one direction pair, three threads
+// per site (a = 0, 1, 2): the projection is recomputed by each thread, the
+// SU(3) row and the accumulation are the thread's own.
+template <int MU, int SIGMA, bool DAG>
+__device__ __forceinline__ void hop_row_df(const float4 *__restrict__ xs, const float4 *__restrict__ u, int a,
+                                           float sgn, cdf acc[4]) {
+  cdf ps[4][3], h[2][3];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) ps[k / 3][k % 3] = load_cdf(xs + k);
+  spin_project<MU, SIGMA>(ps, h);
+  cdf ur[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) ur[b] = load_cdf(u + (DAG ? b * 3 + a : a * 3 + b));
+  cdf x[2];
+#pragma unroll
+  for (int sp = 0; sp < 2; ++sp) {
+    cdf t = DAG ? cmulc(ur[0], h[sp][0]) : cmul(ur[0], h[sp][0]);
+#pragma unroll
+    for (int b = 1; b < 3; ++b) t = cadd(t, DAG ? cmulc(ur[b], h[sp][b]) : cmul(ur[b], h[sp][b]));
+    x[sp] = sgn < 0.f ? cdf{-t.x, -t.y} : t;
+  }
+  // spin reconstruction of spin_accum for colour a
+  acc[0] = cadd(acc[0], x[0]);
+  acc[1] = cadd(acc[1], x[1]);
+  if (MU == 0) {
+    acc[2] = caddi(acc[2], x[1], -SIGMA);
+    acc[3] = caddi(acc[3], x[0], -SIGMA);
+  } else if (MU == 1) {
+    acc[2] = SIGMA > 0 ? cadd(acc[2], x[1]) : csub(acc[2], x[1]);
+    acc[3] = SIGMA > 0 ? csub(acc[3], x[0]) : cadd(acc[3], x[0]);
+  } else if (MU == 2) {
+    acc[2] = caddi(acc[2], x[0], -SIGMA);
+    acc[3] = caddi(acc[3], x[1], SIGMA);
+  } else {
+    acc[2] = SIGMA > 0 ? cadd(acc[2], x[0]) : csub(acc[2], x[0]);
+    acc[3] = SIGMA > 0 ? cadd(acc[3], x[1]) : csub(acc[3], x[1]);
+  }
+}
+
+template <int MU>
+__device__ __forceinline__ void hop_dir_df3(const Geom &g, const int c[4], int s, int a, const float4 *__restrict__ x,
+                                            const float4 *__restrict__ U, cdf acc[4]) {
+  {
+    int cn[4] = {c[0], c[1], c[2], c[3]};
+    cn[MU] = (c[MU] + 1 == g.L[MU]) ? 0 : c[MU] + 1;
+    const int sn = site_of(g, cn);
+    const float sgn = (MU == 3 && c[3] == g.L[3] - 1) ? -1.f : 1.f;
+    hop_row_df<MU, -1, false>(x + (size_t)sn * 12, U + ((size_t)s * 4 + MU) * 9, a, sgn, acc);
+  }
+  {
+    int cn[4] = {c[0], c[1], c[2], c[3]};
+    cn[MU] = (c[MU] == 0) ? g.L[MU] - 1 : c[MU] - 1;
+    const int sn = site_of(g, cn);
+    const float sgn = (MU == 3 && c[3] == 0) ? -1.f : 1.f;
+    hop_row_df<MU, +1, true>(x + (size_t)sn * 12, U + ((size_t)sn * 4 + MU) * 9, a, sgn, acc);
+  }
+}
+
 struct D4R {
   double a, b, c, d;
 };
@@ -113,6 +171,64 @@ __global__ void __launch_bounds__(128) k_resid_df(Geom g, int p_out, const float
   sh[1][threadIdx.x] = bn;
   __syncthreads();
   for (int w = 64; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    part[(size_t)rhs * 2 * gridDim.x + (size_t)p_out * gridDim.x + blockIdx.x] = D4R{0.0, 0.0, sh[0][0], sh[1][0]};
+}
+
+// Three threads per site (one per output colour): r = b - x + kappa H x at the
+// sites of parity p_out; partials as k_resid_df.
+constexpr int DF3_SITES = 64;
+__global__ void __launch_bounds__(3 * DF3_SITES, 4) k_resid_df3(Geom g, int p_out, const float4 *__restrict__ U,
+                                                              const float4 *__restrict__ x,
+                                                              const float4 *__restrict__ b, float2 *r, float kh,
+                                                              float kl, D4R *part) {
+  const int i = blockIdx.x * DF3_SITES + threadIdx.x / 3;
+  const int a = threadIdx.x % 3;
+  const int rhs = blockIdx.y;
+  const size_t stride = (size_t)g.V * 12;
+  float rn = 0.f, bn = 0.f;
+  if (i < g.Vh) {
+    int c[4];
+    coords_of(g, p_out, i, c);
+    const int s = site_of(g, c);
+    cdf acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = cdf{dfl{0.f, 0.f}, dfl{0.f, 0.f}};
+    const float4 *xr = x + (size_t)rhs * stride;
+    hop_dir_df3<0>(g, c, s, a, xr, U, acc);
+    hop_dir_df3<1>(g, c, s, a, xr, U, acc);
+    hop_dir_df3<2>(g, c, s, a, xr, U, acc);
+    hop_dir_df3<3>(g, c, s, a, xr, U, acc);
+    const dfl kd{kh, kl};
+    const size_t o = (size_t)rhs * stride + (size_t)s * 12;
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+      const int k = sp * 3 + a;
+      const cdf bk = load_cdf(b + o + k), xk = load_cdf(xr + (size_t)s * 12 + k);
+      const dfl re = df_norm((bk.x - xk.x) + kd * df_norm(acc[sp].x));
+      const dfl im = df_norm((bk.y - xk.y) + kd * df_norm(acc[sp].y));
+      const float2 v = make_float2(__fadd_rn(re.h, re.l), __fadd_rn(im.h, im.l));
+      r[o + k] = v;
+      rn = fmaf(v.x, v.x, fmaf(v.y, v.y, rn));
+      bn = fmaf(bk.x.h, bk.x.h, fmaf(bk.y.h, bk.y.h, bn));
+    }
+  }
+  __shared__ double sh[2][3 * DF3_SITES];
+  sh[0][threadIdx.x] = rn;
+  sh[1][threadIdx.x] = bn;
+  __syncthreads();
+  if (threadIdx.x < 64) {  // fold 192 -> 64, then a tree
+    sh[0][threadIdx.x] += sh[0][threadIdx.x + 64] + sh[0][threadIdx.x + 128];
+    sh[1][threadIdx.x] += sh[1][threadIdx.x + 64] + sh[1][threadIdx.x + 128];
+  }
+  __syncthreads();
+  for (int w = 32; w > 0; w >>= 1) {
     if (threadIdx.x < w) {
       sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
       sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
@@ -176,7 +292,7 @@ int df_join(lqcd_ctx *ctx, const float4 *in, double2 *out, size_t n, cudaStream_
 int df_residual(lqcd_ctx *ctx, const float4 *x, const float4 *b, float2 *r, int nrhs, double *rr, double *bb,
                 cudaStream_t st) {
   const Geom &g = ctx->geom;
-  const int nblk = (g.Vh + 127) / 128;
+  const int nblk = (g.Vh + DF3_SITES - 1) / DF3_SITES;
   int rc = LQCD_OK;
   Carver sizing(nullptr);
   sizing.take<D4R>((size_t)nrhs * 2 * nblk);
@@ -189,8 +305,8 @@ int df_residual(lqcd_ctx *ctx, const float4 *x, const float4 *b, float2 *r, int 
   double *d_bb = d_rr + nrhs;
   const float kh = (float)ctx->kappa, kl = (float)(ctx->kappa - (double)kh);
   for (int p = 0; p < 2; ++p) {
-    KL k_resid_df<<<dim3(nblk, nrhs), 128, 0, st>>>(g, p, ctx->Udf, x, b, r, kh, kl, part);
-    LQCD_LAUNCH_CHECK(ctx, "k_resid_df");
+    KL k_resid_df3<<<dim3(nblk, nrhs), 3 * DF3_SITES, 0, st>>>(g, p, ctx->Udf, x, b, r, kh, kl, part);
+    LQCD_LAUNCH_CHECK(ctx, "k_resid_df3");
   }
   KL k_df_fin<<<nrhs, 32, 0, st>>>(part, 2 * nblk, d_rr, d_bb);
   LQCD_LAUNCH_CHECK(ctx, "k_df_fin");

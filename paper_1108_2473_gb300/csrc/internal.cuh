@@ -153,7 +153,7 @@ struct lqcd_ctx {
   double2 *U64 = nullptr;     // canonical [V][4][3][3]
   float4 *U32 = nullptr;      // recon-12 FP32  [2 parity][4 mu][3 float4][Vh]
   float4 *Udf = nullptr;      // double-float copy  [V][4][3][3] (hi.re, hi.im, lo.re, lo.im)
-  uint4 *U16 = nullptr;       // recon-12 FP16, each real twice  [2 parity][4 mu][3 uint4][Vh]
+  uint4 *U16 = nullptr;       // FP16, all 18 reals, each twice  [2 parity][4 mu][5 uint4][Vh]
   std::vector<lqcd::DevBuf> ws;  // named workspaces, grow-only
   lqcd::SloppyState *sloppy = nullptr;
   std::string err;

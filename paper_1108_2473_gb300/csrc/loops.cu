@@ -54,16 +54,26 @@ __global__ void __launch_bounds__(LOOP_THREADS) k_loops(Geom g, const double2 *_
         ea[k] = a[k];
         eb[k] = b[k];
       }
+      // The six Gammas use three spin permutations (identity; 3-a; a+2 mod 4):
+      // colour dot products P[perm][alpha] = sum_c conj(src[alpha][c]) sol[perm(alpha)][c]
+      // once, then each Gamma is a signed / i-rotated sum of four of them.
+      double2 P[3][4];
 #pragma unroll
-      for (int gi = 0; gi < 6; ++gi) {
-        double2 sum = make_double2(0.0, 0.0);
+      for (int q = 0; q < 3; ++q)
 #pragma unroll
         for (int al = 0; al < 4; ++al) {
-          const int be = gamma_col(gi, al);
-          const int ph = gamma_ph(gi, al);
-#pragma unroll
-          for (int c = 0; c < 3; ++c) sum = cadd(sum, cmulc(ea[al * 3 + c], gamma_phase(ph, eb[be * 3 + c])));
+          const int be = q == 0 ? al : (q == 1 ? 3 - al : (al + 2) & 3);
+          double2 d = cmulc(ea[al * 3], eb[be * 3]);
+          d = cadd(d, cmulc(ea[al * 3 + 1], eb[be * 3 + 1]));
+          d = cadd(d, cmulc(ea[al * 3 + 2], eb[be * 3 + 2]));
+          P[q][al] = d;
         }
+#pragma unroll
+      for (int gi = 0; gi < 6; ++gi) {
+        const int q = gi < 2 ? 0 : (gi < 4 ? 1 : 2);
+        double2 sum = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int al = 0; al < 4; ++al) sum = cadd(sum, gamma_phase(gamma_ph(gi, al), P[q][al]));
         acc[gi] = cadd(acc[gi], sum);
       }
     }

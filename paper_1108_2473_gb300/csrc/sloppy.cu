@@ -87,7 +87,7 @@ __device__ __forceinline__ void F32F::store(int r, int i, const float2 v[12]) co
 }
 
 // ============================================================ pair fields
-// raw (unscaled) pairs and the norm pair (1, 1 for BF16)
+// raw (unscaled) pairs and the norm pair that scales them (1, 1 for BF16)
 __device__ __forceinline__ void load_raw(const F16P &f, int P, int i, float2 v[24], float2 &nrm) {
   const uint4 *p = f.d + (size_t)P * 6 * f.vh + i;
 #pragma unroll
@@ -354,26 +354,17 @@ __global__ void __launch_bounds__(ST) k_hop32(Geom g, int p_out, const float4 *l
 }
 
 // ====================================================== pair hopping term
-// FP16 link for both members: rows 0-1 from memory as (u, u) pairs, row 2 =
-// (row0 x row1)^* rebuilt with packed arithmetic.
+// FP16 link for both members: all nine entries from memory as (u, u) pairs,
+// layout [2 parity][4 mu][5][Vh] uint4 (the fifth uint4 holds entry (2,2) only).
 __device__ __forceinline__ void load_link_pair(const uint4 *U, int p, int mu, int i, int vh, CP u[3][3]) {
-  size_t base = ((size_t)(p * 4 + mu) * 3) * vh + i;
-  uint4 q0 = U[base], q1 = U[base + vh], q2 = U[base + 2 * (size_t)vh];
-  u[0][0] = CP{h2f(q0.x), h2f(q0.y)};
-  u[0][1] = CP{h2f(q0.z), h2f(q0.w)};
-  u[0][2] = CP{h2f(q1.x), h2f(q1.y)};
-  u[1][0] = CP{h2f(q1.z), h2f(q1.w)};
-  u[1][1] = CP{h2f(q2.x), h2f(q2.y)};
-  u[1][2] = CP{h2f(q2.z), h2f(q2.w)};
+  const size_t base = ((size_t)(p * 4 + mu) * 5) * vh + i;
+  uint4 q[5];
 #pragma unroll
-  for (int j = 0; j < 3; ++j) {
-    const int k = (j + 1) % 3, l = (j + 2) % 3;
-    const CP &a = u[0][k], &b = u[1][l], &c = u[0][l], &d = u[1][k];
-    // (a b - c d)^*:  re = [a.re b.re + c.im d.im] - [a.im b.im + c.re d.re]
-    //                 im = [c.re d.im + c.im d.re] - [a.re b.im + a.im b.re]
-    u[2][j].re = S2(F2(a.re, b.re, M2(c.im, d.im)), F2(a.im, b.im, M2(c.re, d.re)));
-    u[2][j].im = S2(F2(c.re, d.im, M2(c.im, d.re)), F2(a.re, b.im, M2(a.im, b.re)));
-  }
+  for (int k = 0; k < 5; ++k) q[k] = U[base + (size_t)k * vh];
+  const unsigned w[18] = {q[0].x, q[0].y, q[0].z, q[0].w, q[1].x, q[1].y, q[1].z, q[1].w, q[2].x,
+                          q[2].y, q[2].z, q[2].w, q[3].x, q[3].y, q[3].z, q[3].w, q[4].x, q[4].y};
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u[k / 3][k % 3] = CP{h2f(w[2 * k]), h2f(w[2 * k + 1])};
 }
 
 // a + s i b and a + s b on pairs
@@ -387,7 +378,7 @@ template <int S> __device__ __forceinline__ CP cp_addpm(const CP &a, const CP &b
 // Spin projection (1 + SIGMA gamma_mu) of the neighbour spinor, as in
 // spin_project (internal.cuh) but on pairs; then the norm pair scales h.
 template <int MU, int SIGMA>
-__device__ __forceinline__ void project_pair(const float2 v[24], float2 nrm, CP h[2][3]) {
+__device__ __forceinline__ void project_pair(const float2 v[24], CP h[2][3]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const CP p0{v[(0 * 3 + c) * 2], v[(0 * 3 + c) * 2 + 1]};
@@ -408,8 +399,8 @@ __device__ __forceinline__ void project_pair(const float2 v[24], float2 nrm, CP 
       h0 = cp_addpm<SIGMA>(p0, p2);
       h1 = cp_addpm<SIGMA>(p1, p3);
     }
-    h[0][c] = CP{M2(h0.re, nrm), M2(h0.im, nrm)};
-    h[1][c] = CP{M2(h1.re, nrm), M2(h1.im, nrm)};
+    h[0][c] = h0;
+    h[1][c] = h1;
   }
 }
 
@@ -449,27 +440,36 @@ __device__ __forceinline__ CP su3_row_pair(const CP u[3][3], const CP h[3], int 
   return r;
 }
 
-// acc += spin reconstruction of (U h), colour by colour (see spin_accum)
+// acc += n * (spin reconstruction of U h), colour by colour (see spin_accum);
+// n is the neighbour's norm pair (with the boundary sign), folded into the FMAs
+template <int S> __device__ __forceinline__ CP cp_fma_pm(const CP &acc, const CP &x, float2 n, float2 nn) {
+  return S > 0 ? CP{F2(n, x.re, acc.re), F2(n, x.im, acc.im)} : CP{F2(nn, x.re, acc.re), F2(nn, x.im, acc.im)};
+}
+template <int S> __device__ __forceinline__ CP cp_fma_i(const CP &acc, const CP &x, float2 n, float2 nn) {
+  // acc + S i n x:  re -= S n x.im, im += S n x.re
+  return S > 0 ? CP{F2(nn, x.im, acc.re), F2(n, x.re, acc.im)} : CP{F2(n, x.im, acc.re), F2(nn, x.re, acc.im)};
+}
 template <int MU, int SIGMA, bool DAG>
-__device__ __forceinline__ void su3_accum_pair(const CP u[3][3], const CP h[2][3], CP acc[4][3]) {
+__device__ __forceinline__ void su3_accum_pair(const CP u[3][3], const CP h[2][3], float2 n, CP acc[4][3]) {
+  const float2 nn = make_float2(-n.x, -n.y);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const CP x0 = su3_row_pair<DAG>(u, h[0], a);
     const CP x1 = su3_row_pair<DAG>(u, h[1], a);
-    acc[0][a] = cp_addpm<1>(acc[0][a], x0);
-    acc[1][a] = cp_addpm<1>(acc[1][a], x1);
+    acc[0][a] = cp_fma_pm<1>(acc[0][a], x0, n, nn);
+    acc[1][a] = cp_fma_pm<1>(acc[1][a], x1, n, nn);
     if (MU == 0) {
-      acc[2][a] = cp_addi<-SIGMA>(acc[2][a], x1);
-      acc[3][a] = cp_addi<-SIGMA>(acc[3][a], x0);
+      acc[2][a] = cp_fma_i<-SIGMA>(acc[2][a], x1, n, nn);
+      acc[3][a] = cp_fma_i<-SIGMA>(acc[3][a], x0, n, nn);
     } else if (MU == 1) {
-      acc[2][a] = cp_addpm<SIGMA>(acc[2][a], x1);
-      acc[3][a] = cp_addpm<-SIGMA>(acc[3][a], x0);
+      acc[2][a] = cp_fma_pm<SIGMA>(acc[2][a], x1, n, nn);
+      acc[3][a] = cp_fma_pm<-SIGMA>(acc[3][a], x0, n, nn);
     } else if (MU == 2) {
-      acc[2][a] = cp_addi<-SIGMA>(acc[2][a], x0);
-      acc[3][a] = cp_addi<SIGMA>(acc[3][a], x1);
+      acc[2][a] = cp_fma_i<-SIGMA>(acc[2][a], x0, n, nn);
+      acc[3][a] = cp_fma_i<SIGMA>(acc[3][a], x1, n, nn);
     } else {
-      acc[2][a] = cp_addpm<SIGMA>(acc[2][a], x0);
-      acc[3][a] = cp_addpm<SIGMA>(acc[3][a], x1);
+      acc[2][a] = cp_fma_pm<SIGMA>(acc[2][a], x0, n, nn);
+      acc[3][a] = cp_fma_pm<SIGMA>(acc[3][a], x1, n, nn);
     }
   }
 }
@@ -485,9 +485,9 @@ __device__ __forceinline__ void hop_dir_pair(const Geom &g, int p_out, const int
     const int sn = site_of(g, cn);
     load_raw(in, P, sn >> 1, v, nrm);
     if (MU == 3 && c[3] == g.L[3] - 1) nrm = make_float2(-nrm.x, -nrm.y);
-    project_pair<MU, -1>(v, nrm, h);
+    project_pair<MU, -1>(v, h);
     load_link_pair(links, p_out, MU, i, g.Vh, u);
-    su3_accum_pair<MU, -1, false>(u, h, acc);
+    su3_accum_pair<MU, -1, false>(u, h, nrm, acc);
   }
   {  // backward: (1 + gamma_mu) U_mu(x - mu)^+ psi(x - mu)
     int cn[4] = {c[0], c[1], c[2], c[3]};
@@ -495,9 +495,9 @@ __device__ __forceinline__ void hop_dir_pair(const Geom &g, int p_out, const int
     const int sn = site_of(g, cn);
     load_raw(in, P, sn >> 1, v, nrm);
     if (MU == 3 && c[3] == 0) nrm = make_float2(-nrm.x, -nrm.y);
-    project_pair<MU, +1>(v, nrm, h);
+    project_pair<MU, +1>(v, h);
     load_link_pair(links, 1 - p_out, MU, sn >> 1, g.Vh, u);
-    su3_accum_pair<MU, +1, true>(u, h, acc);
+    su3_accum_pair<MU, +1, true>(u, h, nrm, acc);
   }
 }
 
@@ -816,6 +816,87 @@ __global__ void __launch_bounds__(ST) k_accum_df(Geom g, int p, F32F src, float4
       dfl re = df_norm(dfl{o.x, o.z} + sc * dfl{v[k].x, 0.f});
       dfl im = df_norm(dfl{o.y, o.w} + sc * dfl{v[k].y, 0.f});
       q[k] = make_float4(re.h, im.h, re.l, im.l);
+    }
+  }
+}
+
+// Both parities at once: parity-local index i owns canonical sites 2i and 2i+1
+// (one even, one odd), so each thread's canonical data is one contiguous run.
+__device__ __forceinline__ int even_first(const Geom &g, int i) {  // is site 2i the even one?
+  int r = i / g.Lxh;
+  int y = r % g.L[1];
+  r /= g.L[1];
+  return ((y + r % g.L[2] + r / g.L[2]) & 1) == 0;
+}
+
+// dst_e / dst_o (FP32 parity fields) = scale[rhs] * src (canonical FP32)
+__global__ void __launch_bounds__(ST) k_cvt32to32_both(Geom g, const float2 *__restrict__ src, F32F de, F32F dodd,
+                                                       const double *scale, const int *list, const int *count,
+                                                       int nbx) {
+  const int n_items = *count * nbx;
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int rhs = list[w / nbx];
+    const int i = (w % nbx) * ST + threadIdx.x;
+    if (i >= g.Vh) continue;
+    const float2 *q = src + ((size_t)rhs * g.V + 2 * (size_t)i) * 12;
+    const float sc = (float)scale[rhs];
+    const int ef = even_first(g, i);
+    float2 v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = make_float2(q[k].x * sc, q[k].y * sc);
+    (ef ? de : dodd).store(rhs, i, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = make_float2(q[12 + k].x * sc, q[12 + k].y * sc);
+    (ef ? dodd : de).store(rhs, i, v);
+  }
+}
+
+// dst_e / dst_o (FP32 parity fields) = scale[rhs] * src (canonical FP64)
+__global__ void __launch_bounds__(ST) k_cvt64to32_both(Geom g, const double2 *__restrict__ src, F32F de, F32F dodd,
+                                                       const double *scale, const int *list, const int *count,
+                                                       int nbx) {
+  const int n_items = *count * nbx;
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int rhs = list[w / nbx];
+    const int i = (w % nbx) * ST + threadIdx.x;
+    if (i >= g.Vh) continue;
+    const double2 *q = src + ((size_t)rhs * g.V + 2 * (size_t)i) * 12;
+    const double sc = scale[rhs];
+    const int ef = even_first(g, i);
+    float2 v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = make_float2((float)(q[k].x * sc), (float)(q[k].y * sc));
+    (ef ? de : dodd).store(rhs, i, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = make_float2((float)(q[12 + k].x * sc), (float)(q[12 + k].y * sc));
+    (ef ? dodd : de).store(rhs, i, v);
+  }
+}
+
+// x (double-float canonical) += scale[rhs] * (e on even sites, o on odd sites)
+__global__ void __launch_bounds__(ST) k_accum_df_both(Geom g, F32F e, F32F o, float4 *x, const double *scale,
+                                                      const int *list, const int *count, int nbx) {
+  const int n_items = *count * nbx;
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int rhs = list[w / nbx];
+    const int i = (w % nbx) * ST + threadIdx.x;
+    if (i >= g.Vh) continue;
+    float4 *q = x + ((size_t)rhs * g.V + 2 * (size_t)i) * 12;
+    const double scd = scale[rhs];
+    const float sh = (float)scd;
+    const dfl sc{sh, (float)(scd - (double)sh)};
+    const int ef = even_first(g, i);
+    float2 v[12];
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      ((half == 0) == (ef != 0) ? e : o).load(rhs, i, v);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        float4 old = q[half * 12 + k];
+        dfl re = df_norm(dfl{old.x, old.z} + sc * dfl{v[k].x, 0.f});
+        dfl im = df_norm(dfl{old.y, old.w} + sc * dfl{v[k].y, 0.f});
+        q[half * 12 + k] = make_float4(re.h, im.h, re.l, im.l);
+      }
     }
   }
 }
@@ -1291,11 +1372,9 @@ struct MixedRun {
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.flags, hflags.data(), cap * sizeof(int), cudaMemcpyHostToDevice, st));
     // inner right-hand side: b32 = scale (r_e + kappa H_eo r_o), o32 = scale r_o
     if (cycle == 0) {
-      KL k_cvt64to32<<<G, ST, 0, st>>>(g, 0, b, b32, sb.scale, sb.cyc_list, counts + 2, nbx);
-      KL k_cvt64to32<<<G, ST, 0, st>>>(g, 1, b, o32, sb.scale, sb.cyc_list, counts + 2, nbx);
+      KL k_cvt64to32_both<<<G, ST, 0, st>>>(g, b, b32, o32, sb.scale, sb.cyc_list, counts + 2, nbx);
     } else {
-      KL k_cvt32to32<<<G, ST, 0, st>>>(g, 0, ss->r32, b32, sb.scale, sb.cyc_list, counts + 2, nbx);
-      KL k_cvt32to32<<<G, ST, 0, st>>>(g, 1, ss->r32, o32, sb.scale, sb.cyc_list, counts + 2, nbx);
+      KL k_cvt32to32_both<<<G, ST, 0, st>>>(g, ss->r32, b32, o32, sb.scale, sb.cyc_list, counts + 2, nbx);
     }
     KL k_hop32<EPI_AXPY><<<G, ST, 0, st>>>(g, 0, ctx->U32, o32, b32, b32, b32, 1.f, 0.f, kappa, sb.cyc_list,
                                            counts + 2, nullptr, nbx);
@@ -1392,8 +1471,7 @@ struct MixedRun {
     // odd half of the correction: e_o = o32 + kappa H_oe x32; x += |r| e
     KL k_hop32<EPI_AXPY><<<G, ST, 0, st>>>(g, 1, ctx->U32, x32, o32, o32, o32, 1.f, 0.f, kappa, sb.cyc_list,
                                            counts + 2, nullptr, nbx);
-    KL k_accum_df<<<G, ST, 0, st>>>(g, 0, x32, ss->xdf, sb.unscale, sb.cyc_list, counts + 2, nbx);
-    KL k_accum_df<<<G, ST, 0, st>>>(g, 1, o32, ss->xdf, sb.unscale, sb.cyc_list, counts + 2, nbx);
+    KL k_accum_df_both<<<G, ST, 0, st>>>(g, x32, o32, ss->xdf, sb.unscale, sb.cyc_list, counts + 2, nbx);
     LQCD_LAUNCH_CHECK(ctx, "mixed: correction");
     for (int k = 0; k < nrhs; ++k) keep_status[k] = hs[k].status;
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(hs.data(), sb.sc, cap * sizeof(SState), cudaMemcpyDeviceToHost, st));
