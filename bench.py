@@ -231,9 +231,11 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    base = rank * 1000003
+    from paper_1108_2473_gb300 import replicas
+    # disjoint noise vectors per rank (replicas: no data-path collective)
+    idx = replicas.noise_indices(rank, world, args.warmup + 2 * args.steps + 1)
     for w in range(args.warmup):
-        step(base + w)
+        step(idx[w])
     # ---------------------------------------------------------- timed region
     clocks = Clocks(local_rank)
     barrier()
@@ -245,7 +247,7 @@ def run_ours(args, rank, world, local_rank):
     e0.record(stream)
     iters, resid = [], []
     for k in range(args.steps):
-        st, _ = step(base + 100 + k)
+        st, _ = step(idx[args.warmup + k])
         iters += [s["iterations"] for s in st]
         resid += [s["true_rel_residual"] for s in st]
     e1.record(stream)
@@ -254,28 +256,20 @@ def run_ours(args, rank, world, local_rank):
     prof = L.lqcd_profile_end(h)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = replicas.max_over_ranks(ms, device=dev)
     solves = nrhs * args.steps * world
     value = solves / (t_max / 1e3)
 
     # ---------------------------------------- end to end through the C ABI
-    for w in range(1):
-        step(base + 500 + w, host=True)
+    step(idx[args.warmup + args.steps], host=True)  # warm the host path
     barrier()
     t0 = time.perf_counter()
     for k in range(args.steps):
-        _, pt = step(base + 600 + k, host=True)
+        _, pt = step(idx[args.warmup + args.steps + 1 + k], host=True)
         _ = pt.numpy().sum()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e_t = torch.tensor([e2e_s], device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_value = solves / float(e2e_t.item())
+    e2e_s = replicas.max_over_ranks(time.perf_counter() - t0, device=dev)
+    e2e_value = solves / e2e_s
 
     if rank != 0:
         L.lqcd_destroy(h)
@@ -284,7 +278,7 @@ def run_ours(args, rank, world, local_rank):
     # ------------------------------- plain single-RHS FP64 on a sample
     n64 = max(1, args.fp64_rhs)
     xs = torch.empty((n64, V, 4, 3), dtype=torch.complex128, device=dev)
-    L.lqcd_noise_generate(NOISE_SEED, L.LQCD_STREAM_LP, base + 100, DIMS, L.LQCD_DILUTE_TSC, 0, n64, src[:n64])
+    L.lqcd_noise_generate(NOISE_SEED, L.LQCD_STREAM_LP, idx[args.warmup], DIMS, L.LQCD_DILUTE_TSC, 0, n64, src[:n64])
     p64 = L.solver_params(tol=TOL, precision=L.LQCD_PREC_FP64, rhs_block=1)
     L.lqcd_solve_batch(h, src[:n64].contiguous(), xs, p64)  # warm-up
     torch.cuda.synchronize(dev)
