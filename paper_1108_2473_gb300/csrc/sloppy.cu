@@ -504,8 +504,8 @@ __device__ __forceinline__ void hop_dir_pair(const Geom &g, int p_out, const int
 // Sloppy hopping term on RHS pairs: out = cA A + cH (H in) at parity p_out.
 // EPI_PLAIN: out = cH H in.  EPI_DOTR: partial <B, out> per member.
 // EPI_TS: partials <out, A> and |out|^2 per member.
-template <class SP, int EPI>
-__global__ void __launch_bounds__(ST) k_hop_pair(Geom g, int p_out, const uint4 *links, SP in, SP out, SP A, SP B,
+template <class SP, int EPI, int MINB>
+__global__ void __launch_bounds__(ST, MINB) k_hop_pair(Geom g, int p_out, const uint4 *links, SP in, SP out, SP A, SP B,
                                                  float cA, float cH, const int *plist, const int *pcount, D4S *part,
                                                  int nbx, int nrhs, unsigned long long *prof) {
   const int n_items = *pcount * nbx;
@@ -574,6 +574,17 @@ __global__ void __launch_bounds__(ST) k_hop_pair(Geom g, int p_out, const uint4 
     if (EPI == EPI_DOTR || EPI == EPI_TS)
       block_reduce_store2(r0, r1, part + (size_t)(2 * P) * nbx + sb, part + (size_t)(2 * P + 1) * nbx + sb);
   }
+}
+
+// Two compiled variants of the pair hopping term, picked by the autotuner:
+// variant 0 lets the compiler use the registers it wants, variant 1 caps them
+// so that four blocks fit on an SM (more warps to hide neighbour-load latency).
+template <class SP, int EPI, class... Args>
+static void launch_hop_pair(int variant, int G, cudaStream_t q, Args... args) {
+  if (variant == 1)
+    KL k_hop_pair<SP, EPI, 4><<<G, ST, 0, q>>>(args...);
+  else
+    KL k_hop_pair<SP, EPI, 1><<<G, ST, 0, q>>>(args...);
 }
 
 // ============================================================ BLAS kernels
@@ -873,31 +884,45 @@ __global__ void __launch_bounds__(ST) k_cvt64to32_both(Geom g, const double2 *__
   }
 }
 
-// x (double-float canonical) += scale[rhs] * (e on even sites, o on odd sites)
-__global__ void __launch_bounds__(ST) k_accum_df_both(Geom g, F32F e, F32F o, float4 *x, const double *scale,
-                                                      const int *list, const int *count, int nbx) {
+// x (double-float canonical) += scale[rhs] * (e on even sites, o on odd sites).
+// A block's ST parity-local indices own 2 ST consecutive canonical sites: that
+// contiguous run (ST * 384 B) is staged through shared memory so every global
+// load and store is coalesced.
+constexpr int ACC_SITES = 64;  // parity-local indices per block (48 KiB of shared memory)
+__global__ void __launch_bounds__(ACC_SITES * 2) k_accum_df_both(Geom g, F32F e, F32F o, float4 *x,
+                                                                 const double *scale, const int *list,
+                                                                 const int *count, int nbx) {
+  __shared__ float4 tile[ACC_SITES * 24];
   const int n_items = *count * nbx;
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
     const int rhs = list[w / nbx];
-    const int i = (w % nbx) * ST + threadIdx.x;
-    if (i >= g.Vh) continue;
-    float4 *q = x + ((size_t)rhs * g.V + 2 * (size_t)i) * 12;
-    const double scd = scale[rhs];
-    const float sh = (float)scd;
-    const dfl sc{sh, (float)(scd - (double)sh)};
-    const int ef = even_first(g, i);
-    float2 v[12];
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      ((half == 0) == (ef != 0) ? e : o).load(rhs, i, v);
+    const int i0 = (w % nbx) * ACC_SITES;
+    const int nloc = min(ACC_SITES, g.Vh - i0);
+    float4 *base = x + ((size_t)rhs * g.V + 2 * (size_t)i0) * 12;
+    for (int k = threadIdx.x; k < nloc * 24; k += blockDim.x) tile[k] = base[k];
+    __syncthreads();
+    // two threads per parity-local index: one per canonical site of the pair
+    const int li = threadIdx.x >> 1, half = threadIdx.x & 1;
+    if (li < nloc) {
+      const int i = i0 + li;
+      const double scd = scale[rhs];
+      const float sh = (float)scd;
+      const dfl sc{sh, (float)(scd - (double)sh)};
+      const bool even_site = (half == 0) == (even_first(g, i) != 0);
+      float2 v[12];
+      (even_site ? e : o).load(rhs, i, v);
+      float4 *q = tile + (size_t)li * 24 + half * 12;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        float4 old = q[half * 12 + k];
+        float4 old = q[k];
         dfl re = df_norm(dfl{old.x, old.z} + sc * dfl{v[k].x, 0.f});
         dfl im = df_norm(dfl{old.y, old.w} + sc * dfl{v[k].y, 0.f});
-        q[half * 12 + k] = make_float4(re.h, im.h, re.l, im.l);
+        q[k] = make_float4(re.h, im.h, re.l, im.l);
       }
     }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nloc * 24; k += blockDim.x) base[k] = tile[k];
+    __syncthreads();
   }
 }
 
@@ -1237,11 +1262,12 @@ template <> BF16P pair_field<BF16P>(SloppyState *st, int f, int vh) {
   return BF16P{st->sd + (size_t)f * pairs * 6 * vh, vh};
 }
 
-static int tuned_blocks_per_sm(const lqcd_ctx *ctx, int nrhs, int precision) {
+// autotuned launch choice per (nrhs, precision): code = blocks_per_sm * 10 + hop variant
+static int tuned_code(const lqcd_ctx *ctx, int nrhs, int precision) {
   long long key = (long long)nrhs * 8 + precision;
   for (auto &kv : ctx->tuned)
     if (kv.first == key) return kv.second;
-  return 8;
+  return 80;
 }
 
 // One lattice's mixed-precision solve as a resumable state machine:
@@ -1262,7 +1288,7 @@ struct MixedRun {
   double t0;
   SloppyState *ss = nullptr;
   Geom g;
-  int vh = 0, cap = 0, nbx = 0, G = 0, npairs = 0;
+  int vh = 0, cap = 0, nbx = 0, G = 0, npairs = 0, hop_variant = 0;
   float kappa = 0.f, k2 = 0.f;
   double delta = 0.1, floor2 = 4e-12;  // (2e-6)^2: inner FP32 target floor, relative to |b_inner|^2
   SP r, rhat, pp, v, s, t, tmp;
@@ -1285,7 +1311,8 @@ struct MixedRun {
     nbx = (vh + ST - 1) / ST;
     kappa = (float)ctx->kappa;
     k2 = (float)(ctx->kappa * ctx->kappa);
-    G = num_sms(ctx->device) * tuned_blocks_per_sm(ctx, nrhs, p.precision);
+    G = num_sms(ctx->device) * (tuned_code(ctx, nrhs, p.precision) / 10);
+    hop_variant = tuned_code(ctx, nrhs, p.precision) % 10;
     npairs = (nrhs + 1) / 2;
     delta = p.delta > 0 ? p.delta : 0.1;
     r = pair_field<SP>(ss, 0, vh);
@@ -1318,7 +1345,7 @@ struct MixedRun {
 
   // key of the captured iteration graph: everything its kernels capture by value
   std::vector<double> graph_key() const {
-    return {(double)nrhs, (double)p.precision, (double)p.max_iter, delta, (double)kappa, (double)G,
+    return {(double)nrhs, (double)p.precision, (double)p.max_iter, delta, (double)kappa, (double)G, (double)hop_variant,
             (double)(uintptr_t)ss->sd, (double)(uintptr_t)ss->f32, (double)(uintptr_t)ss->small,
             (double)(uintptr_t)ctx->U16, (double)(uintptr_t)ctx->U32, (double)(uintptr_t)ss->xdf};
   }
@@ -1412,21 +1439,21 @@ struct MixedRun {
     for (int it = 0; it < k; ++it) {
       KL k_pair_p<SP><<<G, ST, 0, q>>>(vh, sb.sc, r, rhat, pp, v, sb.act_pairs, counts, nbx);
       ev_begin();
-      KL k_hop_pair<SP, EPI_PLAIN><<<G, ST, 0, q>>>(g, 1, L16, pp, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
+      launch_hop_pair<SP, EPI_PLAIN>(hop_variant, G, q, g, 1, L16, pp, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
                                                     nullptr, nbx, nrhs, prof);
       ev_end();
       ev_begin();
-      KL k_hop_pair<SP, EPI_DOTR><<<G, ST, 0, q>>>(g, 0, L16, tmp, v, pp, rhat, 1.f, -k2, sb.act_pairs, counts,
+      launch_hop_pair<SP, EPI_DOTR>(hop_variant, G, q, g, 0, L16, tmp, v, pp, rhat, 1.f, -k2, sb.act_pairs, counts,
                                                    sb.part, nbx, nrhs, prof);
       ev_end();
       KL k_sfin_alpha<<<npairs, 64, 0, q>>>(sb.sc, sb.flags, sb.act_pairs, counts, sb.part, nbx, nrhs);
       KL k_pair_s<SP><<<G, ST, 0, q>>>(vh, sb.sc, r, v, s, sb.act_pairs, counts, nbx);
       ev_begin();
-      KL k_hop_pair<SP, EPI_PLAIN><<<G, ST, 0, q>>>(g, 1, L16, s, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
+      launch_hop_pair<SP, EPI_PLAIN>(hop_variant, G, q, g, 1, L16, s, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
                                                     nullptr, nbx, nrhs, prof);
       ev_end();
       ev_begin();
-      KL k_hop_pair<SP, EPI_TS><<<G, ST, 0, q>>>(g, 0, L16, tmp, t, s, s, 1.f, -k2, sb.act_pairs, counts, sb.part,
+      launch_hop_pair<SP, EPI_TS>(hop_variant, G, q, g, 0, L16, tmp, t, s, s, 1.f, -k2, sb.act_pairs, counts, sb.part,
                                                  nbx, nrhs, prof);
       ev_end();
       KL k_sfin_omega<<<npairs, 64, 0, q>>>(sb.sc, sb.flags, sb.act_pairs, counts, sb.part, nbx, nrhs);
@@ -1471,7 +1498,8 @@ struct MixedRun {
     // odd half of the correction: e_o = o32 + kappa H_oe x32; x += |r| e
     KL k_hop32<EPI_AXPY><<<G, ST, 0, st>>>(g, 1, ctx->U32, x32, o32, o32, o32, 1.f, 0.f, kappa, sb.cyc_list,
                                            counts + 2, nullptr, nbx);
-    KL k_accum_df_both<<<G, ST, 0, st>>>(g, x32, o32, ss->xdf, sb.unscale, sb.cyc_list, counts + 2, nbx);
+    KL k_accum_df_both<<<G, ACC_SITES * 2, 0, st>>>(g, x32, o32, ss->xdf, sb.unscale, sb.cyc_list, counts + 2,
+                                                    (vh + ACC_SITES - 1) / ACC_SITES);
     LQCD_LAUNCH_CHECK(ctx, "mixed: correction");
     for (int k = 0; k < nrhs; ++k) keep_status[k] = hs[k].status;
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(hs.data(), sb.sc, cap * sizeof(SState), cudaMemcpyDeviceToHost, st));
@@ -1770,42 +1798,45 @@ static int autotune_hop(lqcd_ctx *ctx, int nrhs, int precision, int *best) {
   cudaEventCreate(&e1);
   const int cand[4] = {2, 4, 8, 16};
   float best_ms = 1e30f;
-  int best_b = 8;
+  int best_code = 80;
   const int nsm = num_sms(ctx->device);
-  for (int c : cand) {
-    const int G = nsm * c;
-    for (int rep = 0; rep < 2; ++rep)  // warm-up
-      KL k_hop_pair<SP, EPI_PLAIN><<<G, ST>>>(g, 1, ctx->U16, in, out, out, out, 0.f, 1.f, sb.act_pairs, sb.counts,
-                                              nullptr, nbx, nrhs, nullptr);
-    cudaEventRecord(e0);
-    for (int rep = 0; rep < 5; ++rep)
-      KL k_hop_pair<SP, EPI_PLAIN><<<G, ST>>>(g, 1, ctx->U16, in, out, out, out, 0.f, 1.f, sb.act_pairs, sb.counts,
-                                              nullptr, nbx, nrhs, nullptr);
-    cudaEventRecord(e1);
-    cudaError_t e = cudaEventSynchronize(e1);
-    if (e != cudaSuccess) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return cuda_error(ctx, e, "lqcd_autotune");
+  for (int variant = 0; variant < 2; ++variant)
+    for (int c : cand) {
+      const int G = nsm * c;
+      for (int rep = 0; rep < 2; ++rep)  // warm-up
+        launch_hop_pair<SP, EPI_PLAIN>(variant, G, (cudaStream_t)0, g, 1, (const uint4 *)ctx->U16, in, out, out,
+                                       out, 0.f, 1.f, (const int *)sb.act_pairs, (const int *)sb.counts,
+                                       (D4S *)nullptr, nbx, nrhs, (unsigned long long *)nullptr);
+      cudaEventRecord(e0);
+      for (int rep = 0; rep < 5; ++rep)
+        launch_hop_pair<SP, EPI_PLAIN>(variant, G, (cudaStream_t)0, g, 1, (const uint4 *)ctx->U16, in, out, out,
+                                       out, 0.f, 1.f, (const int *)sb.act_pairs, (const int *)sb.counts,
+                                       (D4S *)nullptr, nbx, nrhs, (unsigned long long *)nullptr);
+      cudaEventRecord(e1);
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_error(ctx, e, "lqcd_autotune");
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_code = c * 10 + variant;
+      }
     }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) {
-      best_ms = ms;
-      best_b = c;
-    }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   long long key = (long long)nrhs * 8 + precision;
   bool found = false;
   for (auto &kv : ctx->tuned)
     if (kv.first == key) {
-      kv.second = best_b;
+      kv.second = best_code;
       found = true;
     }
-  if (!found) ctx->tuned.push_back({key, best_b});
-  if (best) *best = best_b;
+  if (!found) ctx->tuned.push_back({key, best_code});
+  if (best) *best = best_code / 10;
   return LQCD_OK;
 }
 
