@@ -187,10 +187,10 @@ constexpr int DF3_SITES = 64;
 __global__ void __launch_bounds__(3 * DF3_SITES, 4) k_resid_df3(Geom g, int p_out, const float4 *__restrict__ U,
                                                               const float4 *__restrict__ x,
                                                               const float4 *__restrict__ b, float2 *r, float kh,
-                                                              float kl, D4R *part) {
+                                                              float kl, const int *list, D4R *part) {
   const int i = blockIdx.x * DF3_SITES + threadIdx.x / 3;
   const int a = threadIdx.x % 3;
-  const int rhs = blockIdx.y;
+  const int rhs = list[blockIdx.y];
   const size_t stride = (size_t)g.V * 12;
   float rn = 0.f, bn = 0.f;
   if (i < g.Vh) {
@@ -236,7 +236,8 @@ __global__ void __launch_bounds__(3 * DF3_SITES, 4) k_resid_df3(Geom g, int p_ou
     __syncthreads();
   }
   if (threadIdx.x == 0)
-    part[(size_t)rhs * 2 * gridDim.x + (size_t)p_out * gridDim.x + blockIdx.x] = D4R{0.0, 0.0, sh[0][0], sh[1][0]};
+    part[(size_t)blockIdx.y * 2 * gridDim.x + (size_t)p_out * gridDim.x + blockIdx.x] =
+        D4R{0.0, 0.0, sh[0][0], sh[1][0]};
 }
 
 __global__ void k_df_fin(const D4R *part, int nb, double *rr, double *bb) {
@@ -289,30 +290,38 @@ int df_join(lqcd_ctx *ctx, const float4 *in, double2 *out, size_t n, cudaStream_
 }
 
 // r = b - D x in double-float; per-RHS |r|^2, |b|^2 to the host arrays
-int df_residual(lqcd_ctx *ctx, const float4 *x, const float4 *b, float2 *r, int nrhs, double *rr, double *bb,
-                cudaStream_t st) {
+int df_residual(lqcd_ctx *ctx, const float4 *x, const float4 *b, float2 *r, const int *list, int n, double *rr,
+                double *bb, cudaStream_t st) {
+  if (n <= 0) return LQCD_OK;
   const Geom &g = ctx->geom;
   const int nblk = (g.Vh + DF3_SITES - 1) / DF3_SITES;
   int rc = LQCD_OK;
   Carver sizing(nullptr);
-  sizing.take<D4R>((size_t)nrhs * 2 * nblk);
-  sizing.take<double>(2 * (size_t)nrhs);
+  sizing.take<D4R>((size_t)n * 2 * nblk);
+  sizing.take<double>(2 * (size_t)n);
+  sizing.take<int>((size_t)n);
   void *w = workspace(ctx, WS_F64_PART, sizing.size(), &rc);
   if (!w) return rc;
   Carver cv(w);
-  D4R *part = cv.take<D4R>((size_t)nrhs * 2 * nblk);
-  double *d_rr = cv.take<double>(2 * (size_t)nrhs);
-  double *d_bb = d_rr + nrhs;
+  D4R *part = cv.take<D4R>((size_t)n * 2 * nblk);
+  double *d_rr = cv.take<double>(2 * (size_t)n);
+  double *d_bb = d_rr + n;
+  int *d_list = cv.take<int>((size_t)n);
+  LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(d_list, list, n * sizeof(int), cudaMemcpyHostToDevice, st));
   const float kh = (float)ctx->kappa, kl = (float)(ctx->kappa - (double)kh);
   for (int p = 0; p < 2; ++p) {
-    KL k_resid_df3<<<dim3(nblk, nrhs), 3 * DF3_SITES, 0, st>>>(g, p, ctx->Udf, x, b, r, kh, kl, part);
+    KL k_resid_df3<<<dim3(nblk, n), 3 * DF3_SITES, 0, st>>>(g, p, ctx->Udf, x, b, r, kh, kl, d_list, part);
     LQCD_LAUNCH_CHECK(ctx, "k_resid_df3");
   }
-  KL k_df_fin<<<nrhs, 32, 0, st>>>(part, 2 * nblk, d_rr, d_bb);
+  KL k_df_fin<<<n, 32, 0, st>>>(part, 2 * nblk, d_rr, d_bb);
   LQCD_LAUNCH_CHECK(ctx, "k_df_fin");
-  LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(rr, d_rr, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
-  LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(bb, d_bb, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  std::vector<double> h(2 * (size_t)n);
+  LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), d_rr, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
   LQCD_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  for (int j = 0; j < n; ++j) {
+    rr[list[j]] = h[j];
+    bb[list[j]] = h[n + j];
+  }
   return LQCD_OK;
 }
 

@@ -223,8 +223,10 @@ int launch_hop64(lqcd_ctx *ctx, cudaStream_t st, bool dag, bool in_canon, bool o
                  const double2 *B, double cB, double cH, const int *active, int nrhs);
 int df_split(lqcd_ctx *ctx, const double2 *in, float4 *out, size_t n, cudaStream_t st);
 int df_join(lqcd_ctx *ctx, const float4 *in, double2 *out, size_t n, cudaStream_t st);
-int df_residual(lqcd_ctx *ctx, const float4 *x, const float4 *b, float2 *r, int nrhs, double *rr, double *bb,
-                cudaStream_t st);
+// r = b - D x in double-float for the n right-hand sides list[0..n) (host
+// list); rr, bb (host, indexed by right-hand side) receive |r|^2 and |b|^2
+int df_residual(lqcd_ctx *ctx, const float4 *x, const float4 *b, float2 *r, const int *list, int n, double *rr,
+                double *bb, cudaStream_t st);
 int fp64_true_residual(lqcd_ctx *ctx, const double2 *b, const double2 *x, int nrhs, double *rr, double *bb,
                        cudaStream_t st);
 int fp64_apply_dirac(lqcd_ctx *ctx, const double2 *in, double2 *out, int nrhs, bool dagger,

@@ -50,9 +50,25 @@ __global__ void __launch_bounds__(LOOP_THREADS) k_loops(Geom g, const double2 *_
       const double2 *b = sol + ((size_t)i * g.V + s) * 12;
       double2 ea[12], eb[12];
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        ea[k] = a[k];
-        eb[k] = b[k];
+      for (int k = 0; k < 12; ++k) ea[k] = a[k];
+      // Spin rows of the source that are zero contribute exactly zero, and the
+      // solution rows they would pair with are not read: a diluted source is
+      // non-zero on one time slice (and spin, colour) only.
+      bool nz[4];
+#pragma unroll
+      for (int al = 0; al < 4; ++al) {
+        bool z = true;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) z = z && ea[al * 3 + c].x == 0.0 && ea[al * 3 + c].y == 0.0;
+        nz[al] = !z;
+      }
+      if (!(nz[0] || nz[1] || nz[2] || nz[3])) continue;
+#pragma unroll
+      for (int be = 0; be < 4; ++be) {
+        // rows paired with be by the three permutations: be, 3 - be, be + 2 mod 4
+        const bool need = nz[be] || nz[3 - be] || nz[(be + 2) & 3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) eb[be * 3 + c] = need ? b[be * 3 + c] : make_double2(0.0, 0.0);
       }
       // The six Gammas use three spin permutations (identity; 3-a; a+2 mod 4):
       // colour dot products P[perm][alpha] = sum_c conj(src[alpha][c]) sol[perm(alpha)][c]
@@ -63,9 +79,12 @@ __global__ void __launch_bounds__(LOOP_THREADS) k_loops(Geom g, const double2 *_
 #pragma unroll
         for (int al = 0; al < 4; ++al) {
           const int be = q == 0 ? al : (q == 1 ? 3 - al : (al + 2) & 3);
-          double2 d = cmulc(ea[al * 3], eb[be * 3]);
-          d = cadd(d, cmulc(ea[al * 3 + 1], eb[be * 3 + 1]));
-          d = cadd(d, cmulc(ea[al * 3 + 2], eb[be * 3 + 2]));
+          double2 d = make_double2(0.0, 0.0);
+          if (nz[al]) {
+            d = cmulc(ea[al * 3], eb[be * 3]);
+            d = cadd(d, cmulc(ea[al * 3 + 1], eb[be * 3 + 1]));
+            d = cadd(d, cmulc(ea[al * 3 + 2], eb[be * 3 + 2]));
+          }
           P[q][al] = d;
         }
 #pragma unroll

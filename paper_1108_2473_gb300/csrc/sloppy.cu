@@ -1351,14 +1351,26 @@ struct MixedRun {
   }
 
   int cycle_start() {
-    // at x = 0 the residual is b itself (FP64 norms only); later: double-float b - D x
+    // at x = 0 the residual is b itself (FP64 norms only); later: double-float
+    // b - D x for the right-hand sides corrected in the previous cycle (the
+    // others' iterates, and so their residuals, have not changed)
+    std::vector<int> todo;
+    if (cycle == 0) {
+      todo.resize(nrhs);
+      for (int k = 0; k < nrhs; ++k) todo[k] = k;
+    } else {
+      todo = hl;
+    }
     int rc = cycle == 0 ? fp64_residual_into(ctx, b, nullptr, nullptr, nrhs, rr.data(), bb.data(), st)
-                        : df_residual(ctx, ss->xdf, ss->bdf, ss->r32, nrhs, rr.data(), bb.data(), st);
+                        : df_residual(ctx, ss->xdf, ss->bdf, ss->r32, todo.data(), (int)todo.size(), rr.data(),
+                                      bb.data(), st);
     if (rc) return rc;
     hl.clear();
     hp.clear();
     std::fill(hflags.begin(), hflags.end(), 0);
-    for (int k = 0; k < nrhs; ++k) {
+    std::fill(hscale.begin(), hscale.end(), 0.0);
+    std::fill(hun.begin(), hun.end(), 0.0);
+    for (int k : todo) {
       double rel = bb[k] > 0 ? std::sqrt(rr[k] / bb[k]) : 0.0;
       stats[k].true_rel_residual = rel;
       stats[k].iterations = hs[k].iters;
@@ -1374,7 +1386,6 @@ struct MixedRun {
       prev_rel[k] = rel;
       stats[k].status = status;
       hs[k].status = status;
-      hscale[k] = hun[k] = 0.0;
       if (status == LQCD_OK && rel > p.tol) {
         hl.push_back(k);
         if (hp.empty() || hp.back() != k / 2) hp.push_back(k / 2);
