@@ -12,7 +12,9 @@
   with the HP set drawn from stream 1 and phi^{LP} from the same truncated
   solver on both sets.
 
-Per-time-slice loops are sums (not averages) over the sites of a time slice.
+Per-time-slice loops are sums (not averages) over the sites of a time slice;
+momentum-projected loops weight each site with e^{+i p.x} (the sink phase of
+the disconnected correlator, Sec. III).
 Gamma order: 1, gamma5, gamma1, gamma2, gamma3, gamma4.
 
 Parity: pinned by the free-field momentum sum, the hopping expansion to
@@ -118,5 +120,48 @@ def tsm_loops(U, kappa, dims, seed, n_lp, n_hp, tol_lp, tol_hp, scheme=DIL_NONE)
     return lp + corr / n_hp
 
 
-__all__ = ["contract", "per_timeslice", "point_source", "exact_propagator_diag",
+def momentum_loops(per_site, moms):
+    """Momentum-projected loops L_Gamma(p, t) = sum_{x in t} e^{+i p.x} L_Gamma(x).
+
+    The sink-side phase of the disconnected correlator (Sec. III, Eq. for D_AB)
+    and of the current insertion (Eq. 3-point).  per_site: (Lt, Lz, Ly, Lx, 6);
+    moms: integer triples (n_x, n_y, n_z) with p_i = 2 pi n_i / L_i.
+    Returns (n_mom, Lt, 6) complex.
+    """
+    lt, lz, ly, lx, ng = per_site.shape
+    z, y, x = np.meshgrid(np.arange(lz), np.arange(ly), np.arange(lx), indexing="ij")
+    out = np.zeros((len(moms), lt, ng), dtype=np.complex128)
+    for m, (nx, ny, nz) in enumerate(moms):
+        phase = np.exp(2j * np.pi * (nx * x / lx + ny * y / ly + nz * z / lz))
+        for t in range(lt):
+            out[m, t] = (phase[..., None] * per_site[t]).sum(axis=(0, 1, 2))
+    return out
+
+
+def disconnected_correlator(loops_p, loops_mp, l3, unbiased=True):
+    """Disconnected two-point function D_AB(p, t) (Sec. III, Eq. for D_AB).
+
+    D_AB(p, t) = 1/(L^3 Lt) sum_t' < L_A(p, t + t') L_B(-p, t') >, averaged
+    over the source time t' (time-translation invariance).  loops_p /
+    loops_mp: (N, Lt, 6) loops at momentum p / -p of N noise vectors (or N = 1
+    exact loops).  unbiased: average over ordered pairs of distinct vectors
+    r != r' (so no noise enters squared); otherwise over all N^2 pairs, which
+    for N = 1 is the plain product.  Returns (Lt, 6, 6) complex [t, A, B].
+    """
+    n, lt, ng = loops_p.shape
+    if unbiased and n < 2:
+        raise ValueError("the unbiased estimator needs at least two noise vectors")
+    d = np.zeros((lt, ng, ng), dtype=np.complex128)
+    for t in range(lt):
+        for tp in range(lt):
+            for r in range(n):
+                for rp in range(n):
+                    if unbiased and r == rp:
+                        continue
+                    d[t] += np.outer(loops_p[r, (t + tp) % lt], loops_mp[rp, tp])
+    pairs = n * (n - 1) if unbiased else n * n
+    return d / (l3 * lt * pairs)
+
+
+__all__ = ["momentum_loops", "disconnected_correlator", "contract", "per_timeslice", "point_source", "exact_propagator_diag",
            "loops_from_G", "exact_loops", "exact_loops_dense", "stochastic_loops", "tsm_loops", "z2_noise"]

@@ -87,36 +87,65 @@ def z2_noise(dims, seed, noise_index, stream=0):
     return xi
 
 
-# dilution schemes (Sec. II): which indices one diluted source keeps
+# dilution schemes (Sec. II): which indices one diluted source keeps.  A base
+# scheme (none, time, time+spin, time+spin+colour) may carry one spatial
+# partition flag: even-odd (x+y+z mod 2, two classes) or cubic (the eight
+# vertices of an elementary 3-cube, (x mod 2) + 2 (y mod 2) + 4 (z mod 2)).
 DIL_NONE, DIL_T, DIL_TS, DIL_TSC = 0, 1, 2, 3
+DIL_EO, DIL_CUBE = 4, 8
+
+
+def _split(scheme):
+    base, spatial = scheme & 3, scheme & ~3
+    if spatial not in (0, DIL_EO, DIL_CUBE):
+        raise ValueError("unknown dilution scheme")
+    return base, {0: 1, DIL_EO: 2, DIL_CUBE: 8}[spatial], spatial
 
 
 def dilution_count(dims, scheme):
+    base, n_sp, _ = _split(scheme)
     lt = dims[3]
-    return {DIL_NONE: 1, DIL_T: lt, DIL_TS: 4 * lt, DIL_TSC: 12 * lt}[scheme]
+    return {DIL_NONE: 1, DIL_T: lt, DIL_TS: 4 * lt, DIL_TSC: 12 * lt}[base] * n_sp
+
+
+def spatial_class(dims, scheme):
+    """Spatial partition class of every site, shape (Lt, Lz, Ly, Lx) (all zero without a flag)."""
+    lx, ly, lz, lt = dims
+    _, _, spatial = _split(scheme)
+    t, z, y, x = np.meshgrid(np.arange(lt), np.arange(lz), np.arange(ly), np.arange(lx), indexing="ij")
+    if spatial == DIL_EO:
+        return (x + y + z) % 2
+    if spatial == DIL_CUBE:
+        return (x % 2) + 2 * (y % 2) + 4 * (z % 2)
+    return np.zeros_like(t)
 
 
 def dilute(xi, scheme, index):
     """Diluted piece ``index`` of a noise vector.
 
-    Pieces are ordered t-major: index = (t*4 + spin)*3 + colour for TSC,
-    t*4 + spin for TS, t for T.  The pieces of one vector sum to the vector.
+    Pieces are ordered t-major, then spin, colour, spatial class:
+    index = ((t*4 + spin)*3 + colour) * n_spatial + class for TSC,
+    (t*4 + spin) * n_spatial + class for TS, t * n_spatial + class for T and
+    class alone without time dilution.  The pieces of one vector sum to it.
     """
+    base, n_sp, _ = _split(scheme)
+    dims = (xi.shape[3], xi.shape[2], xi.shape[1], xi.shape[0])
+    b, cls = divmod(index, n_sp)
+    keep = spatial_class(dims, scheme) == cls  # (Lt, Lz, Ly, Lx)
     out = np.zeros_like(xi)
-    if scheme == DIL_NONE:
-        return xi.copy()
-    if scheme == DIL_T:
-        t = index
-        out[t] = xi[t]
-    elif scheme == DIL_TS:
-        t, s = divmod(index, 4)
-        out[t, :, :, :, s, :] = xi[t, :, :, :, s, :]
-    elif scheme == DIL_TSC:
-        t, r = divmod(index, 12)
-        s, c = divmod(r, 3)
-        out[t, :, :, :, s, c] = xi[t, :, :, :, s, c]
+    if base == DIL_NONE:
+        out[keep] = xi[keep]
+        return out
+    if base == DIL_T:
+        t = b
+        out[t][keep[t]] = xi[t][keep[t]]
+    elif base == DIL_TS:
+        t, sp = divmod(b, 4)
+        out[t, :, :, :, sp, :][keep[t]] = xi[t, :, :, :, sp, :][keep[t]]
     else:
-        raise ValueError("unknown dilution scheme")
+        t, r = divmod(b, 12)
+        sp, c = divmod(r, 3)
+        out[t, :, :, :, sp, c][keep[t]] = xi[t, :, :, :, sp, c][keep[t]]
     return out
 
 

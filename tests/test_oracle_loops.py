@@ -183,3 +183,96 @@ def test_dense_exact_loops_match_point_source_solves():
     L = exact_loops(U, 0.125, DIMS, sites, tol=1e-13)
     for k, s in enumerate(sites):
         assert np.max(np.abs(full[s] - L[k])) < 1e-10
+
+
+def test_cubic_tsc_dilution_on_2cube_lattice_is_exact():
+    """On a 2^3 x Lt lattice t+s+c dilution with cubic spatial partitioning puts
+    one (site, spin, colour) in each piece, so Eq. (loop stochastic) with one
+    noise vector reproduces the exact loop at every site (|xi|^2 = 1)."""
+    from oracle.loops import exact_loops_dense, stochastic_loops
+    from oracle.philox import DIL_TSC, DIL_CUBE
+    dims = (2, 2, 2, 4)
+    U = haar_su3_field(dims, 12)
+    kappa = 0.13
+    est = stochastic_loops(U, kappa, dims, 5, [0], DIL_TSC | DIL_CUBE, tol=1e-13)
+    exact = exact_loops_dense(U, kappa)
+    assert np.max(np.abs(est - exact)) < 1e-10
+    # even-odd alone is not site-exact on this lattice: off-diagonal noise remains
+    from oracle.philox import DIL_EO
+    est_eo = stochastic_loops(U, kappa, dims, 5, [0], DIL_TSC | DIL_EO, tol=1e-13)
+    assert np.max(np.abs(est_eo - exact)) > 1e-6
+
+
+def test_momentum_loops_plane_wave_and_translation():
+    """sum_x e^{ip.x} e^{-iq.x} = L^3 delta_{p,q}; a spatial shift by a multiplies
+    by e^{ip.a}; p = 0 is the time-slice sum; n_i and n_i + L_i agree."""
+    from oracle.loops import momentum_loops, per_timeslice
+    lx, ly, lz, lt = 4, 6, 2, 3
+    z, y, x = np.meshgrid(np.arange(lz), np.arange(ly), np.arange(lx), indexing="ij")
+    q = (1, 2, 1)
+    wave = np.exp(-2j * np.pi * (q[0] * x / lx + q[1] * y / ly + q[2] * z / lz))
+    ps = np.zeros((lt, lz, ly, lx, 6), dtype=np.complex128)
+    ps[1, ..., 4] = wave
+    moms = [(0, 0, 0), q, (1, 0, 0), (q[0] + lx, q[1] - ly, q[2])]
+    m = momentum_loops(ps, moms)
+    assert abs(m[1, 1, 4] - lx * ly * lz) < 1e-9
+    assert abs(m[3, 1, 4] - lx * ly * lz) < 1e-9
+    assert abs(m[0, 1, 4]) < 1e-9 and abs(m[2, 1, 4]) < 1e-9
+    assert np.max(np.abs(np.delete(m, 1, axis=1))) == 0.0
+    rng = np.random.default_rng(4)
+    ps = rng.normal(size=(lt, lz, ly, lx, 6)) + 1j * rng.normal(size=(lt, lz, ly, lx, 6))
+    assert np.allclose(momentum_loops(ps, [(0, 0, 0)])[0], per_timeslice(ps), atol=1e-12)
+    a = (1, 2, 1)  # L'(x) = L(x - a)
+    shifted = np.roll(ps, shift=(a[2], a[1], a[0]), axis=(1, 2, 3))
+    p = (1, 1, 1)
+    phase = np.exp(2j * np.pi * (p[0] * a[0] / lx + p[1] * a[1] / ly + p[2] * a[2] / lz))
+    assert np.allclose(momentum_loops(shifted, [p])[0], phase * momentum_loops(ps, [p])[0], atol=1e-11)
+    # a single site x0 gives the phase e^{ip.x0}
+    d = np.zeros((lt, lz, ly, lx, 6), dtype=np.complex128)
+    d[2, 1, 3, 2, 0] = 1.0
+    got = momentum_loops(d, [p])[0, 2, 0]
+    assert abs(got - np.exp(2j * np.pi * (p[0] * 2 / lx + p[1] * 3 / ly + p[2] * 1 / lz))) < 1e-14
+
+
+def test_disconnected_correlator_identities():
+    """Unbiased estimator = ((sum_r L^r)(sum_r' L^r') - sum_r L^r L^r) / (N(N-1));
+    time translation invariance; N = 1 product form; zero-mean independent noise
+    on top of fixed loops leaves the unbiased estimator centred on the exact D."""
+    from oracle.loops import disconnected_correlator
+    rng = np.random.default_rng(7)
+    n, lt, l3 = 5, 6, 8
+    A = rng.normal(size=(n, lt, 6)) + 1j * rng.normal(size=(n, lt, 6))
+    B = rng.normal(size=(n, lt, 6)) + 1j * rng.normal(size=(n, lt, 6))
+    D = disconnected_correlator(A, B, l3)
+    sa, sb = A.sum(0), B.sum(0)
+    ref = np.zeros((lt, 6, 6), dtype=np.complex128)
+    for t in range(lt):
+        sa_t = np.roll(sa, -t, axis=0)
+        diag = np.einsum("rta,rtb->ab", np.roll(A, -t, axis=1), B)
+        ref[t] = (np.einsum("ta,tb->ab", sa_t, sb) - diag) / (n * (n - 1))
+    assert np.allclose(D, ref / (l3 * lt), atol=1e-13)
+    # translating every loop in time leaves D unchanged
+    assert np.allclose(disconnected_correlator(np.roll(A, 2, axis=1), np.roll(B, 2, axis=1), l3), D, atol=1e-13)
+    # N = 1 (exact loops): D(t) = 1/(L^3 Lt) sum_t' L_A(t + t') L_B(t')
+    D1 = disconnected_correlator(A[:1], B[:1], l3, unbiased=False)
+    assert np.allclose(D1[1], np.einsum("ta,tb->ab", np.roll(A[0], -1, axis=0), B[0]) / (l3 * lt), atol=1e-13)
+    with pytest.raises(ValueError):
+        disconnected_correlator(A[:1], B[:1], l3)
+    # unbiasedness: L^r = mu + eta^r with independent zero-mean eta
+    mu_a, mu_b = A[0], B[0]
+    exact = disconnected_correlator(mu_a[None], mu_b[None], l3, unbiased=False)
+    reps = []
+    for k in range(400):
+        eta = rng.normal(size=(2, 4, lt, 6))
+        reps.append(disconnected_correlator(mu_a + eta[0], mu_b + eta[1], l3))
+    reps = np.array(reps)
+    err = reps.std(axis=0).real / np.sqrt(len(reps))
+    z = np.abs(reps.mean(axis=0).real - exact.real) / err
+    assert np.mean(z ** 2) < 2.0
+    biased = np.array([disconnected_correlator(mu_a + e[0], mu_a + e[0], l3, unbiased=False)
+                       for e in rng.normal(size=(50, 2, 4, lt, 6))]).mean(axis=0)
+    # with the same noise in both loops the r = r' terms add <eta^2> / N per source time on the
+    # Gamma diagonal at t = 0: bias = Lt <eta^2> / (N L^3 Lt) = 1 / (4 * 8) here
+    bias = np.mean(biased.real[0].diagonal() - disconnected_correlator(mu_a[None], mu_a[None], l3,
+                                                                        unbiased=False)[0].real.diagonal())
+    assert 0.02 < bias < 0.045

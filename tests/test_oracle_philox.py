@@ -6,7 +6,8 @@ its raw output block i is Philox(counter + i + 1, key).
 import numpy as np
 import pytest
 
-from oracle.philox import philox4x64_10, z2_noise, diluted_sources, dilution_count, DIL_TSC, DIL_TS, DIL_T, DIL_NONE, SQRT1_2
+from oracle.philox import (philox4x64_10, z2_noise, diluted_sources, dilution_count, DIL_TSC, DIL_TS, DIL_T,
+                           DIL_NONE, DIL_EO, DIL_CUBE, SQRT1_2)
 
 
 @pytest.mark.parametrize("key,ctr", [((0, 0), (0, 0, 0, 0)), ((1, 2), (5, 0, 0, 0)),
@@ -63,7 +64,8 @@ def test_z2_moments():
     assert not np.array_equal(z2_noise(dims, 77, 0, 0), z2_noise(dims, 77, 0, 1))
 
 
-@pytest.mark.parametrize("scheme", [DIL_NONE, DIL_T, DIL_TS, DIL_TSC])
+@pytest.mark.parametrize("scheme", [DIL_NONE, DIL_T, DIL_TS, DIL_TSC, DIL_EO, DIL_T | DIL_EO, DIL_TS | DIL_CUBE,
+                                    DIL_TSC | DIL_EO, DIL_TSC | DIL_CUBE, DIL_CUBE])
 def test_dilution_partition(scheme):
     dims = (2, 2, 2, 4)
     src = diluted_sources(dims, 9, 2, scheme)
@@ -72,3 +74,43 @@ def test_dilution_partition(scheme):
     # pieces are disjoint
     nz = (np.abs(src) > 0).sum(axis=0)
     assert nz.max() == 1
+
+
+def test_spatial_dilution_classes():
+    """Even-odd: neighbouring spatial sites fall in different pieces; cubic: each
+    piece holds exactly one vertex of every elementary 2^3 cube (Sec. II)."""
+    dims = (4, 4, 4, 2)
+    lx, ly, lz, lt = dims
+    eo = diluted_sources(dims, 3, 0, DIL_T | DIL_EO)
+    assert eo.shape[0] == 2 * lt
+    for k in range(eo.shape[0]):
+        t, cls = divmod(k, 2)
+        support = np.abs(eo[k]).sum(axis=(-1, -2)) > 0  # (Lt, Lz, Ly, Lx)
+        assert support.sum() == lx * ly * lz // 2
+        assert support[t].sum() == support.sum()
+        zz, yy, xx = np.nonzero(support[t])
+        assert np.all((xx + yy + zz) % 2 == cls)
+        # no two sites of a piece are nearest spatial neighbours
+        for ax in range(3):
+            assert not np.any(support[t] & np.roll(support[t], 1, axis=ax))
+    cube = diluted_sources(dims, 3, 0, DIL_CUBE)
+    assert cube.shape[0] == 8
+    for k in range(8):
+        support = np.abs(cube[k]).sum(axis=(-1, -2)) > 0
+        for t in range(lt):
+            for z0 in range(0, lz, 2):
+                for y0 in range(0, ly, 2):
+                    for x0 in range(0, lx, 2):
+                        blk = support[t, z0:z0 + 2, y0:y0 + 2, x0:x0 + 2]
+                        assert blk.sum() == 1
+                        zz, yy, xx = np.nonzero(blk)
+                        assert xx[0] + 2 * yy[0] + 4 * zz[0] == k
+
+
+def test_spatial_dilution_counts():
+    dims = (4, 4, 4, 6)
+    assert dilution_count(dims, DIL_TSC | DIL_EO) == 12 * 6 * 2
+    assert dilution_count(dims, DIL_TSC | DIL_CUBE) == 12 * 6 * 8
+    assert dilution_count(dims, DIL_EO) == 2
+    with pytest.raises(ValueError):
+        dilution_count(dims, DIL_EO | DIL_CUBE)
