@@ -75,6 +75,13 @@ typedef struct CUstream_st *lqcd_stream_t; /* same type as cudaStream_t */
 #define LQCD_DILUTE_T 1    /* Lt pieces, piece = t                                */
 #define LQCD_DILUTE_TS 2   /* 4 Lt pieces, piece = 4 t + spin                     */
 #define LQCD_DILUTE_TSC 3  /* 12 Lt pieces, piece = 12 t + 3 spin + colour        */
+/* Spatial partitioning (Sec. II), OR-ed onto one of the schemes above (at most
+ * one of the two): the base piece b splits into n_sp pieces b * n_sp + class.
+ *   EO:   n_sp = 2, class = (x + y + z) mod 2 (even-odd in space)
+ *   CUBE: n_sp = 8, class = (x mod 2) + 2 (y mod 2) + 4 (z mod 2) (one source
+ *         per vertex of an elementary 3-cube, repeated over the lattice)      */
+#define LQCD_DILUTE_EO 4
+#define LQCD_DILUTE_CUBE 8
 
 #define LQCD_STREAM_LP 0 /* noise stream of the plain / low-precision set      */
 #define LQCD_STREAM_HP 1 /* noise stream of the TSM high-precision correction  */
@@ -199,6 +206,11 @@ int lqcd_noise_generate(uint64_t seed, uint64_t noise_stream, uint64_t noise_ind
                         const int dims[4], int dilution, int first_piece, int n_pieces,
                         double *out, lqcd_stream_t stream);
 
+/* Number of pieces of dilution scheme `dilution` (LQCD_DILUTE_*, optionally
+ * | LQCD_DILUTE_EO or | LQCD_DILUTE_CUBE) on a lattice dims (host, 4 ints);
+ * -1 for an unknown scheme or bad dims.  Host only. */
+int lqcd_dilution_pieces(const int dims[4], int dilution);
+
 /* Loop contraction (Eq. loop stochastic; with point sources Eq. loop):
  *   per_site[x][g] += weight * sum_i src_i(x)^+ Gamma_g sol_i(x)
  *   per_t[t][g]    += weight * sum_{x in slice t} sum_i src_i(x)^+ Gamma_g sol_i(x)
@@ -208,6 +220,29 @@ int lqcd_noise_generate(uint64_t seed, uint64_t noise_stream, uint64_t noise_ind
  * order (bit-reproducible). */
 int lqcd_loops_batch(lqcd_ctx *ctx, const double *src, const double *sol, int nrhs,
                      double weight, double *per_site, double *per_t, lqcd_stream_t stream);
+
+/* Momentum-projected loops (the sink phase of the disconnected correlator,
+ * Sec. III, and of the current insertion of the three-point function):
+ *   out[m][t][g] = sum_{x in slice t} e^{+i p_m . x} per_site[x][g],
+ *   p_m = 2 pi (moms[m][0] / Lx, moms[m][1] / Ly, moms[m][2] / Lz)
+ * per_site: [V][6] complex128 device (as lqcd_loops_batch writes it); moms:
+ * host int [n_mom][3] (any integers); out: [n_mom][Lt][6] complex128 device
+ * (overwritten).  The phase is evaluated from the exact integer numerator of
+ * p.x / 2 pi modulo the spatial volume; FP64 sums in a fixed order. */
+int lqcd_loops_momentum(lqcd_ctx *ctx, const double *per_site, int n_mom, const int *moms, double *out,
+                        lqcd_stream_t stream);
+
+/* Disconnected two-point function (Sec. III, Eq. for D_AB), averaged over the
+ * source time t':
+ *   D[t][A][B] = 1/(l3 Lt) * 1/n_pairs * sum_{(r, r')} sum_t' L^r_A(p, t + t') L^{r'}_B(-p, t')
+ * loops_p, loops_mp: [n_vec][Lt][6] complex128 device -- loops of n_vec noise
+ * vectors (or of one exact evaluation) at momenta p and -p (the same array for
+ * p = 0).  unbiased = 1: the ordered pairs r != r' (n_pairs = n_vec (n_vec - 1),
+ * needs n_vec >= 2), so that no noise vector meets itself; unbiased = 0: all
+ * n_vec^2 pairs (for n_vec = 1 exact loops, the plain product).  l3: spatial
+ * volume.  out: [Lt][6][6] complex128 device (overwritten).  No context needed. */
+int lqcd_disconnected_correlator(const double *loops_p, const double *loops_mp, int n_vec, int lt, int l3,
+                                 int unbiased, double *out, lqcd_stream_t stream);
 
 /* Stochastic loops with dilution and the truncated solver method (Sec. II,
  * Eq. loop stochastic; TSM after Bali, Collins, Schafer):

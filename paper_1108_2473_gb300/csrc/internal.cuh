@@ -31,6 +31,19 @@ __host__ __device__ inline Geom make_geom(const int d[4]) {
 }
 
 // Coordinates of parity-local index i of parity p.  Site s = 2 i + (x & 1).
+// pieces of a dilution scheme (LQCD_DILUTE_* base | optional EO / CUBE flag);
+// -1 for an unknown scheme or bad dims
+inline int dilution_pieces(const int dims[4], int dilution) {
+  if (!dims) return -1;
+  for (int i = 0; i < 4; ++i)
+    if (dims[i] < 2 || (dims[i] & 1)) return -1;
+  const int base = dilution & 3, spatial = dilution & ~3;
+  if (spatial != 0 && spatial != LQCD_DILUTE_EO && spatial != LQCD_DILUTE_CUBE) return -1;
+  const int n_sp = spatial == LQCD_DILUTE_EO ? 2 : (spatial == LQCD_DILUTE_CUBE ? 8 : 1);
+  const int n_base = base == LQCD_DILUTE_NONE ? 1 : base == LQCD_DILUTE_T ? dims[3] : base == LQCD_DILUTE_TS ? 4 * dims[3] : 12 * dims[3];
+  return n_base * n_sp;
+}
+
 __device__ __forceinline__ void coords_of(const Geom &g, int p, int i, int c[4]) {
   int xh = i % g.Lxh;
   int r = i / g.Lxh;

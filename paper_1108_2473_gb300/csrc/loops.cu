@@ -1,6 +1,7 @@
 // Loop contraction (Eq. loop; Eq. loop stochastic):
 //   L_Gamma(x) += w * sum_i src_i(x)^+ Gamma sol_i(x)
 // per site and per time slice, FP64 accumulation in a fixed order.
+#include <algorithm>
 #include <vector>
 
 #include "internal.cuh"
@@ -252,5 +253,117 @@ extern "C" int lqcd_loops_batch_noalloc(const int dims[4], const double *src, co
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_error(nullptr, e, "lqcd_loops_batch_noalloc: k_loops_fin");
   }
+  return LQCD_OK;
+}
+
+// ============================================== momentum projection, D_AB(p, t)
+namespace lqcd {
+
+constexpr int MOM_CHUNK = 128;  // momenta per launch (passed by value)
+constexpr int MOM_THREADS = 256;
+struct MomList {
+  int n[MOM_CHUNK][3];
+};
+
+// out[m][t][g] = sum_{x in slice t} e^{+i p_m.x} per_site[x][g].  p.x / 2 pi is
+// reduced exactly to num / (Lx Ly Lz) with integer arithmetic; the phase is
+// then sincospi(2 num / (Lx Ly Lz)).  One block per (t, m); strided per-thread
+// sums and a fixed tree make the result independent of scheduling.
+__global__ void __launch_bounds__(MOM_THREADS) k_loops_momentum(Geom g, const double2 *__restrict__ per_site,
+                                                                MomList moms, double2 *out) {
+  const int t = blockIdx.x, m = blockIdx.y;
+  const int lx = g.L[0], ly = g.L[1], lz = g.L[2];
+  const int v3 = lx * ly * lz;
+  const int nx = ((moms.n[m][0] % lx) + lx) % lx, ny = ((moms.n[m][1] % ly) + ly) % ly,
+            nz = ((moms.n[m][2] % lz) + lz) % lz;
+  double2 acc[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) acc[k] = make_double2(0.0, 0.0);
+  for (int xs = threadIdx.x; xs < v3; xs += MOM_THREADS) {
+    const int x = xs % lx, y = (xs / lx) % ly, z = xs / (lx * ly);
+    const long long num = ((long long)((nx * x) % lx) * ly * lz + (long long)((ny * y) % ly) * lx * lz +
+                           (long long)((nz * z) % lz) * lx * ly) % v3;
+    double sn, cs;
+    sincospi(2.0 * (double)num / (double)v3, &sn, &cs);
+    const double2 *L = per_site + ((size_t)t * v3 + xs) * 6;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const double2 l = L[k];
+      acc[k].x = fma(cs, l.x, fma(-sn, l.y, acc[k].x));
+      acc[k].y = fma(cs, l.y, fma(sn, l.x, acc[k].y));
+    }
+  }
+  __shared__ double2 sh[MOM_THREADS][6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) sh[threadIdx.x][k] = acc[k];
+  __syncthreads();
+  for (int w = MOM_THREADS / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) sh[threadIdx.x][k] = cadd(sh[threadIdx.x][k], sh[threadIdx.x + w][k]);
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) out[((size_t)m * gridDim.x + t) * 6 + threadIdx.x] = sh[0][threadIdx.x];
+}
+
+// D[t][a][b] for one (t, a, b) per thread:
+//   sum_t' [ S_a(t + t') S'_b(t') - (unbiased ? sum_r A_r,a(t + t') B_r,b(t') : 0) ]
+// with S = sum_r A_r, S' = sum_r B_r, scaled by 1 / (l3 Lt n_pairs).
+__global__ void k_correlator(const double2 *__restrict__ A, const double2 *__restrict__ B, int n, int lt,
+                             double scale, int unbiased, double2 *out) {
+  const int t = blockIdx.x, a = threadIdx.x / 6, b = threadIdx.x % 6;
+  if (threadIdx.x >= 36) return;
+  double2 d = make_double2(0.0, 0.0);
+  for (int tp = 0; tp < lt; ++tp) {
+    const int tf = (t + tp) % lt;
+    double2 sa = make_double2(0.0, 0.0), sb = sa, diag = sa;
+    for (int r = 0; r < n; ++r) {
+      const double2 ar = A[((size_t)r * lt + tf) * 6 + a], br = B[((size_t)r * lt + tp) * 6 + b];
+      sa = cadd(sa, ar);
+      sb = cadd(sb, br);
+      diag = cadd(diag, cmul(ar, br));
+    }
+    d = cadd(d, cmul(sa, sb));
+    if (unbiased) d = csub(d, diag);
+  }
+  out[((size_t)t * 6 + a) * 6 + b] = cscale(d, scale);
+}
+
+}  // namespace lqcd
+
+extern "C" int lqcd_loops_momentum(lqcd_ctx *ctx, const double *per_site, int n_mom, const int *moms, double *out,
+                                   lqcd_stream_t stream) {
+  if (!ctx || n_mom < 0 || (n_mom > 0 && (!per_site || !moms || !out)))
+    return set_error(ctx, LQCD_ERR_INVALID, "lqcd_loops_momentum: bad argument");
+  if (n_mom == 0) return LQCD_OK;
+  if (!is_device_ptr(per_site) || !is_device_ptr(out))
+    return set_error(ctx, LQCD_ERR_INVALID, "lqcd_loops_momentum: per_site and out must be device memory");
+  cudaSetDevice(ctx->device);
+  const Geom &g = ctx->geom;
+  for (int m0 = 0; m0 < n_mom; m0 += MOM_CHUNK) {
+    const int nm = std::min(MOM_CHUNK, n_mom - m0);
+    MomList ml;
+    for (int m = 0; m < nm; ++m)
+      for (int i = 0; i < 3; ++i) ml.n[m][i] = moms[(size_t)(m0 + m) * 3 + i];
+    KL k_loops_momentum<<<dim3(g.L[3], nm), MOM_THREADS, 0, (cudaStream_t)stream>>>(
+        g, (const double2 *)per_site, ml, (double2 *)out + (size_t)m0 * g.L[3] * 6);
+    LQCD_LAUNCH_CHECK(ctx, "k_loops_momentum");
+  }
+  return LQCD_OK;
+}
+
+extern "C" int lqcd_disconnected_correlator(const double *loops_p, const double *loops_mp, int n_vec, int lt, int l3,
+                                            int unbiased, double *out, lqcd_stream_t stream) {
+  if (!loops_p || !loops_mp || !out || n_vec < 1 || lt < 1 || l3 < 1 || (unbiased && n_vec < 2))
+    return set_error(nullptr, LQCD_ERR_INVALID,
+                     "lqcd_disconnected_correlator: bad argument (the unbiased estimator needs n_vec >= 2)");
+  if (!is_device_ptr(loops_p) || !is_device_ptr(loops_mp) || !is_device_ptr(out))
+    return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_disconnected_correlator: arrays must be device memory");
+  const double pairs = unbiased ? (double)n_vec * (n_vec - 1) : (double)n_vec * n_vec;
+  KL k_correlator<<<lt, 64, 0, (cudaStream_t)stream>>>((const double2 *)loops_p, (const double2 *)loops_mp, n_vec,
+                                                      lt, 1.0 / ((double)l3 * lt * pairs), unbiased,
+                                                      (double2 *)out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_error(nullptr, e, "lqcd_disconnected_correlator");
   return LQCD_OK;
 }

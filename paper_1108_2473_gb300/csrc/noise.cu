@@ -1,5 +1,6 @@
 // Complex Z2 noise sources (Sec. II, Eq. delta functions) from Philox4x64-10
-// (Salmon, Moraes, Dror, Shaw, SC'11), with time / spin / colour dilution.
+// (Salmon, Moraes, Dror, Shaw, SC'11), with time / spin / colour dilution and
+// even-odd or cubic spatial partitioning (Sec. II).
 #include "internal.cuh"
 
 namespace lqcd {
@@ -35,6 +36,15 @@ __global__ void k_noise(Geom g, uint64_t seed, uint64_t stream_tag, uint64_t noi
   int piece = first_piece + (int)(idx / g.V);
   int s = (int)(idx % g.V);
   int t = s / (g.L[0] * g.L[1] * g.L[2]);
+  // spatial partition: the piece's class among n_sp, and the site's class
+  const int spatial = dilution & ~3;
+  const int n_sp = spatial == LQCD_DILUTE_EO ? 2 : (spatial == LQCD_DILUTE_CUBE ? 8 : 1);
+  const int x = s % g.L[0], y = (s / g.L[0]) % g.L[1], z = (s / (g.L[0] * g.L[1])) % g.L[2];
+  const int site_cls = spatial == LQCD_DILUTE_EO ? (x + y + z) & 1
+                       : spatial == LQCD_DILUTE_CUBE ? (x & 1) + 2 * (y & 1) + 4 * (z & 1) : 0;
+  const bool in_class = piece % n_sp == site_cls;
+  piece /= n_sp;
+  dilution &= 3;
   int pt = -1, ps = -1, pc = -1;  // kept time slice / spin / colour (-1: all)
   if (dilution == LQCD_DILUTE_T) {
     pt = piece;
@@ -47,7 +57,7 @@ __global__ void k_noise(Geom g, uint64_t seed, uint64_t stream_tag, uint64_t noi
     pc = piece % 3;
   }
   double2 *o = out + idx * 12;
-  if (pt >= 0 && t != pt) {
+  if ((pt >= 0 && t != pt) || !in_class) {
 #pragma unroll
     for (int k = 0; k < 12; ++k) o[k] = make_double2(0.0, 0.0);
     return;
@@ -69,18 +79,17 @@ __global__ void k_noise(Geom g, uint64_t seed, uint64_t stream_tag, uint64_t noi
 
 using namespace lqcd;
 
+extern "C" int lqcd_dilution_pieces(const int dims[4], int dilution) { return dilution_pieces(dims, dilution); }
+
 extern "C" int lqcd_noise_generate(uint64_t seed, uint64_t noise_stream, uint64_t noise_index, const int dims[4],
                                    int dilution, int first_piece, int n_pieces, double *out, lqcd_stream_t stream) {
   if (!dims || !out || n_pieces < 0 || first_piece < 0)
     return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_noise_generate: bad argument");
   for (int i = 0; i < 4; ++i)
     if (dims[i] < 2 || (dims[i] & 1)) return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_noise_generate: bad dims");
-  if (dilution < LQCD_DILUTE_NONE || dilution > LQCD_DILUTE_TSC)
+  const int npieces_total = dilution_pieces(dims, dilution);
+  if (npieces_total < 0)
     return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_noise_generate: unknown dilution %d", dilution);
-  int npieces_total = dilution == LQCD_DILUTE_NONE ? 1
-                      : dilution == LQCD_DILUTE_T  ? dims[3]
-                      : dilution == LQCD_DILUTE_TS ? 4 * dims[3]
-                                                   : 12 * dims[3];
   if (first_piece + n_pieces > npieces_total)
     return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_noise_generate: pieces %d..%d beyond %d", first_piece,
                      first_piece + n_pieces - 1, npieces_total);

@@ -12,15 +12,7 @@ using namespace lqcd;
 
 namespace {
 
-int n_pieces(const int dims[4], int dilution) {
-  switch (dilution) {
-    case LQCD_DILUTE_NONE: return 1;
-    case LQCD_DILUTE_T: return dims[3];
-    case LQCD_DILUTE_TS: return 4 * dims[3];
-    case LQCD_DILUTE_TSC: return 12 * dims[3];
-    default: return -1;
-  }
-}
+int n_pieces(const int dims[4], int dilution) { return dilution_pieces(dims, dilution); }
 
 void merge(lqcd_solve_stats &acc, const lqcd_solve_stats &s) {
   acc.iterations = std::max(acc.iterations, s.iterations);

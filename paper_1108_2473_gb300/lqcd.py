@@ -38,6 +38,8 @@ LQCD_DILUTE_NONE = 0
 LQCD_DILUTE_T = 1
 LQCD_DILUTE_TS = 2
 LQCD_DILUTE_TSC = 3
+LQCD_DILUTE_EO = 4    # spatial even-odd partition, OR-ed onto a scheme above
+LQCD_DILUTE_CUBE = 8  # spatial cubic (2^3 vertices) partition, OR-ed likewise
 LQCD_STREAM_LP = 0
 LQCD_STREAM_HP = 1
 
@@ -118,6 +120,9 @@ _SIGS = {
     "lqcd_profile_begin": (_i, [_vp]),
     "lqcd_profile_end": (_i, [_vp, ctypes.POINTER(lqcd_profile)]),
     "lqcd_launch_count": (ctypes.c_longlong, []),
+    "lqcd_dilution_pieces": (_i, [ctypes.POINTER(_i), _i]),
+    "lqcd_loops_momentum": (_i, [_vp, _vp, _i, ctypes.POINTER(_i), _vp, _vp]),
+    "lqcd_disconnected_correlator": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _vp]),
 }
 OPTIONAL_SIGS = {}
 
@@ -237,6 +242,28 @@ def lqcd_point_sources(h, sites, out):
 def lqcd_noise_generate(seed, noise_stream, noise_index, dims, dilution, first_piece, n_pieces, out):
     rc = load().lqcd_noise_generate(int(seed), int(noise_stream), int(noise_index), _dims(dims), int(dilution),
                                     int(first_piece), int(n_pieces), _ptr(out), _stream(out))
+    return _check(rc, None)
+
+
+def lqcd_dilution_pieces(dims, dilution):
+    n = load().lqcd_dilution_pieces(_dims(dims), int(dilution))
+    if n < 0:
+        raise LqcdError(LQCD_ERR_INVALID, f"unknown dilution scheme {dilution} or bad dims {tuple(dims)}")
+    return n
+
+
+def lqcd_loops_momentum(h, per_site, moms, out):
+    """out[m, t, g] = sum_{x in t} exp(+i p_m.x) per_site[x, g]; moms: integer triples (n_x, n_y, n_z)."""
+    flat = [int(v) for m in moms for v in m]
+    arr = (_i * len(flat))(*flat)
+    return _check(load().lqcd_loops_momentum(h, _ptr(per_site), len(moms), arr, _ptr(out), _stream(out)), h)
+
+
+def lqcd_disconnected_correlator(loops_p, loops_mp, l3, out, unbiased=True):
+    """D[t, A, B] from [n_vec, Lt, 6] loops at momenta p and -p (device tensors)."""
+    n, lt = loops_p.shape[0], loops_p.shape[1]
+    rc = load().lqcd_disconnected_correlator(_ptr(loops_p), _ptr(loops_mp), n, lt, int(l3), int(bool(unbiased)),
+                                             _ptr(out), _stream(out))
     return _check(rc, None)
 
 

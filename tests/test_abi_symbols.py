@@ -44,3 +44,17 @@ def test_binding_loads_and_reports_bad_arguments_without_gpu():
     assert "bad" in lqcd.lqcd_last_error(None)
     out = ctypes.c_void_p()
     assert lib.lqcd_create(ctypes.byref(out), (ctypes.c_int * 4)(4, 4, 5, 4), 0) == lqcd.LQCD_ERR_INVALID
+
+
+def test_dilution_piece_count_matches_oracle_without_gpu():
+    """lqcd_dilution_pieces is host-only: it agrees with the oracle's count for
+    every base scheme with and without a spatial flag, and rejects bad input."""
+    from oracle.philox import dilution_count, DIL_EO, DIL_CUBE
+    from paper_1108_2473_gb300 import lqcd
+    for dims in [(4, 4, 4, 8), (2, 2, 2, 4), (6, 4, 2, 10)]:
+        for base in range(4):
+            for sp in (0, DIL_EO, DIL_CUBE):
+                assert lqcd.lqcd_dilution_pieces(dims, base | sp) == dilution_count(dims, base | sp)
+    lib = lqcd.load()
+    assert lib.lqcd_dilution_pieces((ctypes.c_int * 4)(4, 4, 4, 4), DIL_EO | DIL_CUBE) == -1
+    assert lib.lqcd_dilution_pieces((ctypes.c_int * 4)(4, 3, 4, 4), 3) == -1

@@ -66,7 +66,8 @@ def test_host_gauge_pointer_accepted():
 
 
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 2, 4, 6), (16, 16, 16, 32)])
-@pytest.mark.parametrize("scheme", [oph.DIL_NONE, oph.DIL_T, oph.DIL_TS, oph.DIL_TSC])
+@pytest.mark.parametrize("scheme", [oph.DIL_NONE, oph.DIL_T, oph.DIL_TS, oph.DIL_TSC, oph.DIL_EO,
+                                    oph.DIL_TSC | oph.DIL_EO, oph.DIL_TSC | oph.DIL_CUBE, oph.DIL_T | oph.DIL_CUBE])
 def test_noise_bit_exact(dims, scheme):
     L_ = __import__("tests._gpu", fromlist=["require_gpu"]).require_gpu()
     V = int(np.prod(dims))
