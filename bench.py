@@ -183,6 +183,69 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------- kernels beyond the step
+def _event_ms(fn, stream, reps=10, warm=3):
+    import torch
+    for _ in range(warm):
+        fn()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def next_rows(L, h, per_site, dev, stream, with_oracle):
+    """Times the momentum projection, the disconnected correlator and spatially
+    diluted noise on the bench lattice (after the timed step; not part of it),
+    with the oracle timed beside them on the same inputs."""
+    import numpy as np
+    import torch
+    lx, ly, lz, lt = DIMS
+    V, v3 = lx * ly * lz * lt, lx * ly * lz
+    out = {}
+    moms = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)]
+    mo = torch.empty((len(moms), lt, 6), dtype=torch.complex128, device=dev)
+    ms = _event_ms(lambda: L.lqcd_loops_momentum(h, per_site, moms, mo), stream)
+    # FP64 sincospi + 6 complex FMAs per (site, momentum); per_site is read once per momentum (L2-resident)
+    out["momentum_loops"] = {"n_mom": len(moms), "ms": ms, "site_momenta_per_s": V * len(moms) / (ms / 1e3),
+                             "bound": "alu (FP64)",
+                             "fp64_fma_gflops": V * len(moms) * 48 / (ms / 1e3) / 1e9}  # 24 FMAs per pair
+    nvec = 16
+    g = torch.Generator(device="cpu").manual_seed(5)
+    lp = torch.randn((nvec, lt, 6), dtype=torch.complex128, generator=g).to(dev)
+    lm = torch.randn((nvec, lt, 6), dtype=torch.complex128, generator=g).to(dev)
+    D = torch.empty((lt, 6, 6), dtype=torch.complex128, device=dev)
+    ms_c = _event_ms(lambda: L.lqcd_disconnected_correlator(lp, lm, v3, D, True), stream)
+    out["correlator"] = {"n_vec": nvec, "lt": lt, "ms": ms_c}
+    nz = 384
+    buf = torch.empty((nz, V, 4, 3), dtype=torch.complex128, device=dev)
+    for name, scheme in (("tsc", L.LQCD_DILUTE_TSC), ("tsc_eo", L.LQCD_DILUTE_TSC | L.LQCD_DILUTE_EO),
+                         ("tsc_cube", L.LQCD_DILUTE_TSC | L.LQCD_DILUTE_CUBE)):
+        ms_n = _event_ms(lambda: L.lqcd_noise_generate(NOISE_SEED, 0, 0, DIMS, scheme, 0, nz, buf), stream, reps=3)
+        out[f"noise_{name}"] = {"pieces_per_vector": L.lqcd_dilution_pieces(DIMS, scheme), "chunk": nz, "ms": ms_n,
+                                "write_GBps": nz * V * 192 / (ms_n / 1e3) / 1e9}
+    del buf
+    if with_oracle:
+        from oracle import loops as olp
+        ps = per_site.cpu().numpy().reshape(lt, lz, ly, lx, 6)
+        t0 = time.perf_counter()
+        ref = olp.momentum_loops(ps, moms)
+        out["momentum_loops"]["oracle_ms"] = 1e3 * (time.perf_counter() - t0)
+        got = mo.cpu().numpy()
+        out["momentum_loops"]["max_rel_diff_vs_oracle"] = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        a, b = lp.cpu().numpy(), lm.cpu().numpy()
+        t0 = time.perf_counter()
+        refd = olp.disconnected_correlator(a, b, v3, True)
+        out["correlator"]["oracle_ms"] = 1e3 * (time.perf_counter() - t0)
+        out["correlator"]["max_rel_diff_vs_oracle"] = float(np.max(np.abs(D.cpu().numpy() - refd)) /
+                                                             np.max(np.abs(refd)))
+    return out
+
+
 # ------------------------------------------------------------------------ ours
 def run_ours(args, rank, world, local_rank):
     import numpy as np
@@ -288,6 +351,7 @@ def run_ours(args, rank, world, local_rank):
     rc, st64 = L.lqcd_solve_batch(h, src[:n64].contiguous(), xs, p64)
     torch.cuda.synchronize(dev)
     fp64_rate = n64 / (time.perf_counter() - t0)
+    extras = next_rows(L, h, per_site, dev, stream, not args.no_cpu)
     L.lqcd_destroy(h)
 
     # ---------------------------------------------------------- roofline
@@ -337,6 +401,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": "RHS solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clk,
+        "next_rows": extras,
     }
     print(json.dumps(line), flush=True)
 

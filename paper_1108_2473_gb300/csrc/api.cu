@@ -68,7 +68,15 @@ __device__ __forceinline__ double2 dmul(double2 a, double2 b) { return cmul(a, b
 
 // Check unitarity and unit determinant of every link; write the FP32 and FP16
 // reconstruct-12 copies (rows 0 and 1) in parity-split SoA order.
-__global__ void k_pack_gauge(const double2 *__restrict__ U, Geom g, float4 *U32, uint4 *U16, float4 *Udf, int *flag) {
+// FP32 -> tf32 with round-to-nearest (ties away), kept in an FP32 register
+__device__ __forceinline__ float to_tf32(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__global__ void k_pack_gauge(const double2 *__restrict__ U, Geom g, float4 *U32, uint4 *U16, float4 *Udf,
+                             float2 *Utf, int *flag) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= g.V * 4) return;
   int s = idx >> 2, mu = idx & 3;
@@ -127,6 +135,10 @@ __global__ void k_pack_gauge(const double2 *__restrict__ U, Geom g, float4 *U32,
 #pragma unroll
   for (int k = 0; k < 5; ++k)
     U16[base16 + (size_t)k * g.Vh] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+  // tf32 copy for the tensor-core pair kernel: the 9 entries of one link contiguous
+  float2 *ut = Utf + ((size_t)(p * 4 + mu) * g.Vh + i) * 9;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) ut[k] = make_float2(to_tf32((float)m[k / 3][k % 3].x), to_tf32((float)m[k / 3][k % 3].y));
 }
 
 // Plaquette partial sums: one double per block.
@@ -231,6 +243,7 @@ int lqcd_destroy(lqcd_ctx *ctx) {
   cudaFree(ctx->U64);
   cudaFree(ctx->U32);
   cudaFree(ctx->U16);
+  cudaFree(ctx->Utf);
   cudaFree(ctx->Udf);
   cudaFree(ctx->d_flag);
   cudaFree(ctx->d_prof);
@@ -261,6 +274,7 @@ static int set_gauge_impl(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream, 
     LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->U64, n64 * sizeof(double2)));
     LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->U32, (size_t)g.V * 4 * 3 * sizeof(float4)));
     LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->U16, (size_t)g.Vh * 2 * 4 * 5 * sizeof(uint4)));
+    LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->Utf, (size_t)g.Vh * 2 * 4 * 9 * sizeof(float2)));
     LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->Udf, n64 * sizeof(float4)));
   }
   int st_ = LQCD_OK;
@@ -270,7 +284,7 @@ static int set_gauge_impl(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream, 
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(stage, U, n64 * sizeof(double2), kind, st));
   LQCD_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), st));
   int threads = 256, blocks = (g.V * 4 + threads - 1) / threads;
-  KL k_pack_gauge<<<blocks, threads, 0, st>>>(stage, g, ctx->U32, ctx->U16, ctx->Udf, ctx->d_flag);
+  KL k_pack_gauge<<<blocks, threads, 0, st>>>(stage, g, ctx->U32, ctx->U16, ctx->Udf, ctx->Utf, ctx->d_flag);
   LQCD_LAUNCH_CHECK(ctx, "k_pack_gauge");
   int flag = 0;
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(&flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));

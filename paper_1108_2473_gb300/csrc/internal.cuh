@@ -167,6 +167,7 @@ struct lqcd_ctx {
   float4 *U32 = nullptr;      // recon-12 FP32  [2 parity][4 mu][3 float4][Vh]
   float4 *Udf = nullptr;      // double-float copy  [V][4][3][3] (hi.re, hi.im, lo.re, lo.im)
   uint4 *U16 = nullptr;       // FP16, all 18 reals, each twice  [2 parity][4 mu][5 uint4][Vh]
+  float2 *Utf = nullptr;      // tf32-rounded FP32, [2 parity][4 mu][Vh][3][3] complex (tensor-core hop)
   std::vector<lqcd::DevBuf> ws;  // named workspaces, grow-only
   lqcd::SloppyState *sloppy = nullptr;
   std::string err;

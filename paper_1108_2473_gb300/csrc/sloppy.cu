@@ -33,10 +33,13 @@
 // order: a right-hand side's arithmetic does not depend on its batch mates.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
 #include "df.cuh"
+
 #include "sloppy.cuh"
 
 namespace lqcd {
@@ -303,6 +306,40 @@ __device__ __forceinline__ void block_reduce_store2(D4S v0, D4S v1, D4S *dst0, D
   __syncthreads();
 }
 
+// As block_reduce_store2 for each group of ST threads of a block of PPB * ST
+// threads; groups with store == false only take part in the barriers.
+template <int PPB>
+__device__ __forceinline__ void group_reduce_store2(D4S v0, D4S v1, D4S *dst0, D4S *dst1, bool store) {
+  __shared__ D4S sh[PPB][2][ST / 32];
+  const int grp = threadIdx.x / ST, tid = threadIdx.x % ST;
+  const int lane = tid & 31, w = tid >> 5;
+  v0.a = warp_sum_d(v0.a);
+  v0.b = warp_sum_d(v0.b);
+  v0.c = warp_sum_d(v0.c);
+  v0.d = warp_sum_d(v0.d);
+  v1.a = warp_sum_d(v1.a);
+  v1.b = warp_sum_d(v1.b);
+  v1.c = warp_sum_d(v1.c);
+  v1.d = warp_sum_d(v1.d);
+  if (lane == 0) {
+    sh[grp][0][w] = v0;
+    sh[grp][1][w] = v1;
+  }
+  __syncthreads();
+  if (tid < 2 && store) {
+    D4S t = sh[grp][tid][0];
+#pragma unroll
+    for (int k = 1; k < ST / 32; ++k) {
+      t.a += sh[grp][tid][k].a;
+      t.b += sh[grp][tid][k].b;
+      t.c += sh[grp][tid][k].c;
+      t.d += sh[grp][tid][k].d;
+    }
+    *(tid ? dst1 : dst0) = t;
+  }
+  __syncthreads();
+}
+
 // FP32 hopping term: out = cA A + cB B + cH (H in) at the sites of parity p_out.
 // EPI_PLAIN: A, B unused.  EPI_AXPY: B unused.  EPI_RES: partial |out|^2.
 template <int EPI>
@@ -504,19 +541,27 @@ __device__ __forceinline__ void hop_dir_pair(const Geom &g, int p_out, const int
 // Sloppy hopping term on RHS pairs: out = cA A + cH (H in) at parity p_out.
 // EPI_PLAIN: out = cH H in.  EPI_DOTR: partial <B, out> per member.
 // EPI_TS: partials <out, A> and |out|^2 per member.
-template <class SP, int EPI, int MINB>
-__global__ void __launch_bounds__(ST, MINB) k_hop_pair(Geom g, int p_out, const uint4 *links, SP in, SP out, SP A, SP B,
-                                                 float cA, float cH, const int *plist, const int *pcount, D4S *part,
-                                                 int nbx, int nrhs, unsigned long long *prof) {
-  const int n_items = *pcount * nbx;
+// A block of PPB * ST threads takes PPB active pairs on the same ST sites, so
+// the links those sites read are fetched from L2 once per block and then hit
+// in L1 for the other pairs.
+template <class SP, int EPI, int MINB, int PPB>
+__global__ void __launch_bounds__(ST * PPB, MINB) k_hop_pair(Geom g, int p_out, const uint4 *links, SP in, SP out,
+                                                       SP A, SP B, float cA, float cH, const int *plist,
+                                                       const int *pcount, D4S *part, int nbx, int nrhs,
+                                                       unsigned long long *prof) {
+  const int count = *pcount;
+  const int n_items = (count + PPB - 1) / PPB * nbx;
   const float2 cA2 = make_float2(cA, cA), cH2 = make_float2(cH, cH);
+  const int grp = threadIdx.x / ST, tid = threadIdx.x % ST;
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const int P = plist[w / nbx], sb = w % nbx;
-    const int i = sb * ST + threadIdx.x;
-    if (prof && threadIdx.x == 0)
+    const int j = (w / nbx) * PPB + grp, sb = w % nbx;
+    const bool valid = j < count;
+    const int P = valid ? plist[j] : 0;
+    const int i = sb * ST + tid;
+    if (prof && tid == 0 && valid)
       atomicAdd(prof + EPI, (unsigned long long)min(ST, g.Vh - sb * ST) * (2 * P + 1 < nrhs ? 2 : 1));
     D4S r0 = {0, 0, 0, 0}, r1 = {0, 0, 0, 0};
-    if (i < g.Vh) {
+    if (valid && i < g.Vh) {
       int c[4];
       coords_of(g, p_out, i, c);
       CP acc[4][3];
@@ -572,19 +617,355 @@ __global__ void __launch_bounds__(ST, MINB) k_hop_pair(Geom g, int p_out, const 
       }
     }
     if (EPI == EPI_DOTR || EPI == EPI_TS)
-      block_reduce_store2(r0, r1, part + (size_t)(2 * P) * nbx + sb, part + (size_t)(2 * P + 1) * nbx + sb);
+      group_reduce_store2<PPB>(r0, r1, part + (size_t)(2 * P) * nbx + sb, part + (size_t)(2 * P + 1) * nbx + sb,
+                               valid);
   }
 }
 
-// Two compiled variants of the pair hopping term, picked by the autotuner:
-// variant 0 lets the compiler use the registers it wants, variant 1 caps them
-// so that four blocks fit on an SM (more warps to hide neighbour-load latency).
-template <class SP, int EPI, class... Args>
-static void launch_hop_pair(int variant, int G, cudaStream_t q, Args... args) {
-  if (variant == 1)
-    KL k_hop_pair<SP, EPI, 4><<<G, ST, 0, q>>>(args...);
-  else
-    KL k_hop_pair<SP, EPI, 1><<<G, ST, 0, q>>>(args...);
+// ======================================== pair hopping term on tensor cores
+// The SU(3) products of the hopping term are moved onto the tensor cores with
+// mma.sync m16n8k8 (tf32 in, FP32 accumulate); spin projection, the norms and
+// the spin reconstruction stay on the FP32 units.  A warp takes 8 pairs of one
+// site; lane (g, t) = (lane / 4, lane % 4) owns pair g and colour t (t = 3
+// carries zeros).  For one (site, direction, half-spinor j) the MMA computes
+//   D[row][n] = sum_k A[row][k] B[k][n]
+// with rows g / g + 8 = the two members of pair g, k = (Re c0, Re c1, Re c2, 0,
+// Im c0, Im c1, Im c2, 0) the projected half-spinor h_j and B the real form of
+// U^T (or of U^+^T backwards), columns n = (Re a0, Im a0, Re a1, ... , 0, 0):
+// so each lane's operands and results are its own pair and colour, read from
+// and written to the pair layout directly, with no data exchange between lanes.
+__device__ __forceinline__ unsigned tf32_bits(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void mma_tf32(float d[4], const unsigned a[4], unsigned b0, unsigned b1) {
+  asm(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%10,%10,%10,%10};"
+      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1), "f"(0.f));
+}
+__device__ __forceinline__ float2 unpack_word(const F16P &, unsigned w) { return h2f(w); }
+__device__ __forceinline__ float2 unpack_word(const BF16P &, unsigned w) { return b2f(w); }
+
+// colour t of all four spins of pair P at site i (values as stored, unscaled)
+template <class SP>
+__device__ __forceinline__ void load_colour(const SP &f, int P, int i, int t, CP p[4]) {
+  const uint4 *base = f.d + (size_t)P * 6 * f.vh + i;
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp) {
+    const int k = 6 * sp + 2 * t;  // words k (Re) and k + 1 (Im) of this colour and spin
+    const uint2 q = reinterpret_cast<const uint2 *>(base + (size_t)(k >> 2) * f.vh)[(k >> 1) & 1];
+    p[sp] = CP{unpack_word(f, q.x), unpack_word(f, q.y)};
+  }
+}
+template <class SP>
+__device__ __forceinline__ void store_colour(const SP &f, int P, int i, int t, const CP o[4], float2 inv) {
+  uint4 *base = f.d + (size_t)P * 6 * f.vh + i;
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp) {
+    const int k = 6 * sp + 2 * t;
+    unsigned wr, wi;
+    if constexpr (std::is_same<SP, F16P>::value) {
+      wr = f2h(M2(o[sp].re, inv));
+      wi = f2h(M2(o[sp].im, inv));
+    } else {
+      wr = f2b(o[sp].re);
+      wi = f2b(o[sp].im);
+    }
+    reinterpret_cast<uint2 *>(base + (size_t)(k >> 2) * f.vh)[(k >> 1) & 1] = make_uint2(wr, wi);
+  }
+}
+
+// spin projection (1 + SIGMA gamma_mu) of one colour (cf. project_pair)
+template <int MU, int SIGMA>
+__device__ __forceinline__ void project_colour(const CP p[4], CP &h0, CP &h1) {
+  if (MU == 0) {
+    h0 = cp_addi<SIGMA>(p[0], p[3]);
+    h1 = cp_addi<SIGMA>(p[1], p[2]);
+  } else if (MU == 1) {
+    h0 = cp_addpm<-SIGMA>(p[0], p[3]);
+    h1 = cp_addpm<SIGMA>(p[1], p[2]);
+  } else if (MU == 2) {
+    h0 = cp_addi<SIGMA>(p[0], p[2]);
+    h1 = cp_addi<-SIGMA>(p[1], p[3]);
+  } else {
+    h0 = cp_addpm<SIGMA>(p[0], p[2]);
+    h1 = cp_addpm<SIGMA>(p[1], p[3]);
+  }
+}
+// spin reconstruction of one colour (cf. su3_accum_pair)
+template <int MU, int SIGMA>
+__device__ __forceinline__ void accum_colour(CP acc[4], const CP &x0, const CP &x1, float2 n) {
+  const float2 nn = make_float2(-n.x, -n.y);
+  acc[0] = cp_fma_pm<1>(acc[0], x0, n, nn);
+  acc[1] = cp_fma_pm<1>(acc[1], x1, n, nn);
+  if (MU == 0) {
+    acc[2] = cp_fma_i<-SIGMA>(acc[2], x1, n, nn);
+    acc[3] = cp_fma_i<-SIGMA>(acc[3], x0, n, nn);
+  } else if (MU == 1) {
+    acc[2] = cp_fma_pm<SIGMA>(acc[2], x1, n, nn);
+    acc[3] = cp_fma_pm<-SIGMA>(acc[3], x0, n, nn);
+  } else if (MU == 2) {
+    acc[2] = cp_fma_i<-SIGMA>(acc[2], x0, n, nn);
+    acc[3] = cp_fma_i<SIGMA>(acc[3], x1, n, nn);
+  } else {
+    acc[2] = cp_fma_pm<SIGMA>(acc[2], x0, n, nn);
+    acc[3] = cp_fma_pm<SIGMA>(acc[3], x1, n, nn);
+  }
+}
+
+// raw operands of one neighbour, loaded before any arithmetic so that all eight
+// neighbours' loads of a site are in flight together
+struct MmaIn {
+  uint2 w[4];  // words (Re, Im) of colour t, spins 0..3
+  float2 n;    // member norms (with the time-boundary sign)
+  float2 u;    // link entry for this lane (forward U[a][c], backward U[c][a])
+};
+
+template <class SP>
+__device__ __forceinline__ void mma_load(const SP &in, int P, bool act, int nidx, bool flip, const float2 *lk,
+                                         bool lk_ok, int t, MmaIn &r) {
+  if (act) {
+    const uint4 *base = in.d + (size_t)P * 6 * in.vh + nidx;
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) {
+      const int k = 6 * sp + 2 * t;
+      r.w[sp] = reinterpret_cast<const uint2 *>(base + (size_t)(k >> 2) * in.vh)[(k >> 1) & 1];
+    }
+    r.n = read_norm(in, P, nidx);
+    if (flip) r.n = make_float2(-r.n.x, -r.n.y);
+  } else {
+#pragma unroll
+    for (int sp = 0; sp < 4; ++sp) r.w[sp] = make_uint2(0u, 0u);
+    r.n = make_float2(0.f, 0.f);
+  }
+  r.u = lk_ok ? *lk : make_float2(0.f, 0.f);
+}
+
+// project, two MMAs (h0, h1), reconstruct into acc; SIGMA = -1 forward, +1 backward
+template <int MU, int SIGMA, class SP>
+__device__ __forceinline__ void mma_compute(const SP &in, const MmaIn &r, int g4, CP acc[4]) {
+  CP p[4];
+#pragma unroll
+  for (int sp = 0; sp < 4; ++sp) p[sp] = CP{unpack_word(in, r.w[sp].x), unpack_word(in, r.w[sp].y)};
+  CP h0, h1;
+  project_colour<MU, SIGMA>(p, h0, h1);
+  // B fragment: lane (g4, t) holds B[k = Re c_t][n = g4] and B[k = Im c_t][n = g4] of the
+  // real form of M = U (forward) or U^+ (backward; the lane loaded U[c][a], M[a][c] = conj)
+  const float ur = r.u.x, ui = SIGMA < 0 ? r.u.y : -r.u.y;
+  unsigned b0, b1;
+  if ((g4 & 1) == 0) {  // output Re a: (Re M, -Im M)
+    b0 = __float_as_uint(ur);
+    b1 = __float_as_uint(-ui);
+  } else {  // output Im a: (Im M, Re M)
+    b0 = __float_as_uint(ui);
+    b1 = __float_as_uint(ur);
+  }
+  unsigned a[4];
+  float d0[4], d1[4];
+  a[0] = tf32_bits(h0.re.x);
+  a[1] = tf32_bits(h0.re.y);
+  a[2] = tf32_bits(h0.im.x);
+  a[3] = tf32_bits(h0.im.y);
+  mma_tf32(d0, a, b0, b1);
+  a[0] = tf32_bits(h1.re.x);
+  a[1] = tf32_bits(h1.re.y);
+  a[2] = tf32_bits(h1.im.x);
+  a[3] = tf32_bits(h1.im.y);
+  mma_tf32(d1, a, b0, b1);
+  const CP x0{make_float2(d0[0], d0[2]), make_float2(d0[1], d0[3])};
+  const CP x1{make_float2(d1[0], d1[2]), make_float2(d1[1], d1[3])};
+  accum_colour<MU, SIGMA>(acc, x0, x1, r.n);
+}
+
+// all eight neighbours of site i (coordinates c) for this lane's pair and colour
+template <class SP>
+__device__ __forceinline__ void hop_mma_site(const Geom &g, int p_out, const int c[4], int i, const SP &in, int P,
+                                             bool act, const float2 *links, int g4, int t, CP acc[4]) {
+  const bool lk_ok = g4 < 6 && t < 3;
+  const int a = g4 >> 1;
+  MmaIn r[8];  // [2 mu + (0 forward, 1 backward)]
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    int cf[4] = {c[0], c[1], c[2], c[3]}, cb[4] = {c[0], c[1], c[2], c[3]};
+    cf[mu] = (c[mu] + 1 == g.L[mu]) ? 0 : c[mu] + 1;
+    cb[mu] = (c[mu] == 0) ? g.L[mu] - 1 : c[mu] - 1;
+    const int nf = site_of(g, cf) >> 1, nb = site_of(g, cb) >> 1;
+    const float2 *lf = links + ((size_t)(p_out * 4 + mu) * g.Vh + i) * 9 + (lk_ok ? a * 3 + t : 0);
+    const float2 *lb = links + ((size_t)((1 - p_out) * 4 + mu) * g.Vh + nb) * 9 + (lk_ok ? t * 3 + a : 0);
+    mma_load(in, P, act, nf, mu == 3 && c[3] == g.L[3] - 1, lf, lk_ok, t, r[2 * mu]);
+    mma_load(in, P, act, nb, mu == 3 && c[3] == 0, lb, lk_ok, t, r[2 * mu + 1]);
+  }
+  mma_compute<0, -1>(in, r[0], g4, acc);
+  mma_compute<0, 1>(in, r[1], g4, acc);
+  mma_compute<1, -1>(in, r[2], g4, acc);
+  mma_compute<1, 1>(in, r[3], g4, acc);
+  mma_compute<2, -1>(in, r[4], g4, acc);
+  mma_compute<2, 1>(in, r[5], g4, acc);
+  mma_compute<3, -1>(in, r[6], g4, acc);
+  mma_compute<3, 1>(in, r[7], g4, acc);
+}
+
+constexpr int MMA_SITES = 128;  // sites per work item (4 warps x 32 sites), = ST
+constexpr int MMA_MINB = 3;     // resident blocks per SM the register budget is cut for
+// out = cA A + cH (H in) at parity p_out for groups of 8 active pairs, with the
+// same epilogues and partial layout as k_hop_pair (one partial per member and
+// block of ST sites).
+template <class SP, int EPI>
+__global__ void __launch_bounds__(128, MMA_MINB) k_hop_mma(Geom g, int p_out, const float2 *links, SP in, SP out, SP A,
+                                                    SP B, float cA, float cH, const int *plist, const int *pcount,
+                                                    D4S *part, int nbx, int nrhs, unsigned long long *prof) {
+  const int count = *pcount;
+  const int n_items = (count + 7) / 8 * nbx;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g4 = lane >> 2, t = lane & 3;
+  const float2 cA2 = make_float2(cA, cA), cH2 = make_float2(cH, cH);
+  __shared__ float4 red[4][8][2];  // [warp][pair][member] (re, im, |.|^2, 0)
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int j = (w / nbx) * 8 + g4, sb = w % nbx;
+    const bool valid = j < count;
+    const int P = valid ? plist[j] : 0;
+    const bool act = valid && t < 3;
+    if (prof && valid && t == 0 && warp == 0)
+      atomicAdd(prof + EPI, (unsigned long long)min(MMA_SITES, g.Vh - sb * MMA_SITES) * (2 * P + 1 < nrhs ? 2 : 1));
+    float2 sre = make_float2(0.f, 0.f), sim = sre, snn = sre;
+    for (int k = 0; k < 32; ++k) {
+      const int i = sb * MMA_SITES + warp * 32 + k;  // the same for the whole warp
+      if (i >= g.Vh) break;
+      int c[4];
+      coords_of(g, p_out, i, c);
+      CP acc[4];
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp) acc[sp] = CP{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      hop_mma_site(g, p_out, c, i, in, P, act, links, g4, t, acc);
+      CP o[4], av[4];
+#pragma unroll
+      for (int sp = 0; sp < 4; ++sp) o[sp] = CP{M2(acc[sp].re, cH2), M2(acc[sp].im, cH2)};
+      if (EPI != EPI_PLAIN) {
+        if (act) {
+          load_colour(A, P, i, t, av);
+          const float2 an = read_norm(A, P, i);
+#pragma unroll
+          for (int sp = 0; sp < 4; ++sp) av[sp] = CP{M2(av[sp].re, an), M2(av[sp].im, an)};
+        } else {
+#pragma unroll
+          for (int sp = 0; sp < 4; ++sp) av[sp] = CP{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        }
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) o[sp] = CP{F2(cA2, av[sp].re, o[sp].re), F2(cA2, av[sp].im, o[sp].im)};
+      }
+      // encode and store (FP16: the site norm is the largest |real| over the three colour lanes)
+      float2 inv = make_float2(1.f, 1.f);
+      if constexpr (std::is_same<SP, F16P>::value) {
+        float2 m = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) {
+          m.x = fmaxf(m.x, fmaxf(fabsf(o[sp].re.x), fabsf(o[sp].im.x)));
+          m.y = fmaxf(m.y, fmaxf(fabsf(o[sp].re.y), fabsf(o[sp].im.y)));
+        }
+        m.x = fmaxf(m.x, __shfl_xor_sync(0xffffffffu, m.x, 1));
+        m.y = fmaxf(m.y, __shfl_xor_sync(0xffffffffu, m.y, 1));
+        m.x = fmaxf(m.x, __shfl_xor_sync(0xffffffffu, m.x, 2));
+        m.y = fmaxf(m.y, __shfl_xor_sync(0xffffffffu, m.y, 2));
+        inv = make_float2(m.x > 0.f ? 1.f / m.x : 0.f, m.y > 0.f ? 1.f / m.y : 0.f);
+        if (valid && t == 0) write_norm(out, P, i, m);
+      }
+      if (act) store_colour(out, P, i, t, o, inv);
+      if (EPI == EPI_DOTR && act) {  // <B, out>
+        CP bv[4];
+        load_colour(B, P, i, t, bv);
+        const float2 bn = read_norm(B, P, i);
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) {
+          const float2 br = M2(bv[sp].re, bn), bi = M2(bv[sp].im, bn);
+          sre = F2(br, o[sp].re, sre);
+          sre = F2(bi, o[sp].im, sre);
+          sim = F2(br, o[sp].im, sim);
+          sim = F2(make_float2(-bi.x, -bi.y), o[sp].re, sim);
+        }
+      } else if (EPI == EPI_TS && act) {  // <out, A> and |out|^2
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) {
+          sre = F2(o[sp].re, av[sp].re, sre);
+          sre = F2(o[sp].im, av[sp].im, sre);
+          sim = F2(o[sp].re, av[sp].im, sim);
+          sim = F2(make_float2(-o[sp].im.x, -o[sp].im.y), av[sp].re, sim);
+          snn = F2(o[sp].re, o[sp].re, snn);
+          snn = F2(o[sp].im, o[sp].im, snn);
+        }
+      }
+    }
+    if (EPI == EPI_DOTR || EPI == EPI_TS) {
+      // fixed-order reduction: colour lanes, then the four warps
+#pragma unroll
+      for (int o = 1; o <= 2; o <<= 1) {
+        sre.x += __shfl_xor_sync(0xffffffffu, sre.x, o);
+        sre.y += __shfl_xor_sync(0xffffffffu, sre.y, o);
+        sim.x += __shfl_xor_sync(0xffffffffu, sim.x, o);
+        sim.y += __shfl_xor_sync(0xffffffffu, sim.y, o);
+        snn.x += __shfl_xor_sync(0xffffffffu, snn.x, o);
+        snn.y += __shfl_xor_sync(0xffffffffu, snn.y, o);
+      }
+      if (t == 0) {
+        red[warp][g4][0] = make_float4(sre.x, sim.x, snn.x, 0.f);
+        red[warp][g4][1] = make_float4(sre.y, sim.y, snn.y, 0.f);
+      }
+      __syncthreads();
+      if (threadIdx.x < 16) {
+        const int pg = threadIdx.x >> 1, mem = threadIdx.x & 1;
+        const int jj = (w / nbx) * 8 + pg;
+        if (jj < count) {
+          double re = 0.0, im = 0.0, nn = 0.0;
+#pragma unroll
+          for (int ww = 0; ww < 4; ++ww) {
+            re += red[ww][pg][mem].x;
+            im += red[ww][pg][mem].y;
+            nn += red[ww][pg][mem].z;
+          }
+          part[(size_t)(2 * plist[jj] + mem) * nbx + sb] = EPI == EPI_DOTR ? D4S{re, im, 0, 0} : D4S{re, im, 0, nn};
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Compiled variants of the pair hopping term, picked by the autotuner:
+//   0: one pair per block, registers as the compiler wants
+//   1: one pair per block, registers capped for four 128-thread blocks per SM
+//   2: two pairs per block (256 threads), the same register cap
+//   3: four pairs per block (512 threads), the same register cap
+//   4: SU(3) products on the tensor cores (k_hop_mma)
+constexpr int HOP_VARIANTS = 5;
+template <class SP, int EPI>
+static void launch_hop_pair(int variant, int G, cudaStream_t q, const lqcd_ctx *ctx, Geom g, int p_out, SP in, SP out,
+                            SP A, SP B, float cA, float cH, const int *plist, const int *pcount, D4S *part, int nbx,
+                            int nrhs, unsigned long long *prof) {
+  const uint4 *L16 = ctx->U16;
+  switch (variant) {
+    case 1:
+      KL k_hop_pair<SP, EPI, 4, 1><<<G, ST, 0, q>>>(g, p_out, L16, in, out, A, B, cA, cH, plist, pcount, part, nbx,
+                                                     nrhs, prof);
+      break;
+    case 2:
+      KL k_hop_pair<SP, EPI, 2, 2><<<G, 2 * ST, 0, q>>>(g, p_out, L16, in, out, A, B, cA, cH, plist, pcount, part, nbx,
+                                                         nrhs, prof);
+      break;
+    case 3:
+      KL k_hop_pair<SP, EPI, 1, 4><<<G, 4 * ST, 0, q>>>(g, p_out, L16, in, out, A, B, cA, cH, plist, pcount, part, nbx,
+                                                         nrhs, prof);
+      break;
+    case 4:
+      KL k_hop_mma<SP, EPI><<<G, 128, 0, q>>>(g, p_out, ctx->Utf, in, out, A, B, cA, cH, plist, pcount, part, nbx, nrhs,
+                                              prof);
+      break;
+    default:
+      KL k_hop_pair<SP, EPI, 1, 1><<<G, ST, 0, q>>>(g, p_out, L16, in, out, A, B, cA, cH, plist, pcount, part, nbx,
+                                                     nrhs, prof);
+      break;
+  }
 }
 
 // ============================================================ BLAS kernels
@@ -1262,12 +1643,17 @@ template <> BF16P pair_field<BF16P>(SloppyState *st, int f, int vh) {
   return BF16P{st->sd + (size_t)f * pairs * 6 * vh, vh};
 }
 
-// autotuned launch choice per (nrhs, precision): code = blocks_per_sm * 10 + hop variant
+// autotuned launch choice per (nrhs, precision): code = blocks_per_sm * 10 + hop variant;
+// LQCD_HOP_VARIANT=0..4 in the environment overrides the variant (for tests)
 static int tuned_code(const lqcd_ctx *ctx, int nrhs, int precision) {
   long long key = (long long)nrhs * 8 + precision;
+  int code = 80;
   for (auto &kv : ctx->tuned)
-    if (kv.first == key) return kv.second;
-  return 80;
+    if (kv.first == key) code = kv.second;
+  const char *force = getenv("LQCD_HOP_VARIANT");
+  if (force && force[0] >= '0' && force[0] < '0' + HOP_VARIANTS && force[1] == 0)
+    code = code / 10 * 10 + (force[0] - '0');
+  return code;
 }
 
 // One lattice's mixed-precision solve as a resumable state machine:
@@ -1428,7 +1814,6 @@ struct MixedRun {
   // Enqueue k inner iterations on stream q (RHS that finish simply drop out of the lists).
   void launch_iters(cudaStream_t q, int k) {
     int *counts = sb.counts;
-    const uint4 *L16 = ctx->U16;
     const float4 *L32 = ctx->U32;
     unsigned long long *prof = ctx->prof_on ? ctx->d_prof : nullptr;
     if (ctx->prof_on) ctx->prof_prec = p.precision;
@@ -1450,21 +1835,21 @@ struct MixedRun {
     for (int it = 0; it < k; ++it) {
       KL k_pair_p<SP><<<G, ST, 0, q>>>(vh, sb.sc, r, rhat, pp, v, sb.act_pairs, counts, nbx);
       ev_begin();
-      launch_hop_pair<SP, EPI_PLAIN>(hop_variant, G, q, g, 1, L16, pp, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
+      launch_hop_pair<SP, EPI_PLAIN>(hop_variant, G, q, ctx, g, 1, pp, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
                                                     nullptr, nbx, nrhs, prof);
       ev_end();
       ev_begin();
-      launch_hop_pair<SP, EPI_DOTR>(hop_variant, G, q, g, 0, L16, tmp, v, pp, rhat, 1.f, -k2, sb.act_pairs, counts,
+      launch_hop_pair<SP, EPI_DOTR>(hop_variant, G, q, ctx, g, 0, tmp, v, pp, rhat, 1.f, -k2, sb.act_pairs, counts,
                                                    sb.part, nbx, nrhs, prof);
       ev_end();
       KL k_sfin_alpha<<<npairs, 64, 0, q>>>(sb.sc, sb.flags, sb.act_pairs, counts, sb.part, nbx, nrhs);
       KL k_pair_s<SP><<<G, ST, 0, q>>>(vh, sb.sc, r, v, s, sb.act_pairs, counts, nbx);
       ev_begin();
-      launch_hop_pair<SP, EPI_PLAIN>(hop_variant, G, q, g, 1, L16, s, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
+      launch_hop_pair<SP, EPI_PLAIN>(hop_variant, G, q, ctx, g, 1, s, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
                                                     nullptr, nbx, nrhs, prof);
       ev_end();
       ev_begin();
-      launch_hop_pair<SP, EPI_TS>(hop_variant, G, q, g, 0, L16, tmp, t, s, s, 1.f, -k2, sb.act_pairs, counts, sb.part,
+      launch_hop_pair<SP, EPI_TS>(hop_variant, G, q, ctx, g, 0, tmp, t, s, s, 1.f, -k2, sb.act_pairs, counts, sb.part,
                                                  nbx, nrhs, prof);
       ev_end();
       KL k_sfin_omega<<<npairs, 64, 0, q>>>(sb.sc, sb.flags, sb.act_pairs, counts, sb.part, nbx, nrhs);
@@ -1808,19 +2193,20 @@ static int autotune_hop(lqcd_ctx *ctx, int nrhs, int precision, int *best) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   const int cand[4] = {2, 4, 8, 16};
+  const bool verbose = getenv("LQCD_AUTOTUNE_VERBOSE") != nullptr;  // timings to stderr
   float best_ms = 1e30f;
   int best_code = 80;
   const int nsm = num_sms(ctx->device);
-  for (int variant = 0; variant < 2; ++variant)
+  for (int variant = 0; variant < HOP_VARIANTS; ++variant)
     for (int c : cand) {
       const int G = nsm * c;
       for (int rep = 0; rep < 2; ++rep)  // warm-up
-        launch_hop_pair<SP, EPI_PLAIN>(variant, G, (cudaStream_t)0, g, 1, (const uint4 *)ctx->U16, in, out, out,
+        launch_hop_pair<SP, EPI_PLAIN>(variant, G, (cudaStream_t)0, ctx, g, 1, in, out, out,
                                        out, 0.f, 1.f, (const int *)sb.act_pairs, (const int *)sb.counts,
                                        (D4S *)nullptr, nbx, nrhs, (unsigned long long *)nullptr);
       cudaEventRecord(e0);
       for (int rep = 0; rep < 5; ++rep)
-        launch_hop_pair<SP, EPI_PLAIN>(variant, G, (cudaStream_t)0, g, 1, (const uint4 *)ctx->U16, in, out, out,
+        launch_hop_pair<SP, EPI_PLAIN>(variant, G, (cudaStream_t)0, ctx, g, 1, in, out, out,
                                        out, 0.f, 1.f, (const int *)sb.act_pairs, (const int *)sb.counts,
                                        (D4S *)nullptr, nbx, nrhs, (unsigned long long *)nullptr);
       cudaEventRecord(e1);
@@ -1832,6 +2218,8 @@ static int autotune_hop(lqcd_ctx *ctx, int nrhs, int precision, int *best) {
       }
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
+      if (verbose) fprintf(stderr, "lqcd_autotune: nrhs %d variant %d blocks/SM %d: %.4f ms per hop\n", nrhs, variant, c,
+                           ms / 5);
       if (ms < best_ms) {
         best_ms = ms;
         best_code = c * 10 + variant;

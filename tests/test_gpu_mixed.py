@@ -15,6 +15,14 @@ pytestmark = pytest.mark.gpu
 PRECS = ["fp16", "bf16"]
 
 
+@pytest.fixture(autouse=True, params=["0", "1", "4"], ids=["hop-ffma2", "hop-ffma2-capped", "hop-mma"])
+def hop_variant(request, monkeypatch):
+    """Every test here runs with the FP32-unit pair hop (uncapped / register-capped)
+    and with the tensor-core pair hop (LQCD_HOP_VARIANT is read at solve setup)."""
+    monkeypatch.setenv("LQCD_HOP_VARIANT", request.param)
+    return request.param
+
+
 def _prec(L, name):
     return {"fp16": L.LQCD_PREC_MIXED_FP16, "bf16": L.LQCD_PREC_MIXED_BF16}[name]
 
