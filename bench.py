@@ -58,9 +58,11 @@ def _peaks():
 # FP32 ALU peak of the hopping term: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# DRAM bytes per hopping-term launch from the ncu capture summarised in
-# profiles/hop_sloppy_fp16_16x16x16x32.md (None until captured for this kernel)
-HOP_DRAM_BYTES_PER_SITE_RHS = None
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per output (site, RHS) of
+# k_hop_pair<BF16P, *, 4, 1>, from one ncu --set full capture on 16^3x32 with 48 RHS
+# (pair fields larger than L2): PLAIN 145.6, DOTR 285.8, TS 208.7; the solver runs them
+# 2 : 1 : 1 over the same pairs.  Scaled to a launch by the (site, RHS) it processes.
+HOP_DRAM_BYTES_PER_SITE_RHS = (2 * 145.6 + 285.8 + 208.7) / 4
 
 
 class Clocks:
@@ -198,7 +200,7 @@ def _event_ms(fn, stream, reps=10, warm=3):
     return a.elapsed_time(b) / reps
 
 
-def next_rows(L, h, per_site, dev, stream, with_oracle):
+def next_rows(L, h, per_site, dev, stream, with_oracle, per_site_rhs=384):
     """Times the momentum projection, the disconnected correlator and spatially
     diluted noise on the bench lattice (after the timed step; not part of it),
     with the oracle timed beside them on the same inputs."""
@@ -221,7 +223,7 @@ def next_rows(L, h, per_site, dev, stream, with_oracle):
     D = torch.empty((lt, 6, 6), dtype=torch.complex128, device=dev)
     ms_c = _event_ms(lambda: L.lqcd_disconnected_correlator(lp, lm, v3, D, True), stream)
     out["correlator"] = {"n_vec": nvec, "lt": lt, "ms": ms_c}
-    nz = 384
+    nz = min(384, per_site_rhs)
     buf = torch.empty((nz, V, 4, 3), dtype=torch.complex128, device=dev)
     for name, scheme in (("tsc", L.LQCD_DILUTE_TSC), ("tsc_eo", L.LQCD_DILUTE_TSC | L.LQCD_DILUTE_EO),
                          ("tsc_cube", L.LQCD_DILUTE_TSC | L.LQCD_DILUTE_CUBE)):
@@ -270,7 +272,7 @@ def run_ours(args, rank, world, local_rank):
     prec = L.LQCD_PREC_MIXED_FP16 if args.prec == "fp16" else L.LQCD_PREC_MIXED_BF16
     params = L.solver_params(tol=TOL, precision=prec, delta=args.delta)
     # launch-shape choice (grid size, hop register budget) measured once, outside the timed region
-    blocks_per_sm = L.lqcd_autotune(h, nrhs, prec)
+    blocks_per_sm, hop_variant = L.lqcd_autotune(h, nrhs, prec, with_variant=True)
     src = torch.empty((nrhs, V, 4, 3), dtype=torch.complex128, device=dev)
     x = torch.empty_like(src)
     per_site = torch.zeros((V, 6), dtype=torch.complex128, device=dev)
@@ -351,7 +353,7 @@ def run_ours(args, rank, world, local_rank):
     rc, st64 = L.lqcd_solve_batch(h, src[:n64].contiguous(), xs, p64)
     torch.cuda.synchronize(dev)
     fp64_rate = n64 / (time.perf_counter() - t0)
-    extras = next_rows(L, h, per_site, dev, stream, not args.no_cpu)
+    extras = next_rows(L, h, per_site, dev, stream, not args.no_cpu, nrhs)
     L.lqcd_destroy(h)
 
     # ---------------------------------------------------------- roofline
@@ -359,7 +361,9 @@ def run_ours(args, rank, world, local_rank):
     hop_s = prof["hop_ms"] / 1e3
     achieved = prof["hop_bytes"] / hop_s / 1e9 if hop_s > 0 else 0.0
     traffic = None
-    if HOP_DRAM_BYTES_PER_SITE_RHS is not None and prof["hop_launches"] > 0:
+    # the captured counters describe the BF16 kernel of variant 1 only
+    if HOP_DRAM_BYTES_PER_SITE_RHS is not None and prof["hop_launches"] > 0 and args.prec == "bf16" \
+            and hop_variant == 1:
         traffic = HOP_DRAM_BYTES_PER_SITE_RHS * prof["hop_site_rhs"] / prof["hop_launches"]
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -391,7 +395,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD, "global_batch": nrhs * world, "lattice": "16x16x16x32",
                    "precision": args.prec, "parallelism": f"replicas x{world}",
                    "inputs_vs_l2": "working set ~30 GB per step >> 129 MB L2 (no flush needed)",
-                   "plaquette": plaq, "blocks_per_sm": blocks_per_sm},
+                   "plaquette": plaq, "blocks_per_sm": blocks_per_sm, "hop_variant": hop_variant},
         "mixed_vs_plain_fp64": value / world / fp64_rate,
         "fp64_plain": {"value": fp64_rate, "unit": "RHS solves/s", "sample_rhs": n64,
                        "iterations": [s["iterations"] for s in st64]},

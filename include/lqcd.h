@@ -181,11 +181,15 @@ int lqcd_batch_run(lqcd_batch *batch, const lqcd_solver_params *params, lqcd_sol
 int lqcd_batch_destroy(lqcd_batch *batch);
 
 /* Autotuner: time the reduced-precision hopping term for nrhs right-hand
- * sides of `precision` on this context over the candidate launch grids
- * (2, 4, 8, 16 blocks of 128 sites per SM) and keep the fastest for later
- * solves of that (nrhs, precision); *best_blocks_per_sm (host, may be NULL)
- * receives it.  Needs a gauge field.  Synchronises the device. */
-int lqcd_autotune(lqcd_ctx *ctx, int nrhs, int precision, int *best_blocks_per_sm);
+ * sides of `precision` on this context over its compiled variants (register
+ * budget, pairs per block, FP32-unit or tensor-core SU(3) products) and the
+ * candidate launch grids (2, 4, 8, 16 blocks per SM), and keep the fastest for
+ * later solves of that (nrhs, precision).  *best_blocks_per_sm and
+ * *best_hop_variant (host, each may be NULL) receive the choice.  Needs a
+ * gauge field.  Synchronises the device.  With LQCD_AUTOTUNE_VERBOSE set in the
+ * environment every timing is printed to stderr; LQCD_HOP_VARIANT=<digit>
+ * overrides the variant the solves use (for tests and profiling). */
+int lqcd_autotune(lqcd_ctx *ctx, int nrhs, int precision, int *best_blocks_per_sm, int *best_hop_variant);
 
 /* Point sources e_{x,spin,colour} (Sec. II: exact all-to-all propagator from
  * one inversion per site, spin and colour).  sites: host array of n_sites

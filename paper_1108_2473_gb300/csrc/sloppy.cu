@@ -2174,7 +2174,7 @@ int lqcd_batch_run(lqcd_batch *batch, const lqcd_solver_params *params, lqcd_sol
 namespace lqcd {
 
 template <class SP>
-static int autotune_hop(lqcd_ctx *ctx, int nrhs, int precision, int *best) {
+static int autotune_hop(lqcd_ctx *ctx, int nrhs, int precision, int *best, int *best_variant) {
   int rc = sloppy_alloc(ctx, nrhs);
   if (rc) return rc;
   SloppyState *ss = ctx->sloppy;
@@ -2236,17 +2236,21 @@ static int autotune_hop(lqcd_ctx *ctx, int nrhs, int precision, int *best) {
     }
   if (!found) ctx->tuned.push_back({key, best_code});
   if (best) *best = best_code / 10;
+  if (best_variant) *best_variant = best_code % 10;
   return LQCD_OK;
 }
 
 }  // namespace lqcd
 
-extern "C" int lqcd_autotune(lqcd_ctx *ctx, int nrhs, int precision, int *best_blocks_per_sm) {
+extern "C" int lqcd_autotune(lqcd_ctx *ctx, int nrhs, int precision, int *best_blocks_per_sm,
+                             int *best_hop_variant) {
   if (!ctx || nrhs <= 0 || nrhs > 4096) return set_error(ctx, LQCD_ERR_INVALID, "lqcd_autotune: bad argument");
   if (!ctx->have_gauge || !ctx->gauge_su3) return set_error(ctx, LQCD_ERR_NO_GAUGE, "lqcd_autotune: needs an SU(3) gauge field");
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
-  if (precision == LQCD_PREC_MIXED_FP16) return autotune_hop<F16P>(ctx, nrhs, precision, best_blocks_per_sm);
-  if (precision == LQCD_PREC_MIXED_BF16) return autotune_hop<BF16P>(ctx, nrhs, precision, best_blocks_per_sm);
+  if (precision == LQCD_PREC_MIXED_FP16)
+    return autotune_hop<F16P>(ctx, nrhs, precision, best_blocks_per_sm, best_hop_variant);
+  if (precision == LQCD_PREC_MIXED_BF16)
+    return autotune_hop<BF16P>(ctx, nrhs, precision, best_blocks_per_sm, best_hop_variant);
   return set_error(ctx, LQCD_ERR_INVALID, "lqcd_autotune: only the mixed-precision paths are tuned");
 }

@@ -111,7 +111,7 @@ _SIGS = {
     "lqcd_batch_add": (_i, [_vp, _vp, _vp, _vp, _i]),
     "lqcd_batch_run": (_i, [_vp, ctypes.POINTER(lqcd_solver_params), ctypes.POINTER(lqcd_solve_stats), _vp]),
     "lqcd_batch_destroy": (_i, [_vp]),
-    "lqcd_autotune": (_i, [_vp, _i, _i, ctypes.POINTER(_i)]),
+    "lqcd_autotune": (_i, [_vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "lqcd_loops_stochastic": (_i, [_vp, ctypes.POINTER(lqcd_stochastic_params), ctypes.POINTER(lqcd_solver_params),
                                    _vp, _vp, ctypes.POINTER(lqcd_solve_stats), _vp]),
     "lqcd_gradient": (_i, [_vp, _vp, _vp, _i, _vp, _d, ctypes.POINTER(lqcd_solver_params), ctypes.POINTER(_d), _vp,
@@ -357,7 +357,9 @@ def lqcd_batch_destroy(batch):
     return load().lqcd_batch_destroy(batch)
 
 
-def lqcd_autotune(h, nrhs, precision):
+def lqcd_autotune(h, nrhs, precision, with_variant=False):
+    """Tune the hop kernel; returns blocks per SM (and the hop variant if with_variant)."""
     best = ctypes.c_int(0)
-    _check(load().lqcd_autotune(h, int(nrhs), int(precision), ctypes.byref(best)), h)
-    return best.value
+    var = ctypes.c_int(0)
+    _check(load().lqcd_autotune(h, int(nrhs), int(precision), ctypes.byref(best), ctypes.byref(var)), h)
+    return (best.value, var.value) if with_variant else best.value

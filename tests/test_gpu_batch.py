@@ -106,8 +106,11 @@ def test_autotune_keeps_results_bit_identical():
         bd = to_dev(b)
         x0 = torch.empty_like(bd)
         L.lqcd_solve_batch(h, bd, x0, L.solver_params(tol=1e-10, precision=L.LQCD_PREC_MIXED_FP16))
-        best = L.lqcd_autotune(h, 4, L.LQCD_PREC_MIXED_FP16)
-        assert best in (2, 4, 8, 16)
+        best, variant = L.lqcd_autotune(h, 4, L.LQCD_PREC_MIXED_FP16, with_variant=True)
+        assert best in (2, 4, 8, 16) and 0 <= variant <= 4
         x1 = torch.empty_like(bd)
         L.lqcd_solve_batch(h, bd, x1, L.solver_params(tol=1e-10, precision=L.LQCD_PREC_MIXED_FP16))
-        assert torch.equal(x0, x1)
+        if variant < 4:  # the FP32-unit variants differ only in launch shape: same arithmetic
+            assert torch.equal(x0, x1)
+        else:  # tensor-core SU(3) products: a different rounding, the same converged solution
+            assert (x0 - x1).abs().max().item() <= 1e-8 * x0.abs().max().item()
