@@ -223,3 +223,51 @@ def test_solve_with_host_buffers():
         xd = torch.empty((2, 256, 4, 3), dtype=torch.complex128, device="cuda")
         L.lqcd_solve_batch(h, to_dev(b), xd, L.solver_params(tol=1e-11))
         assert torch.equal(xh, xd.cpu())
+
+
+def _golden_rows(name):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    return [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
+
+
+def test_noise_signs_match_golden_philox_words():
+    """GPU noise against stored words of an independent Philox4x64-10 (tests/golden):
+    bits 2k / 2k + 1 of word 0 are the signs of Re / Im of component k."""
+    L_ = __import__("tests._gpu", fromlist=["require_gpu"]).require_gpu()
+    dims = (16, 16, 16, 32)
+    V = int(np.prod(dims))
+    by_vec = {}
+    for r in _golden_rows("philox4x64_words.txt"):
+        seed, stream, ni, site, w0 = (int(v) for v in r[:5])
+        by_vec.setdefault((seed, stream, ni), []).append((site, w0))
+    for (seed, stream, ni), items in by_vec.items():
+        out = torch.empty((1, V, 4, 3), dtype=torch.complex128, device="cuda")
+        L_.lqcd_noise_generate(seed, stream, ni, dims, L_.LQCD_DILUTE_NONE, 0, 1, out)
+        got = out.cpu().numpy().reshape(V, 12)
+        for site, w0 in items:
+            for k in range(12):
+                re_neg, im_neg = (w0 >> (2 * k)) & 1, (w0 >> (2 * k + 1)) & 1
+                assert (got[site, k].real < 0) == bool(re_neg) and (got[site, k].imag < 0) == bool(im_neg)
+                assert abs(abs(got[site, k]) - 1.0) < 1e-15
+
+
+def test_free_field_exact_loops_match_golden_traces():
+    """Point-source FP64 solves of the free field against the closed-form traces (tests/golden)."""
+    for r in _golden_rows("free_field_loops.txt"):
+        dims = tuple(int(v) for v in r[:4])
+        kappa, trace = float(r[4]), float(r[5])
+        V = int(np.prod(dims))
+        with lattice(dims, unit_gauge_field(dims), kappa) as (L, h):
+            sites = [0, V - 1]
+            src = torch.empty((12 * len(sites), V, 4, 3), dtype=torch.complex128, device="cuda")
+            L.lqcd_point_sources(h, sites, src)
+            x = torch.empty_like(src)
+            rc, st = L.lqcd_solve_batch(h, src, x, L.solver_params(tol=1e-13, precision=L.LQCD_PREC_FP64))
+            assert rc == 0
+            per_site = torch.zeros((V, 6), dtype=torch.complex128, device="cuda")
+            L.lqcd_loops_batch(h, src, x, 1.0, per_site, None)
+            got = per_site.cpu().numpy()
+        for s in sites:
+            assert abs(got[s, 0] - trace) < 1e-10
+            assert np.max(np.abs(got[s, 1:])) < 1e-12

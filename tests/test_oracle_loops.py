@@ -276,3 +276,20 @@ def test_disconnected_correlator_identities():
     bias = np.mean(biased.real[0].diagonal() - disconnected_correlator(mu_a[None], mu_a[None], l3,
                                                                         unbiased=False)[0].real.diagonal())
     assert 0.02 < bias < 0.045
+
+
+def _golden_free():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "free_field_loops.txt")
+    rows = [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
+    return [((int(r[0]), int(r[1]), int(r[2]), int(r[3])), float(r[4]), float(r[5])) for r in rows]
+
+
+def test_free_field_golden_traces():
+    """Exact loops of the free field against the stored closed-form traces (tests/golden)."""
+    for dims, kappa, trace in _golden_free():
+        U = unit_gauge_field(dims)
+        L = exact_loops(U, kappa, dims, [(0, 0, 0, 0), (dims[3] - 1, dims[2] - 1, 0, 1)], tol=1e-13)
+        for row in L:
+            assert abs(row[0] - trace) < 1e-10
+            assert np.max(np.abs(row[1:])) < 1e-12

@@ -114,3 +114,21 @@ def test_spatial_dilution_counts():
     assert dilution_count(dims, DIL_EO) == 2
     with pytest.raises(ValueError):
         dilution_count(dims, DIL_EO | DIL_CUBE)
+
+
+def _golden_words():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x64_words.txt")
+    rows = [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
+    return [tuple(int(v) for v in r) for r in rows]
+
+
+def test_philox_golden_words():
+    """Stored words of numpy's independent Philox4x64-10 (tests/golden) for the
+    noise generator's key / counter convention."""
+    rows = _golden_words()
+    assert len(rows) >= 10
+    for seed, stream, ni, site, *w in rows:
+        out = philox4x64_10((np.uint64(site), np.uint64(ni), np.uint64(0), np.uint64(0)),
+                            (np.uint64(seed), np.uint64(stream)))
+        assert [int(o) for o in out] == w
