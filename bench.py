@@ -200,6 +200,15 @@ def _event_ms(fn, stream, reps=10, warm=3):
     return a.elapsed_time(b) / reps
 
 
+def _links_cpu(h, L, dev, V):
+    """The context's links as a CPU array [Lt, Lz, Ly, Lx, 4, 3, 3] (zero APE steps copy them)."""
+    import torch
+    lx, ly, lz, lt = DIMS
+    u = torch.empty(V * 36, dtype=torch.complex128, device=dev)
+    L.lqcd_smear_ape(h, 0.0, 0, u)  # zero steps: copies the context's links
+    return u.cpu().numpy().reshape(lt, lz, ly, lx, 4, 3, 3)
+
+
 def next_rows(L, h, per_site, dev, stream, with_oracle, per_site_rhs=384):
     """Times the momentum projection, the disconnected correlator and spatially
     diluted noise on the bench lattice (after the timed step; not part of it),
@@ -231,6 +240,25 @@ def next_rows(L, h, per_site, dev, stream, with_oracle, per_site_rhs=384):
         out[f"noise_{name}"] = {"pieces_per_vector": L.lqcd_dilution_pieces(DIMS, scheme), "chunk": nz, "ms": ms_n,
                                 "write_GBps": nz * V * 192 / (ms_n / 1e3) / 1e9}
     del buf
+    # smearing of connected-correlator sources: 12 point sources, APE links, F = (1 + 4 H)^50
+    src12 = torch.empty((12, V, 4, 3), dtype=torch.complex128, device=dev)
+    L.lqcd_point_sources(h, [0], src12)
+    sm12 = torch.empty_like(src12)
+    ms_ape = _event_ms(lambda: L.lqcd_smear_ape(h, 0.5, 20), stream, reps=2, warm=1)
+    ms_g = _event_ms(lambda: L.lqcd_smear_gaussian(h, src12, sm12, 4.0, 50, ape_links=True, normalise=True),
+                     stream, reps=2, warm=1)
+    # FP64: 6 hops x 4 spins x 9 complex multiply-adds (8 flops) per (site, RHS, step)
+    out["smear_gaussian"] = {"rhs": 12, "alpha": 4.0, "steps": 50, "ms": ms_g, "bound": "alu (FP64)",
+                             "fp64_gflops": 12 * V * 50 * 6 * 4 * 9 * 8 / (ms_g / 1e3) / 1e9}
+    out["smear_ape"] = {"alpha": 0.5, "steps": 20, "ms": ms_ape}
+    if with_oracle:
+        from oracle import smear as osm
+        q1 = src12[:1].cpu().numpy().reshape(1, lt, lz, ly, lx, 4, 3)
+        Ucpu = _links_cpu(h, L, dev, V)
+        t0 = time.perf_counter()
+        osm.gaussian_smear(Ucpu, q1, 4.0, 2, True)
+        out["smear_gaussian"]["oracle_ms_per_rhs_step"] = 1e3 * (time.perf_counter() - t0) / 2
+        out["smear_gaussian"]["ms_per_rhs_step"] = ms_g / (12 * 50)
     if with_oracle:
         from oracle import loops as olp
         ps = per_site.cpu().numpy().reshape(lt, lz, ly, lx, 6)
@@ -417,7 +445,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["fp16", "bf16"])
-    ap.add_argument("--delta", type=float, default=0.1, help="reliable-update threshold of the mixed solver")
+    ap.add_argument("--delta", type=float, default=0.05, help="reliable-update threshold of the mixed solver")
     ap.add_argument("--nrhs", type=int, default=12 * DIMS[3], help="diluted sources per step (384 = all)")
     ap.add_argument("--fp64-rhs", type=int, default=4)
     ap.add_argument("--cpu-rhs", type=int, default=16)

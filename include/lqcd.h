@@ -95,7 +95,7 @@ typedef struct {
   int solver;        /* LQCD_SOLVER_*                                               */
   double delta;      /* mixed precision: reliable update when the iterated residual
                         drops below delta * its maximum since the last update;
-                        <= 0 selects 0.1                                            */
+                        <= 0 selects 0.05 (fastest on GB300 at 16^3x32)             */
   int rhs_block;     /* RHS solved together per launch; 0 = automatic (autotuned
                         for mixed precision, 1 for FP64 = the plain solver)         */
   double timeout_ms; /* wall-clock budget of the call; <= 0 = none                  */
@@ -247,6 +247,30 @@ int lqcd_loops_momentum(lqcd_ctx *ctx, const double *per_site, int n_mom, const 
  * volume.  out: [Lt][6][6] complex128 device (overwritten).  No context needed. */
 int lqcd_disconnected_correlator(const double *loops_p, const double *loops_mp, int n_vec, int lt, int l3,
                                  int unbiased, double *out, lqcd_stream_t stream);
+
+/* APE smearing of the spatial links (Sec. III: the links entering the
+ * smearing hopping matrix are APE-smeared; the paper gives neither formula nor
+ * parameters).  n_iter steps of
+ *   U_i'(x) = P[ U_i(x) + alpha sum_{j != i spatial} S_ij(x) ],
+ *   S_ij(x) = U_j(x) U_i(x+j) U_j(x+i)^+ + U_j(x-j)^+ U_i(x-j) U_j(x-j+i),
+ * on the context's gauge field, temporal links unchanged; P = unitary polar
+ * factor divided by the principal cube root of its determinant (FP64).  The
+ * result is kept in the context (for lqcd_smear_gaussian) until the next
+ * lqcd_set_gauge, and copied to out ([V][4][3][3] complex128 device, may be
+ * NULL).  Errors: INVALID (negative n_iter, non-finite alpha, host out),
+ * NO_GAUGE. */
+int lqcd_smear_ape(lqcd_ctx *ctx, double alpha, int n_iter, double *out, lqcd_stream_t stream);
+
+/* Gaussian smearing of quark fields (Sec. III): out = F in with
+ *   F = (1 + alpha H)^n_iter,  (H q)(x) = sum_{i = x,y,z} [ U_i(x) q(x+i) + U_i(x-i)^+ q(x-i) ]
+ * within each time slice, all four spins alike (the paper uses alpha = 4,
+ * n = 50).  ape_links = 1 uses the links of the last lqcd_smear_ape, 0 the
+ * context's links; normalise = 1 divides each factor by (1 + 6 alpha).
+ * in, out: [nrhs][V][4][3] complex128 device, distinct.  FP64.  Errors:
+ * INVALID (in == out, host pointers, ape_links without lqcd_smear_ape),
+ * NO_GAUGE. */
+int lqcd_smear_gaussian(lqcd_ctx *ctx, const double *in, double *out, int nrhs, double alpha, int n_iter,
+                        int ape_links, int normalise, lqcd_stream_t stream);
 
 /* Stochastic loops with dilution and the truncated solver method (Sec. II,
  * Eq. loop stochastic; TSM after Bali, Collins, Schafer):

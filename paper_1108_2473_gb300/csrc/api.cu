@@ -244,6 +244,7 @@ int lqcd_destroy(lqcd_ctx *ctx) {
   cudaFree(ctx->U32);
   cudaFree(ctx->U16);
   cudaFree(ctx->Utf);
+  cudaFree(ctx->Uape);
   cudaFree(ctx->Udf);
   cudaFree(ctx->d_flag);
   cudaFree(ctx->d_prof);
@@ -295,6 +296,7 @@ static int set_gauge_impl(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream, 
   }
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->U64, stage, n64 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   ctx->have_gauge = true;
+  ctx->have_ape = false;  // smeared links belong to the previous field
   ctx->gauge_su3 = !flag;
   int rc = pack_gauge_sloppy(ctx, st);
   if (rc != LQCD_OK) return rc;

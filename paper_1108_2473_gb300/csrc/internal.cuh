@@ -168,6 +168,8 @@ struct lqcd_ctx {
   float4 *Udf = nullptr;      // double-float copy  [V][4][3][3] (hi.re, hi.im, lo.re, lo.im)
   uint4 *U16 = nullptr;       // FP16, all 18 reals, each twice  [2 parity][4 mu][5 uint4][Vh]
   float2 *Utf = nullptr;      // tf32-rounded FP32, [2 parity][4 mu][Vh][3][3] complex (tensor-core hop)
+  double2 *Uape = nullptr;    // APE-smeared copy (spatial links smeared) [V][4][3][3], on first use
+  bool have_ape = false;
   std::vector<lqcd::DevBuf> ws;  // named workspaces, grow-only
   lqcd::SloppyState *sloppy = nullptr;
   std::string err;
@@ -227,7 +229,7 @@ bool is_device_ptr(const void *p);
 enum WsSlot {
   WS_STAGE_IN = 0, WS_STAGE_OUT, WS_STAGE_AUX,
   WS_F64_VECS, WS_F64_SCAL, WS_F64_PART, WS_F64_FULL,
-  WS_LOOP_PART, WS_GRAD, WS_GRAD2,
+  WS_LOOP_PART, WS_GRAD, WS_GRAD2, WS_SMEAR, WS_SMEAR_LINKS,
   WS_COUNT
 };
 

@@ -1676,7 +1676,7 @@ struct MixedRun {
   Geom g;
   int vh = 0, cap = 0, nbx = 0, G = 0, npairs = 0, hop_variant = 0;
   float kappa = 0.f, k2 = 0.f;
-  double delta = 0.1, floor2 = 4e-12;  // (2e-6)^2: inner FP32 target floor, relative to |b_inner|^2
+  double delta = 0.05, floor2 = 4e-12;  // (2e-6)^2: inner FP32 target floor, relative to |b_inner|^2
   SP r, rhat, pp, v, s, t, tmp;
   F32F x32, b32, r32, t32, o32;
   SmallBufs sb;
@@ -1700,7 +1700,7 @@ struct MixedRun {
     G = num_sms(ctx->device) * (tuned_code(ctx, nrhs, p.precision) / 10);
     hop_variant = tuned_code(ctx, nrhs, p.precision) % 10;
     npairs = (nrhs + 1) / 2;
-    delta = p.delta > 0 ? p.delta : 0.1;
+    delta = p.delta > 0 ? p.delta : 0.05;
     r = pair_field<SP>(ss, 0, vh);
     rhat = pair_field<SP>(ss, 1, vh);
     pp = pair_field<SP>(ss, 2, vh);

@@ -83,7 +83,7 @@ def stochastic_params(seed, n_lp, n_hp=0, tol_lp=1e-10, tol_hp=1e-10, dilution=L
     return lqcd_stochastic_params(seed, first_noise, dilution, n_lp, n_hp, tol_lp, tol_hp, chunk)
 
 
-def solver_params(tol=1e-10, max_iter=20000, precision=LQCD_PREC_FP64, solver=LQCD_SOLVER_BICGSTAB, delta=0.1,
+def solver_params(tol=1e-10, max_iter=20000, precision=LQCD_PREC_FP64, solver=LQCD_SOLVER_BICGSTAB, delta=0.05,
                   rhs_block=0, timeout_ms=0.0):
     return lqcd_solver_params(tol, max_iter, precision, solver, delta, rhs_block, timeout_ms)
 
@@ -123,6 +123,8 @@ _SIGS = {
     "lqcd_dilution_pieces": (_i, [ctypes.POINTER(_i), _i]),
     "lqcd_loops_momentum": (_i, [_vp, _vp, _i, ctypes.POINTER(_i), _vp, _vp]),
     "lqcd_disconnected_correlator": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _vp]),
+    "lqcd_smear_ape": (_i, [_vp, _d, _i, _vp, _vp]),
+    "lqcd_smear_gaussian": (_i, [_vp, _vp, _vp, _i, _d, _i, _i, _i, _vp]),
 }
 OPTIONAL_SIGS = {}
 
@@ -265,6 +267,19 @@ def lqcd_disconnected_correlator(loops_p, loops_mp, l3, out, unbiased=True):
     rc = load().lqcd_disconnected_correlator(_ptr(loops_p), _ptr(loops_mp), n, lt, int(l3), int(bool(unbiased)),
                                              _ptr(out), _stream(out))
     return _check(rc, None)
+
+
+def lqcd_smear_ape(h, alpha, n_iter, out=None, stream=None):
+    """APE-smear the context's spatial links (kept for lqcd_smear_gaussian); optional copy to out."""
+    st = stream if (out is None and stream is not None) else _stream(out)
+    return _check(load().lqcd_smear_ape(h, float(alpha), int(n_iter), _ptr(out), st), h)
+
+
+def lqcd_smear_gaussian(h, src, out, alpha=4.0, n_iter=50, ape_links=False, normalise=False):
+    """out = (1 + alpha H)^n_iter src on each time slice (device tensors [n, V, 4, 3])."""
+    rc = load().lqcd_smear_gaussian(h, _ptr(src), _ptr(out), src.shape[0], float(alpha), int(n_iter),
+                                    int(bool(ape_links)), int(bool(normalise)), _stream(out))
+    return _check(rc, h)
 
 
 def lqcd_loops_batch(h, src, sol, weight=1.0, per_site=None, per_t=None):
