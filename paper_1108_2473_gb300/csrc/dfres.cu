@@ -6,8 +6,9 @@
 //   sum:     TwoSum (Knuth; Dekker) for the high parts, low parts added,
 //   product: TwoProduct with an FMA for hi*hi, cross terms added to the low part,
 // everything with the _rn intrinsics, which the compiler never contracts or
-// reorders.  Gauge links, the iterate x and the source b are held as such
-// pairs (split once from FP64); the residual goes out in FP32 (it only seeds
+// reorders.  Gauge links and the iterate x are held as such pairs (the links
+// split once from FP64); the FP64 source b is split where it is read; the
+// residual goes out in FP32 (it only seeds
 // the next inner solve) together with FP64-accumulated norms |r|^2, |b|^2.
 // The rounding error of one evaluation is a few 1e-14 of |x|, far below the
 // 1e-10 residual it certifies (tests compare it with the IEEE FP64 residual).
@@ -23,62 +24,49 @@ __device__ __forceinline__ cdf load_cdf(const float4 *p) {
   float4 q = *p;
   return cdf{dfl{q.x, q.z}, dfl{q.y, q.w}};
 }
-
-template <int MU>
-__device__ __forceinline__ void hop_dir_df(const Geom &g, const int c[4], int s, const float4 *__restrict__ x,
-                                           const float4 *__restrict__ U, cdf acc[4][3]) {
-  cdf ps[4][3], h[2][3], xo[2][3], u[3][3];
-  {  // forward: (1 - gamma_mu) U_mu(x) psi(x + mu)
-    int cn[4] = {c[0], c[1], c[2], c[3]};
-    cn[MU] = (c[MU] + 1 == g.L[MU]) ? 0 : c[MU] + 1;
-    const int sn = site_of(g, cn);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) ps[k / 3][k % 3] = load_cdf(x + (size_t)sn * 12 + k);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) u[k / 3][k % 3] = load_cdf(U + ((size_t)s * 4 + MU) * 9 + k);
-    spin_project<MU, -1>(ps, h);
-    su3_mul<false>(u, h, xo);
-    if (MU == 3 && c[3] == g.L[3] - 1) {
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) xo[a][b] = cdf{-xo[a][b].x, -xo[a][b].y};
-    }
-    spin_accum<MU, -1>(acc, xo);
-  }
-  {  // backward: (1 + gamma_mu) U_mu(x - mu)^+ psi(x - mu)
-    int cn[4] = {c[0], c[1], c[2], c[3]};
-    cn[MU] = (c[MU] == 0) ? g.L[MU] - 1 : c[MU] - 1;
-    const int sn = site_of(g, cn);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) ps[k / 3][k % 3] = load_cdf(x + (size_t)sn * 12 + k);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) u[k / 3][k % 3] = load_cdf(U + ((size_t)sn * 4 + MU) * 9 + k);
-    spin_project<MU, +1>(ps, h);
-    su3_mul<true>(u, h, xo);
-    if (MU == 3 && c[3] == 0) {
-#pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) xo[a][b] = cdf{-xo[a][b].x, -xo[a][b].y};
-    }
-    spin_accum<MU, +1>(acc, xo);
-  }
+// FP64 -> double-float: hi = fl32(v), lo = fl32(v - hi)
+__device__ __forceinline__ cdf split_cdf(double2 v) {
+  const float hx = (float)v.x, hy = (float)v.y;
+  return cdf{dfl{hx, (float)(v.x - (double)hx)}, dfl{hy, (float)(v.y - (double)hy)}};
 }
 
-// One output colour row a of the hop for one direction pair, three threads
-// per site (a = 0, 1, 2): the projection is recomputed by each thread, the
-// SU(3) row and the accumulation are the thread's own.
+// Shared-projection variant: the three threads of a site (lanes base .. base + 2
+// of one warp) each project only their own colour a of the neighbour spinor and
+// fetch the other two colours' half spinors from their neighbours by shuffles.
+__device__ __forceinline__ cdf shfl_cdf(const cdf &v, int src) {
+  return cdf{dfl{__shfl_sync(0xffffffffu, v.x.h, src), __shfl_sync(0xffffffffu, v.x.l, src)},
+             dfl{__shfl_sync(0xffffffffu, v.y.h, src), __shfl_sync(0xffffffffu, v.y.l, src)}};
+}
 template <int MU, int SIGMA, bool DAG>
-__device__ __forceinline__ void hop_row_df(const float4 *__restrict__ xs, const float4 *__restrict__ u, int a,
-                                           float sgn, cdf acc[4]) {
-  cdf ps[4][3], h[2][3];
+__device__ __forceinline__ void hop_row_df_sh(const float4 *__restrict__ xs, const float4 *__restrict__ u, int a,
+                                              int base, bool act, float sgn, cdf acc[4]) {
+  cdf p[4];
 #pragma unroll
-  for (int k = 0; k < 12; ++k) ps[k / 3][k % 3] = load_cdf(xs + k);
-  spin_project<MU, SIGMA>(ps, h);
+  for (int sp = 0; sp < 4; ++sp) p[sp] = act ? load_cdf(xs + sp * 3 + a) : cdf{dfl{0.f, 0.f}, dfl{0.f, 0.f}};
+  cdf h0, h1;  // spin projection of colour a (as spin_project)
+  if (MU == 0) {
+    h0 = caddi(p[0], p[3], SIGMA);
+    h1 = caddi(p[1], p[2], SIGMA);
+  } else if (MU == 1) {
+    h0 = SIGMA > 0 ? csub(p[0], p[3]) : cadd(p[0], p[3]);
+    h1 = SIGMA > 0 ? cadd(p[1], p[2]) : csub(p[1], p[2]);
+  } else if (MU == 2) {
+    h0 = caddi(p[0], p[2], SIGMA);
+    h1 = caddi(p[1], p[3], -SIGMA);
+  } else {
+    h0 = SIGMA > 0 ? cadd(p[0], p[2]) : csub(p[0], p[2]);
+    h1 = SIGMA > 0 ? cadd(p[1], p[3]) : csub(p[1], p[3]);
+  }
+  cdf h[2][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    h[0][b] = shfl_cdf(h0, base + b);
+    h[1][b] = shfl_cdf(h1, base + b);
+  }
   cdf ur[3];
 #pragma unroll
-  for (int b = 0; b < 3; ++b) ur[b] = load_cdf(u + (DAG ? b * 3 + a : a * 3 + b));
+  for (int b = 0; b < 3; ++b)
+    ur[b] = act ? load_cdf(u + (DAG ? b * 3 + a : a * 3 + b)) : cdf{dfl{0.f, 0.f}, dfl{0.f, 0.f}};
   cdf x[2];
 #pragma unroll
   for (int sp = 0; sp < 2; ++sp) {
@@ -87,7 +75,6 @@ __device__ __forceinline__ void hop_row_df(const float4 *__restrict__ xs, const 
     for (int b = 1; b < 3; ++b) t = cadd(t, DAG ? cmulc(ur[b], h[sp][b]) : cmul(ur[b], h[sp][b]));
     x[sp] = sgn < 0.f ? cdf{-t.x, -t.y} : t;
   }
-  // spin reconstruction of spin_accum for colour a
   acc[0] = cadd(acc[0], x[0]);
   acc[1] = cadd(acc[1], x[1]);
   if (MU == 0) {
@@ -106,21 +93,21 @@ __device__ __forceinline__ void hop_row_df(const float4 *__restrict__ xs, const 
 }
 
 template <int MU>
-__device__ __forceinline__ void hop_dir_df3(const Geom &g, const int c[4], int s, int a, const float4 *__restrict__ x,
-                                            const float4 *__restrict__ U, cdf acc[4]) {
+__device__ __forceinline__ void hop_dir_df_sh(const Geom &g, const int c[4], int s, int a, int base, bool act,
+                                              const float4 *__restrict__ x, const float4 *__restrict__ U, cdf acc[4]) {
   {
     int cn[4] = {c[0], c[1], c[2], c[3]};
     cn[MU] = (c[MU] + 1 == g.L[MU]) ? 0 : c[MU] + 1;
     const int sn = site_of(g, cn);
     const float sgn = (MU == 3 && c[3] == g.L[3] - 1) ? -1.f : 1.f;
-    hop_row_df<MU, -1, false>(x + (size_t)sn * 12, U + ((size_t)s * 4 + MU) * 9, a, sgn, acc);
+    hop_row_df_sh<MU, -1, false>(x + (size_t)sn * 12, U + ((size_t)s * 4 + MU) * 9, a, base, act, sgn, acc);
   }
   {
     int cn[4] = {c[0], c[1], c[2], c[3]};
     cn[MU] = (c[MU] == 0) ? g.L[MU] - 1 : c[MU] - 1;
     const int sn = site_of(g, cn);
     const float sgn = (MU == 3 && c[3] == 0) ? -1.f : 1.f;
-    hop_row_df<MU, +1, true>(x + (size_t)sn * 12, U + ((size_t)sn * 4 + MU) * 9, a, sgn, acc);
+    hop_row_df_sh<MU, +1, true>(x + (size_t)sn * 12, U + ((size_t)sn * 4 + MU) * 9, a, base, act, sgn, acc);
   }
 }
 
@@ -128,89 +115,43 @@ struct D4R {
   double a, b, c, d;
 };
 
-// r = b - x + kappa H x at the sites of parity p_out (all canonical: [rhs][V][12]);
-// partials |r|^2 (.c) and |b|^2 (.d) per block at part[rhs][p_out * nblk + block]
-__global__ void __launch_bounds__(128) k_resid_df(Geom g, int p_out, const float4 *__restrict__ U,
-                                                  const float4 *__restrict__ x, const float4 *__restrict__ b,
-                                                  float2 *r, float kh, float kl, D4R *part) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int rhs = blockIdx.y;
-  const size_t stride = (size_t)g.V * 12;
-  float rn = 0.f, bn = 0.f;
-  if (i < g.Vh) {
-    int c[4];
-    coords_of(g, p_out, i, c);
-    const int s = site_of(g, c);
-    cdf acc[4][3];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) acc[a][q] = cdf{dfl{0.f, 0.f}, dfl{0.f, 0.f}};
-    const float4 *xr = x + (size_t)rhs * stride;
-    hop_dir_df<0>(g, c, s, xr, U, acc);
-    hop_dir_df<1>(g, c, s, xr, U, acc);
-    hop_dir_df<2>(g, c, s, xr, U, acc);
-    hop_dir_df<3>(g, c, s, xr, U, acc);
-    const dfl kd{kh, kl};
-    const size_t o = (size_t)rhs * stride + (size_t)s * 12;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      const cdf bk = load_cdf(b + o + k), xk = load_cdf(xr + (size_t)s * 12 + k);
-      const cdf hk = acc[k / 3][k % 3];
-      const dfl re = df_norm((bk.x - xk.x) + kd * df_norm(hk.x));
-      const dfl im = df_norm((bk.y - xk.y) + kd * df_norm(hk.y));
-      const float2 v = make_float2(__fadd_rn(re.h, re.l), __fadd_rn(im.h, im.l));
-      r[o + k] = v;
-      rn = fmaf(v.x, v.x, fmaf(v.y, v.y, rn));
-      bn = fmaf(bk.x.h, bk.x.h, fmaf(bk.y.h, bk.y.h, bn));
-    }
-  }
-  // fixed-order block reduction in FP64
-  __shared__ double sh[2][128];
-  sh[0][threadIdx.x] = rn;
-  sh[1][threadIdx.x] = bn;
-  __syncthreads();
-  for (int w = 64; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
-      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0)
-    part[(size_t)rhs * 2 * gridDim.x + (size_t)p_out * gridDim.x + blockIdx.x] = D4R{0.0, 0.0, sh[0][0], sh[1][0]};
-}
-
-// Three threads per site (one per output colour): r = b - x + kappa H x at the
-// sites of parity p_out; partials as k_resid_df.
-constexpr int DF3_SITES = 64;
-__global__ void __launch_bounds__(3 * DF3_SITES, 4) k_resid_df3(Geom g, int p_out, const float4 *__restrict__ U,
-                                                              const float4 *__restrict__ x,
-                                                              const float4 *__restrict__ b, float2 *r, float kh,
-                                                              float kl, const int *list, D4R *part) {
-  const int i = blockIdx.x * DF3_SITES + threadIdx.x / 3;
-  const int a = threadIdx.x % 3;
+// Three threads per site (one per output colour, sharing the spin projection
+// by shuffles): r = b - x + kappa H x at the sites of parity p_out.  A warp
+// takes 10 sites (lanes 0..29; lanes 30, 31 only take part in the shuffles), a
+// block 6 warps.  Partials |r|^2 (.c) and |b|^2 (.d) per block.
+constexpr int DF3_WARP_SITES = 10;
+constexpr int DF3_WARPS = 6;
+constexpr int DF3_SITES = DF3_WARP_SITES * DF3_WARPS;
+__global__ void __launch_bounds__(32 * DF3_WARPS, 4) k_resid_df3(Geom g, int p_out, const float4 *__restrict__ U,
+                                                               const float4 *__restrict__ x,
+                                                               const double2 *__restrict__ b, float2 *r, float kh,
+                                                               float kl, const int *list, D4R *part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int sl = lane / 3, a = lane - 3 * sl;  // site within the warp, output colour
+  const int i = blockIdx.x * DF3_SITES + warp * DF3_WARP_SITES + sl;
+  const bool act = sl < DF3_WARP_SITES && i < g.Vh;
+  const int base = 3 * sl;
   const int rhs = list[blockIdx.y];
   const size_t stride = (size_t)g.V * 12;
   float rn = 0.f, bn = 0.f;
-  if (i < g.Vh) {
-    int c[4];
-    coords_of(g, p_out, i, c);
-    const int s = site_of(g, c);
-    cdf acc[4];
+  int c[4];
+  coords_of(g, p_out, act ? i : 0, c);
+  const int s = site_of(g, c);
+  cdf acc[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = cdf{dfl{0.f, 0.f}, dfl{0.f, 0.f}};
-    const float4 *xr = x + (size_t)rhs * stride;
-    hop_dir_df3<0>(g, c, s, a, xr, U, acc);
-    hop_dir_df3<1>(g, c, s, a, xr, U, acc);
-    hop_dir_df3<2>(g, c, s, a, xr, U, acc);
-    hop_dir_df3<3>(g, c, s, a, xr, U, acc);
+  for (int q = 0; q < 4; ++q) acc[q] = cdf{dfl{0.f, 0.f}, dfl{0.f, 0.f}};
+  const float4 *xr = x + (size_t)rhs * stride;
+  hop_dir_df_sh<0>(g, c, s, a, base, act, xr, U, acc);
+  hop_dir_df_sh<1>(g, c, s, a, base, act, xr, U, acc);
+  hop_dir_df_sh<2>(g, c, s, a, base, act, xr, U, acc);
+  hop_dir_df_sh<3>(g, c, s, a, base, act, xr, U, acc);
+  if (act) {
     const dfl kd{kh, kl};
     const size_t o = (size_t)rhs * stride + (size_t)s * 12;
 #pragma unroll
     for (int sp = 0; sp < 4; ++sp) {
       const int k = sp * 3 + a;
-      const cdf bk = load_cdf(b + o + k), xk = load_cdf(xr + (size_t)s * 12 + k);
+      const cdf bk = split_cdf(b[o + k]), xk = load_cdf(xr + (size_t)s * 12 + k);
       const dfl re = df_norm((bk.x - xk.x) + kd * df_norm(acc[sp].x));
       const dfl im = df_norm((bk.y - xk.y) + kd * df_norm(acc[sp].y));
       const float2 v = make_float2(__fadd_rn(re.h, re.l), __fadd_rn(im.h, im.l));
@@ -219,7 +160,7 @@ __global__ void __launch_bounds__(3 * DF3_SITES, 4) k_resid_df3(Geom g, int p_ou
       bn = fmaf(bk.x.h, bk.x.h, fmaf(bk.y.h, bk.y.h, bn));
     }
   }
-  __shared__ double sh[2][3 * DF3_SITES];
+  __shared__ double sh[2][32 * DF3_WARPS];
   sh[0][threadIdx.x] = rn;
   sh[1][threadIdx.x] = bn;
   __syncthreads();
@@ -258,28 +199,12 @@ __global__ void k_df_fin(const D4R *part, int nb, double *rr, double *bb) {
   }
 }
 
-// FP64 canonical -> double-float canonical (hi = fl32(v), lo = fl32(v - hi))
-__global__ void k_split_df(const double2 *__restrict__ in, float4 *out, size_t n) {
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-    double2 v = in[k];
-    float hx = (float)v.x, hy = (float)v.y;
-    out[k] = make_float4(hx, hy, (float)(v.x - (double)hx), (float)(v.y - (double)hy));
-  }
-}
-
 // double-float canonical -> FP64 canonical
 __global__ void k_join_df(const float4 *__restrict__ in, double2 *out, size_t n) {
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
     float4 q = in[k];
     out[k] = make_double2((double)q.x + (double)q.z, (double)q.y + (double)q.w);
   }
-}
-
-int df_split(lqcd_ctx *ctx, const double2 *in, float4 *out, size_t n, cudaStream_t st) {
-  unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
-  KL k_split_df<<<blocks, 256, 0, st>>>(in, out, n);
-  LQCD_LAUNCH_CHECK(ctx, "k_split_df");
-  return LQCD_OK;
 }
 
 int df_join(lqcd_ctx *ctx, const float4 *in, double2 *out, size_t n, cudaStream_t st) {
@@ -290,7 +215,7 @@ int df_join(lqcd_ctx *ctx, const float4 *in, double2 *out, size_t n, cudaStream_
 }
 
 // r = b - D x in double-float; per-RHS |r|^2, |b|^2 to the host arrays
-int df_residual(lqcd_ctx *ctx, const float4 *x, const float4 *b, float2 *r, const int *list, int n, double *rr,
+int df_residual(lqcd_ctx *ctx, const float4 *x, const double2 *b, float2 *r, const int *list, int n, double *rr,
                 double *bb, cudaStream_t st) {
   if (n <= 0) return LQCD_OK;
   const Geom &g = ctx->geom;
@@ -310,7 +235,7 @@ int df_residual(lqcd_ctx *ctx, const float4 *x, const float4 *b, float2 *r, cons
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(d_list, list, n * sizeof(int), cudaMemcpyHostToDevice, st));
   const float kh = (float)ctx->kappa, kl = (float)(ctx->kappa - (double)kh);
   for (int p = 0; p < 2; ++p) {
-    KL k_resid_df3<<<dim3(nblk, n), 3 * DF3_SITES, 0, st>>>(g, p, ctx->Udf, x, b, r, kh, kl, d_list, part);
+    KL k_resid_df3<<<dim3(nblk, n), 32 * DF3_WARPS, 0, st>>>(g, p, ctx->Udf, x, b, r, kh, kl, d_list, part);
     LQCD_LAUNCH_CHECK(ctx, "k_resid_df3");
   }
   KL k_df_fin<<<n, 32, 0, st>>>(part, 2 * nblk, d_rr, d_bb);

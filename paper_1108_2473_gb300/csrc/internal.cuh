@@ -237,11 +237,10 @@ enum WsSlot {
 int launch_hop64(lqcd_ctx *ctx, cudaStream_t st, bool dag, bool in_canon, bool out_canon, int p_out,
                  const double2 *in, size_t in_stride, double2 *out, size_t out_stride, const double2 *A, double cA,
                  const double2 *B, double cB, double cH, const int *active, int nrhs);
-int df_split(lqcd_ctx *ctx, const double2 *in, float4 *out, size_t n, cudaStream_t st);
 int df_join(lqcd_ctx *ctx, const float4 *in, double2 *out, size_t n, cudaStream_t st);
 // r = b - D x in double-float for the n right-hand sides list[0..n) (host
 // list); rr, bb (host, indexed by right-hand side) receive |r|^2 and |b|^2
-int df_residual(lqcd_ctx *ctx, const float4 *x, const float4 *b, float2 *r, const int *list, int n, double *rr,
+int df_residual(lqcd_ctx *ctx, const float4 *x, const double2 *b, float2 *r, const int *list, int n, double *rr,
                 double *bb, cudaStream_t st);
 int fp64_true_residual(lqcd_ctx *ctx, const double2 *b, const double2 *x, int nrhs, double *rr, double *bb,
                        cudaStream_t st);

@@ -1530,7 +1530,6 @@ struct SloppyState {
   float2 *sn = nullptr;    // their FP16 norms
   float4 *f32 = nullptr;   // 5 FP32 fields
   float4 *xdf = nullptr;   // the iterate, double-float canonical [cap][V][12]
-  float4 *bdf = nullptr;   // the source, double-float canonical
   float2 *r32 = nullptr;   // residual b - D x, FP32 canonical (seeds the next inner solve)
   char *small = nullptr;
   int *h_counts = nullptr;  // pinned
@@ -1546,7 +1545,6 @@ void sloppy_free(lqcd_ctx *ctx) {
   cudaFree(s->sn);
   cudaFree(s->f32);
   cudaFree(s->xdf);
-  cudaFree(s->bdf);
   cudaFree(s->r32);
   cudaFree(s->small);
   if (s->h_counts) cudaFreeHost(s->h_counts);
@@ -1609,10 +1607,9 @@ static int sloppy_alloc(lqcd_ctx *ctx, int nrhs) {
   cudaFree(s->sn);
   cudaFree(s->f32);
   cudaFree(s->xdf);
-  cudaFree(s->bdf);
   cudaFree(s->r32);
   cudaFree(s->small);
-  s->sd = nullptr; s->sn = nullptr; s->f32 = nullptr; s->xdf = nullptr; s->bdf = nullptr; s->r32 = nullptr;
+  s->sd = nullptr; s->sn = nullptr; s->f32 = nullptr; s->xdf = nullptr; s->r32 = nullptr;
   s->small = nullptr;
   s->cap = 0;
   const Geom &g = ctx->geom;
@@ -1622,7 +1619,6 @@ static int sloppy_alloc(lqcd_ctx *ctx, int nrhs) {
   LQCD_CUDA_TRY(ctx, cudaMalloc(&s->sn, 7 * pairs * vh * sizeof(float2)));
   LQCD_CUDA_TRY(ctx, cudaMalloc(&s->f32, 5 * (size_t)cap * 6 * vh * sizeof(float4)));
   LQCD_CUDA_TRY(ctx, cudaMalloc(&s->xdf, (size_t)cap * g.V * 12 * sizeof(float4)));
-  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->bdf, (size_t)cap * g.V * 12 * sizeof(float4)));
   LQCD_CUDA_TRY(ctx, cudaMalloc(&s->r32, (size_t)cap * g.V * 12 * sizeof(float2)));
   LQCD_CUDA_TRY(ctx, cudaMalloc(&s->small, small_layout(nullptr, cap, nbx).size()));
   if (!s->h_counts) LQCD_CUDA_TRY(ctx, cudaMallocHost(&s->h_counts, 16 * sizeof(int)));
@@ -1723,7 +1719,7 @@ struct MixedRun {
     for (int k = 0; k < nrhs; ++k) stats[k] = lqcd_solve_stats{0, LQCD_OK, 0.0, 0, 0};
     const size_t n = (size_t)nrhs * g.V * 12;
     LQCD_CUDA_TRY(ctx, cudaMemsetAsync(ss->xdf, 0, n * sizeof(float4), st));
-    return df_split(ctx, b, ss->bdf, n, st);
+    return LQCD_OK;
   }
 
   // the FP64 solution from the double-float iterate
@@ -1748,7 +1744,7 @@ struct MixedRun {
       todo = hl;
     }
     int rc = cycle == 0 ? fp64_residual_into(ctx, b, nullptr, nullptr, nrhs, rr.data(), bb.data(), st)
-                        : df_residual(ctx, ss->xdf, ss->bdf, ss->r32, todo.data(), (int)todo.size(), rr.data(),
+                        : df_residual(ctx, ss->xdf, b, ss->r32, todo.data(), (int)todo.size(), rr.data(),
                                       bb.data(), st);
     if (rc) return rc;
     hl.clear();
