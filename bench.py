@@ -122,9 +122,9 @@ def _oracle_worker(args):
     src = oph.dilute(oph.z2_noise(DIMS, NOISE_SEED, 0, 0), oph.DIL_TSC, piece)[None]
     t0 = time.perf_counter()
     phi, info = osv.solve(U, KAPPA, src, tol=TOL)
-    ol.contract(src, phi)
+    per_site = ol.contract(src, phi)
     dt = time.perf_counter() - t0
-    return dt, float(info["true_rel_residual"][0])
+    return dt, float(info["true_rel_residual"][0]), ol.per_timeslice(per_site)
 
 
 def _oracle_warmup():
@@ -133,18 +133,25 @@ def _oracle_warmup():
     osv.solve(haar_su3_field((4, 4, 4, 4), 0), 0.125, gaussian_spinors((4, 4, 4, 4), 1, 0), tol=1e-10)
 
 
-def oracle_rate(n_workers, n_rhs):
+def oracle_pieces(n_rhs):
+    """The diluted pieces of noise vector 0 the oracle baseline solves."""
+    return [(17 * k) % (12 * DIMS[3]) for k in range(n_rhs)]
+
+
+def oracle_rate(n_workers, n_rhs, with_loops=False):
     """RHS solves/s of the oracle on n_rhs sources over n_workers spawned processes."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
-    pieces = [(17 * k) % (12 * DIMS[3]) for k in range(n_rhs)]
+    pieces = oracle_pieces(n_rhs)
     t0 = time.perf_counter()
     with ctx.Pool(n_workers) as pool:
         res = pool.map(_oracle_worker, [(p,) for p in pieces])
     wall = time.perf_counter() - t0
     busy = max(r[0] for r in res) if n_workers >= n_rhs else wall
-    return n_rhs / busy, {"rhs": n_rhs, "max_worker_s": busy, "wall_s": wall,
-                          "max_residual": max(r[1] for r in res)}
+    info = {"rhs": n_rhs, "max_worker_s": busy, "wall_s": wall, "max_residual": max(r[1] for r in res)}
+    if with_loops:
+        info["loops"] = [r[2] for r in res]
+    return n_rhs / busy, info
 
 
 def host_cores():
@@ -382,6 +389,20 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     fp64_rate = n64 / (time.perf_counter() - t0)
     extras = next_rows(L, h, per_site, dev, stream, not args.no_cpu, nrhs)
+    gpu_piece_loops = None
+    if not args.no_cpu:  # the same pieces the oracle baseline solves, for the loop error
+        pcs = oracle_pieces(args.cpu_rhs)
+        srcp = torch.empty((len(pcs), V, 4, 3), dtype=torch.complex128, device=dev)
+        for k, pc in enumerate(pcs):
+            L.lqcd_noise_generate(NOISE_SEED, L.LQCD_STREAM_LP, 0, DIMS, L.LQCD_DILUTE_TSC, pc, 1, srcp[k:k + 1])
+        xp = torch.empty_like(srcp)
+        L.lqcd_solve_batch(h, srcp, xp, params)
+        gpu_piece_loops = []
+        for k in range(len(pcs)):
+            ptk = torch.zeros((DIMS[3], 6), dtype=torch.complex128, device=dev)
+            L.lqcd_loops_batch(h, srcp[k:k + 1], xp[k:k + 1], 1.0, None, ptk)
+            gpu_piece_loops.append(ptk.cpu().numpy())
+        del srcp, xp
     L.lqcd_destroy(h)
 
     # ---------------------------------------------------------- roofline
@@ -409,8 +430,11 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_cpu:
         cores = host_cores()
         nw = min(cores, args.cpu_rhs)
-        v, info = oracle_rate(nw, args.cpu_rhs)
+        v, info = oracle_rate(nw, args.cpu_rhs, with_loops=True)
+        errs = [float(np.max(np.abs(gl - ol_)) / np.max(np.abs(ol_)))
+                for gl, ol_ in zip(gpu_piece_loops, info["loops"])]
         cpu = {"value": v, "unit": "RHS solves/s", "cores": nw, "kind": "oracle",
+               "loop_max_rel_err_gpu_vs_oracle": max(errs),
                "sample": f"{args.cpu_rhs} of the 384 diluted sources, one per spawned process, FP64 numpy "
                          f"even-odd BiCGstab to 1e-10 + contraction; slowest process {info['max_worker_s']:.1f} s"}
 

@@ -210,6 +210,7 @@ __global__ void k_point_sources(const int64_t *sites, int n_sites, int V, double
 extern "C" {
 
 int lqcd_create(lqcd_ctx **out, const int dims[4], int device) {
+  LQCD_TRACE("lqcd_create");
   if (!out || !dims) return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_create: null argument");
   *out = nullptr;
   for (int i = 0; i < 4; ++i)
@@ -234,6 +235,7 @@ int lqcd_create(lqcd_ctx **out, const int dims[4], int device) {
 }
 
 int lqcd_destroy(lqcd_ctx *ctx) {
+  LQCD_TRACE("lqcd_destroy");
   if (!ctx) return LQCD_OK;
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
@@ -258,10 +260,12 @@ const char *lqcd_last_error(const lqcd_ctx *ctx) { return ctx ? ctx->err.c_str()
 static int set_gauge_impl(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream, bool require_su3);
 
 int lqcd_set_gauge(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream) {
+  LQCD_TRACE("lqcd_set_gauge");
   return set_gauge_impl(ctx, U, stream, true);
 }
 
 int lqcd_set_gauge_general(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream) {
+  LQCD_TRACE("lqcd_set_gauge_general");
   return set_gauge_impl(ctx, U, stream, false);
 }
 
@@ -305,6 +309,7 @@ static int set_gauge_impl(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream, 
 }
 
 int lqcd_set_kappa(lqcd_ctx *ctx, double kappa) {
+  LQCD_TRACE("lqcd_set_kappa");
   if (!ctx) return LQCD_ERR_INVALID;
   if (!std::isfinite(kappa)) return set_error(ctx, LQCD_ERR_INVALID, "lqcd_set_kappa: non-finite kappa");
   ctx->kappa = kappa;
@@ -312,6 +317,7 @@ int lqcd_set_kappa(lqcd_ctx *ctx, double kappa) {
 }
 
 int lqcd_plaquette(lqcd_ctx *ctx, double *plaq, lqcd_stream_t stream) {
+  LQCD_TRACE("lqcd_plaquette");
   if (!ctx || !plaq) return set_error(ctx, LQCD_ERR_INVALID, "lqcd_plaquette: null argument");
   if (!ctx->have_gauge) return set_error(ctx, LQCD_ERR_NO_GAUGE, "lqcd_plaquette: no gauge field");
   cudaSetDevice(ctx->device);
@@ -333,6 +339,7 @@ int lqcd_plaquette(lqcd_ctx *ctx, double *plaq, lqcd_stream_t stream) {
 }
 
 int lqcd_apply_dirac(lqcd_ctx *ctx, const double *in, double *out, int nrhs, int dagger, lqcd_stream_t stream) {
+  LQCD_TRACE("lqcd_apply_dirac");
   if (!ctx || !in || !out || nrhs < 0) return set_error(ctx, LQCD_ERR_INVALID, "lqcd_apply_dirac: bad argument");
   if (!ctx->have_gauge) return set_error(ctx, LQCD_ERR_NO_GAUGE, "lqcd_apply_dirac: no gauge field");
   if (nrhs == 0) return LQCD_OK;
@@ -342,6 +349,7 @@ int lqcd_apply_dirac(lqcd_ctx *ctx, const double *in, double *out, int nrhs, int
 
 int lqcd_solve_batch(lqcd_ctx *ctx, const double *b, double *x, int nrhs, const lqcd_solver_params *params,
                      lqcd_solve_stats *stats, lqcd_stream_t stream) {
+  LQCD_TRACE("lqcd_solve_batch");
   if (!ctx || !params || nrhs < 0 || (nrhs > 0 && (!b || !x || !stats)))
     return set_error(ctx, LQCD_ERR_INVALID, "lqcd_solve_batch: bad argument");
   if (!ctx->have_gauge) return set_error(ctx, LQCD_ERR_NO_GAUGE, "lqcd_solve_batch: no gauge field");
@@ -384,6 +392,7 @@ int lqcd_solve_batch(lqcd_ctx *ctx, const double *b, double *x, int nrhs, const 
 }
 
 int lqcd_point_sources(lqcd_ctx *ctx, const int64_t *sites, int n_sites, double *out, lqcd_stream_t stream) {
+  LQCD_TRACE("lqcd_point_sources");
   if (!ctx || !sites || !out || n_sites < 0) return set_error(ctx, LQCD_ERR_INVALID, "lqcd_point_sources: bad argument");
   if (n_sites == 0) return LQCD_OK;
   cudaSetDevice(ctx->device);
@@ -417,6 +426,7 @@ extern "C" {
 long long lqcd_launch_count(void) { return lqcd::g_launches.load(); }
 
 int lqcd_profile_begin(lqcd_ctx *ctx) {
+  LQCD_TRACE("lqcd_profile_begin");
   if (!ctx) return LQCD_ERR_INVALID;
   cudaSetDevice(ctx->device);
   if (!ctx->d_prof) LQCD_CUDA_TRY(ctx, cudaMalloc(&ctx->d_prof, 8 * sizeof(unsigned long long)));
@@ -429,6 +439,7 @@ int lqcd_profile_begin(lqcd_ctx *ctx) {
 }
 
 int lqcd_profile_end(lqcd_ctx *ctx, lqcd_profile *out) {
+  LQCD_TRACE("lqcd_profile_end");
   if (!ctx || !out) return LQCD_ERR_INVALID;
   cudaSetDevice(ctx->device);
   LQCD_CUDA_TRY(ctx, cudaDeviceSynchronize());

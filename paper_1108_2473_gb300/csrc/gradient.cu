@@ -197,6 +197,7 @@ using namespace lqcd;
 extern "C" int lqcd_gradient(lqcd_ctx *ctx, const double *src, const double *sol, int nrhs, const double *coef,
                              double weight, const lqcd_solver_params *params, double *dkappa, double *dU,
                              lqcd_solve_stats *stats, lqcd_stream_t stream) {
+  LQCD_TRACE("lqcd_gradient");
   if (!ctx || !params || nrhs < 0 || !coef || (nrhs > 0 && (!src || !sol || !stats)))
     return set_error(ctx, LQCD_ERR_INVALID, "lqcd_gradient: bad argument");
   if (!ctx->have_gauge) return set_error(ctx, LQCD_ERR_NO_GAUGE, "lqcd_gradient: no gauge field");

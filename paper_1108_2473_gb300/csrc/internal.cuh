@@ -10,9 +10,22 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lqcd.h"
 
 namespace lqcd {
+
+// NVTX range around one ABI call (shows up in Nsight timelines; a no-op
+// without a tool attached)
+struct TraceRange {
+  explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange &) = delete;
+  TraceRange &operator=(const TraceRange &) = delete;
+};
+#define LQCD_TRACE(name) ::lqcd::TraceRange lqcd_trace_range_(name)
+
 
 // ------------------------------------------------------------------ geometry
 struct Geom {

@@ -140,6 +140,7 @@ using namespace lqcd;
 
 extern "C" int lqcd_loops_batch(lqcd_ctx *ctx, const double *src, const double *sol, int nrhs, double weight,
                                 double *per_site, double *per_t, lqcd_stream_t stream) {
+  LQCD_TRACE("lqcd_loops_batch");
   if (!ctx || nrhs < 0 || (nrhs > 0 && (!src || !sol)))
     return set_error(ctx, LQCD_ERR_INVALID, "lqcd_loops_batch: bad argument");
   if (nrhs == 0 || (!per_site && !per_t)) return LQCD_OK;
@@ -216,6 +217,7 @@ static int noalloc_scratch(double2 **out) {
 
 extern "C" int lqcd_loops_batch_noalloc(const int dims[4], const double *src, const double *sol, int nrhs,
                                         double weight, double *per_site, double *per_t, lqcd_stream_t stream) {
+  LQCD_TRACE("lqcd_loops_batch_noalloc");
   if (!dims || nrhs < 0 || (nrhs > 0 && (!src || !sol)))
     return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_loops_batch_noalloc: bad argument");
   for (int i = 0; i < 4; ++i)
@@ -333,6 +335,7 @@ __global__ void k_correlator(const double2 *__restrict__ A, const double2 *__res
 
 extern "C" int lqcd_loops_momentum(lqcd_ctx *ctx, const double *per_site, int n_mom, const int *moms, double *out,
                                    lqcd_stream_t stream) {
+  LQCD_TRACE("lqcd_loops_momentum");
   if (!ctx || n_mom < 0 || (n_mom > 0 && (!per_site || !moms || !out)))
     return set_error(ctx, LQCD_ERR_INVALID, "lqcd_loops_momentum: bad argument");
   if (n_mom == 0) return LQCD_OK;
@@ -354,6 +357,7 @@ extern "C" int lqcd_loops_momentum(lqcd_ctx *ctx, const double *per_site, int n_
 
 extern "C" int lqcd_disconnected_correlator(const double *loops_p, const double *loops_mp, int n_vec, int lt, int l3,
                                             int unbiased, double *out, lqcd_stream_t stream) {
+  LQCD_TRACE("lqcd_disconnected_correlator");
   if (!loops_p || !loops_mp || !out || n_vec < 1 || lt < 1 || l3 < 1 || (unbiased && n_vec < 2))
     return set_error(nullptr, LQCD_ERR_INVALID,
                      "lqcd_disconnected_correlator: bad argument (the unbiased estimator needs n_vec >= 2)");

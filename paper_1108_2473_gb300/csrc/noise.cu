@@ -95,10 +95,12 @@ __global__ void k_noise(Geom g, uint64_t seed, uint64_t stream_tag, uint64_t noi
 
 using namespace lqcd;
 
-extern "C" int lqcd_dilution_pieces(const int dims[4], int dilution) { return dilution_pieces(dims, dilution); }
+extern "C" int lqcd_dilution_pieces(const int dims[4], int dilution) {
+  LQCD_TRACE("lqcd_dilution_pieces"); return dilution_pieces(dims, dilution); }
 
 extern "C" int lqcd_noise_generate(uint64_t seed, uint64_t noise_stream, uint64_t noise_index, const int dims[4],
                                    int dilution, int first_piece, int n_pieces, double *out, lqcd_stream_t stream) {
+  LQCD_TRACE("lqcd_noise_generate");
   if (!dims || !out || n_pieces < 0 || first_piece < 0)
     return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_noise_generate: bad argument");
   for (int i = 0; i < 4; ++i)

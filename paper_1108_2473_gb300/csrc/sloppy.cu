@@ -2078,12 +2078,14 @@ using namespace lqcd;
 extern "C" {
 
 int lqcd_batch_create(lqcd_batch **out) {
+  LQCD_TRACE("lqcd_batch_create");
   if (!out) return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_batch_create: null argument");
   *out = new lqcd_batch();
   return LQCD_OK;
 }
 
 int lqcd_batch_destroy(lqcd_batch *batch) {
+  LQCD_TRACE("lqcd_batch_destroy");
   if (!batch) return LQCD_OK;
   if (batch->graph) cudaGraphExecDestroy(batch->graph);
   for (cudaStream_t s : batch->side) cudaStreamDestroy(s);
@@ -2092,6 +2094,7 @@ int lqcd_batch_destroy(lqcd_batch *batch) {
 }
 
 int lqcd_batch_add(lqcd_batch *batch, lqcd_ctx *ctx, const double *b, double *x, int nrhs) {
+  LQCD_TRACE("lqcd_batch_add");
   if (!batch || !ctx || nrhs <= 0 || !b || !x) return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_batch_add: bad argument");
   if (!is_device_ptr(b) || !is_device_ptr(x))
     return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_batch_add: b and x must be device memory");
@@ -2105,6 +2108,7 @@ int lqcd_batch_add(lqcd_batch *batch, lqcd_ctx *ctx, const double *b, double *x,
 
 int lqcd_batch_run(lqcd_batch *batch, const lqcd_solver_params *params, lqcd_solve_stats *stats,
                    lqcd_stream_t stream) {
+  LQCD_TRACE("lqcd_batch_run");
   if (!batch || !params || !stats) return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_batch_run: null argument");
   if (batch->entries.empty()) return LQCD_OK;
   const lqcd_solver_params &p = *params;
@@ -2240,6 +2244,7 @@ static int autotune_hop(lqcd_ctx *ctx, int nrhs, int precision, int *best, int *
 
 extern "C" int lqcd_autotune(lqcd_ctx *ctx, int nrhs, int precision, int *best_blocks_per_sm,
                              int *best_hop_variant) {
+  LQCD_TRACE("lqcd_autotune");
   if (!ctx || nrhs <= 0 || nrhs > 4096) return set_error(ctx, LQCD_ERR_INVALID, "lqcd_autotune: bad argument");
   if (!ctx->have_gauge || !ctx->gauge_su3) return set_error(ctx, LQCD_ERR_NO_GAUGE, "lqcd_autotune: needs an SU(3) gauge field");
   cudaSetDevice(ctx->device);

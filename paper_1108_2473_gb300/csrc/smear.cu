@@ -202,6 +202,7 @@ __global__ void k_gauss_step(Geom g, const double2 *__restrict__ U, const double
 using namespace lqcd;
 
 extern "C" int lqcd_smear_ape(lqcd_ctx *ctx, double alpha, int n_iter, double *out, lqcd_stream_t stream) {
+  LQCD_TRACE("lqcd_smear_ape");
   if (!ctx || n_iter < 0 || !std::isfinite(alpha)) return set_error(ctx, LQCD_ERR_INVALID, "lqcd_smear_ape: bad argument");
   if (!ctx->have_gauge) return set_error(ctx, LQCD_ERR_NO_GAUGE, "lqcd_smear_ape: no gauge field");
   if (out && !is_device_ptr(out)) return set_error(ctx, LQCD_ERR_INVALID, "lqcd_smear_ape: out must be device memory");
@@ -232,6 +233,7 @@ extern "C" int lqcd_smear_ape(lqcd_ctx *ctx, double alpha, int n_iter, double *o
 
 extern "C" int lqcd_smear_gaussian(lqcd_ctx *ctx, const double *in, double *out, int nrhs, double alpha, int n_iter,
                                    int ape_links, int normalise, lqcd_stream_t stream) {
+  LQCD_TRACE("lqcd_smear_gaussian");
   if (!ctx || nrhs < 0 || n_iter < 0 || !std::isfinite(alpha) || (nrhs > 0 && (!in || !out)) || (in && in == out))
     return set_error(ctx, LQCD_ERR_INVALID, "lqcd_smear_gaussian: bad argument (in and out must differ)");
   if (!ctx->have_gauge) return set_error(ctx, LQCD_ERR_NO_GAUGE, "lqcd_smear_gaussian: no gauge field");

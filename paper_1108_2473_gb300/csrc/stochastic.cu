@@ -27,6 +27,7 @@ void merge(lqcd_solve_stats &acc, const lqcd_solve_stats &s) {
 extern "C" int lqcd_loops_stochastic(lqcd_ctx *ctx, const lqcd_stochastic_params *sp,
                                      const lqcd_solver_params *solver, double *per_site, double *per_t,
                                      lqcd_solve_stats *summary, lqcd_stream_t stream) {
+  LQCD_TRACE("lqcd_loops_stochastic");
   if (!ctx || !sp || !solver) return set_error(ctx, LQCD_ERR_INVALID, "lqcd_loops_stochastic: null argument");
   const int np = n_pieces(ctx->dims, sp->dilution);
   if (np < 0) return set_error(ctx, LQCD_ERR_INVALID, "lqcd_loops_stochastic: unknown dilution %d", sp->dilution);
