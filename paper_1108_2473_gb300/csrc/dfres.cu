@@ -118,20 +118,29 @@ struct D4R {
 // Three threads per site (one per output colour, sharing the spin projection
 // by shuffles): r = b - x + kappa H x at the sites of parity p_out.  A warp
 // takes 10 sites (lanes 0..29; lanes 30, 31 only take part in the shuffles), a
-// block 6 warps.  Partials |r|^2 (.c) and |b|^2 (.d) per block.
+// block 6 warps.  Blocks are ordered (chunk of DF3_CHUNK listed right-hand
+// sides, site block, right-hand side in the chunk): blocks issued together
+// share their sites' links across the chunk, while the time neighbours of a
+// site block stay a few hundred blocks away (both reused from L2).
+// Partials |r|^2 (.c) and |b|^2 (.d) per block.
 constexpr int DF3_WARP_SITES = 10;
 constexpr int DF3_WARPS = 6;
 constexpr int DF3_SITES = DF3_WARP_SITES * DF3_WARPS;
+constexpr int DF3_CHUNK = 8;
 __global__ void __launch_bounds__(32 * DF3_WARPS, 4) k_resid_df3(Geom g, int p_out, const float4 *__restrict__ U,
                                                                const float4 *__restrict__ x,
                                                                const double2 *__restrict__ b, float2 *r, float kh,
-                                                               float kl, const int *list, D4R *part) {
+                                                               float kl, const int *list, int n, D4R *part,
+                                                               int nblk) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int sl = lane / 3, a = lane - 3 * sl;  // site within the warp, output colour
-  const int i = blockIdx.x * DF3_SITES + warp * DF3_WARP_SITES + sl;
+  const int in_chunk = blockIdx.x % DF3_CHUNK, rest = blockIdx.x / DF3_CHUNK;
+  const int blk = rest % nblk, slot = (rest / nblk) * DF3_CHUNK + in_chunk;
+  if (slot >= n) return;  // ragged last chunk: the whole block leaves together
+  const int i = blk * DF3_SITES + warp * DF3_WARP_SITES + sl;
   const bool act = sl < DF3_WARP_SITES && i < g.Vh;
   const int base = 3 * sl;
-  const int rhs = list[blockIdx.y];
+  const int rhs = list[slot];
   const size_t stride = (size_t)g.V * 12;
   float rn = 0.f, bn = 0.f;
   int c[4];
@@ -177,7 +186,7 @@ __global__ void __launch_bounds__(32 * DF3_WARPS, 4) k_resid_df3(Geom g, int p_o
     __syncthreads();
   }
   if (threadIdx.x == 0)
-    part[(size_t)blockIdx.y * 2 * gridDim.x + (size_t)p_out * gridDim.x + blockIdx.x] =
+    part[(size_t)slot * 2 * nblk + (size_t)p_out * nblk + blk] =
         D4R{0.0, 0.0, sh[0][0], sh[1][0]};
 }
 
@@ -235,7 +244,8 @@ int df_residual(lqcd_ctx *ctx, const float4 *x, const double2 *b, float2 *r, con
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(d_list, list, n * sizeof(int), cudaMemcpyHostToDevice, st));
   const float kh = (float)ctx->kappa, kl = (float)(ctx->kappa - (double)kh);
   for (int p = 0; p < 2; ++p) {
-    KL k_resid_df3<<<dim3(nblk, n), 32 * DF3_WARPS, 0, st>>>(g, p, ctx->Udf, x, b, r, kh, kl, d_list, part);
+    const long long blocks = (long long)((n + DF3_CHUNK - 1) / DF3_CHUNK) * nblk * DF3_CHUNK;
+    KL k_resid_df3<<<(unsigned)blocks, 32 * DF3_WARPS, 0, st>>>(g, p, ctx->Udf, x, b, r, kh, kl, d_list, n, part, nblk);
     LQCD_LAUNCH_CHECK(ctx, "k_resid_df3");
   }
   KL k_df_fin<<<n, 32, 0, st>>>(part, 2 * nblk, d_rr, d_bb);
