@@ -219,6 +219,76 @@ def gradient_step(L, h, src, x, params, dev, stream):
             "dkappa": dk, "dU_norm": float(torch.linalg.vector_norm(dU).item())}
 
 
+# ----------------------------------------- the other measured configurations
+def config_runs(L, h, dev, stream):
+    """The truncated solver method run (400 undiluted low-precision vectors to 1e-3 plus
+    20 high-precision corrections to 1e-10, on the bench field) and the uneven batch of
+    four lattices in one graph, each timed once after a warm-up."""
+    import numpy as np
+    import torch
+    from lattice_inputs import eps_su3_field, haar_su3_field
+    out = {}
+    V = int(np.prod(DIMS))
+    solver = L.solver_params(tol=1e-10, precision=L.LQCD_PREC_MIXED_BF16)
+    ps = torch.zeros((V, 6), dtype=torch.complex128, device=dev)
+    pt = torch.zeros((DIMS[3], 6), dtype=torch.complex128, device=dev)
+    L.lqcd_loops_stochastic(h, L.stochastic_params(7, 20, 0, 1e-3, 1e-10, L.LQCD_DILUTE_NONE, 1000), solver, ps, pt)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    rc, summ = L.lqcd_loops_stochastic(h, L.stochastic_params(7, 400, 20, 1e-3, 1e-10, L.LQCD_DILUTE_NONE), solver,
+                                       ps, pt)
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter() - t0
+    out["tsm"] = {"lp_vectors": 400, "hp_vectors": 20, "dilution": "none", "lp_tol": 1e-3, "hp_tol": 1e-10,
+                  "s": t, "solves": 420 + 20, "solves_per_s": 440 / t, "status": rc,
+                  "lp_max_iterations": summ[0]["iterations"], "hp_max_iterations": summ[1]["iterations"],
+                  "hp_max_true_rel_residual": summ[1]["true_rel_residual"]}
+    # uneven batch: four lattices, fields and kappas in one captured graph
+    specs = [((8, 8, 8, 16), "haar", 0.157, 768), ((12, 12, 12, 24), "eps", 0.115, 384),
+             ((16, 16, 16, 32), "eps", 0.120, 192), ((24, 24, 24, 48), "haar", 0.157, 48)]
+    handles, bufs = [], []
+    batch = L.lqcd_batch_create()
+    try:
+        for k, (dims, kind, kappa, n) in enumerate(specs):
+            U = haar_su3_field(dims, 10 + k) if kind == "haar" else eps_su3_field(dims, 0.35, 10 + k)
+            hk = L.lqcd_create(dims, 0)
+            handles.append(hk)
+            L.lqcd_set_gauge(hk, torch.from_numpy(U.reshape(-1)).to(dev))
+            L.lqcd_set_kappa(hk, kappa)
+            Vl = int(np.prod(dims))
+            b = torch.empty((n, Vl, 4, 3), dtype=torch.complex128, device=dev)
+            npc = L.lqcd_dilution_pieces(dims, L.LQCD_DILUTE_TSC)
+            for v0 in range(0, n, npc):  # several diluted vectors when n exceeds one vector's pieces
+                m = min(npc, n - v0)
+                L.lqcd_noise_generate(3, 0, 100 * k + v0 // npc, dims, L.LQCD_DILUTE_TSC, 0, m, b[v0:v0 + m])
+            xk = torch.empty_like(b)
+            bufs.append((b, xk))
+            L.lqcd_batch_add(batch, hk, b, xk)
+        total = sum(sp[3] for sp in specs)
+        bstream = torch.cuda.Stream(device=dev)  # the batch graph is captured on a created stream
+        torch.cuda.synchronize(dev)
+        L.lqcd_batch_run(batch, solver, total, bstream)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rc, st = L.lqcd_batch_run(batch, solver, total, bstream)
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter() - t0
+        per, k0 = [], 0
+        for dims, kind, kappa, n in specs:
+            s_ = st[k0:k0 + n]
+            k0 += n
+            per.append({"lattice": "x".join(map(str, dims)), "field": kind, "kappa": kappa, "rhs": n,
+                        "iterations_max": max(r["iterations"] for r in s_),
+                        "max_true_rel_residual": max(r["true_rel_residual"] for r in s_)})
+        out["uneven_batch"] = {"rhs": total, "s": t, "solves_per_s": total / t, "status": rc, "lattices": per}
+    finally:
+        L.lqcd_batch_destroy(batch)
+        for hk in handles:
+            L.lqcd_destroy(hk)
+        del bufs
+    return out
+
+
 # ------------------------------------------------- kernels beyond the step
 def _event_ms(fn, stream, reps=10, warm=3):
     import torch
@@ -418,6 +488,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize(dev)
     fp64_rate = n64 / (time.perf_counter() - t0)
     extras = next_rows(L, h, per_site, dev, stream, not args.no_cpu, nrhs)
+    configs = config_runs(L, h, dev, stream)
     gpu_piece_loops = None
     if not args.no_cpu:  # the same pieces the oracle baseline solves, for the loop error
         pcs = oracle_pieces(args.cpu_rhs)
@@ -487,6 +558,7 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": launches,
         "clocks": clk,
         "gradient": grad,
+        "configs": configs,
         "next_rows": extras,
     }
     print(json.dumps(line), flush=True)

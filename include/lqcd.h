@@ -289,7 +289,9 @@ typedef struct {
   int n_hp;       /* vectors of the high-precision correction set, >= 0   */
   double tol_lp;  /* relative residual of the LP (or plain) solves         */
   double tol_hp;  /* relative residual of the HP solves                    */
-  int chunk;      /* dilution pieces solved together; 0 = automatic        */
+  int chunk;      /* right-hand sides per batched solve: the dilution pieces
+                     of one vector, or whole vectors grouped when a vector
+                     has fewer pieces (undiluted TSM); 0 = 384              */
 } lqcd_stochastic_params;
 
 /* Runs the estimator above end to end on the device (noise generation,
