@@ -208,10 +208,21 @@ __global__ void k_df_fin(const D4R *part, int nb, double *rr, double *bb) {
   }
 }
 
-// double-float canonical -> FP64 canonical
+// double-float canonical -> FP64 canonical; four independent elements per thread
+// and iteration keep enough loads in flight to stream at the HBM rate
 __global__ void k_join_df(const float4 *__restrict__ in, double2 *out, size_t n) {
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-    float4 q = in[k];
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  for (; k + 3 * stride < n; k += 4 * stride) {
+    float4 q[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) q[u] = in[k + u * stride];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      out[k + u * stride] = make_double2((double)q[u].x + (double)q[u].z, (double)q[u].y + (double)q[u].w);
+  }
+  for (; k < n; k += stride) {
+    const float4 q = in[k];
     out[k] = make_double2((double)q.x + (double)q.z, (double)q.y + (double)q.w);
   }
 }

@@ -1280,7 +1280,16 @@ __global__ void __launch_bounds__(ACC_SITES * 2) k_accum_df_both(Geom g, F32F e,
     const int i0 = (w % nbx) * ACC_SITES;
     const int nloc = min(ACC_SITES, g.Vh - i0);
     float4 *base = x + ((size_t)rhs * g.V + 2 * (size_t)i0) * 12;
-    for (int k = threadIdx.x; k < nloc * 24; k += blockDim.x) tile[k] = base[k];
+    constexpr int PER = ACC_SITES * 24 / (ACC_SITES * 2);  // elements per thread of a full tile
+    if (nloc == ACC_SITES) {  // all loads issued before any store: PER requests in flight
+      float4 q[PER];
+#pragma unroll
+      for (int u = 0; u < PER; ++u) q[u] = base[threadIdx.x + u * blockDim.x];
+#pragma unroll
+      for (int u = 0; u < PER; ++u) tile[threadIdx.x + u * blockDim.x] = q[u];
+    } else {
+      for (int k = threadIdx.x; k < nloc * 24; k += blockDim.x) tile[k] = base[k];
+    }
     __syncthreads();
     // two threads per parity-local index: one per canonical site of the pair
     const int li = threadIdx.x >> 1, half = threadIdx.x & 1;
@@ -1302,7 +1311,12 @@ __global__ void __launch_bounds__(ACC_SITES * 2) k_accum_df_both(Geom g, F32F e,
       }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < nloc * 24; k += blockDim.x) base[k] = tile[k];
+    if (nloc == ACC_SITES) {
+#pragma unroll
+      for (int u = 0; u < PER; ++u) base[threadIdx.x + u * blockDim.x] = tile[threadIdx.x + u * blockDim.x];
+    } else {
+      for (int k = threadIdx.x; k < nloc * 24; k += blockDim.x) base[k] = tile[k];
+    }
     __syncthreads();
   }
 }
