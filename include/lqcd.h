@@ -125,9 +125,11 @@ const char *lqcd_last_error(const lqcd_ctx *ctx);
 
 /* Upload and pack the gauge field (Sec. II: the configuration the loops are
  * computed on).  U: [V][4][3][3] complex128, device or host pointer.  Keeps an
- * FP64 copy, an FP32 and an FP16 reconstruct-12 copy (first two rows; the
- * third row is (row1 x row2)^*).  Errors: LQCD_ERR_NOT_SU3 if a link deviates
- * from unitarity or unit determinant by more than 1e-12 (nothing is kept). */
+ * FP64 copy and the reduced-precision copies the mixed-precision solver reads:
+ * FP32 reconstruct-12 (first two rows; the third is (row1 x row2)^*), FP16 with
+ * all 18 reals duplicated, tf32 and double-float.  Errors: LQCD_ERR_NOT_SU3 if
+ * a link deviates from unitarity or unit determinant by more than 1e-12
+ * (nothing is kept). */
 int lqcd_set_gauge(lqcd_ctx *ctx, const double *U, lqcd_stream_t stream);
 
 /* As lqcd_set_gauge but for arbitrary complex 3x3 links (no SU(3) check).

@@ -66,8 +66,6 @@ bool is_device_ptr(const void *p) {
 // ------------------------------------------------------------ gauge packing
 __device__ __forceinline__ double2 dmul(double2 a, double2 b) { return cmul(a, b); }
 
-// Check unitarity and unit determinant of every link; write the FP32 and FP16
-// reconstruct-12 copies (rows 0 and 1) in parity-split SoA order.
 // FP32 -> tf32 with round-to-nearest (ties away), kept in an FP32 register
 __device__ __forceinline__ float to_tf32(float x) {
   unsigned r;
@@ -75,6 +73,9 @@ __device__ __forceinline__ float to_tf32(float x) {
   return __uint_as_float(r);
 }
 
+// Check unitarity and unit determinant of every link; write the reduced-precision
+// copies (FP32 reconstruct-12, FP16 with all 18 reals duplicated, tf32,
+// double-float) in parity-split order.
 __global__ void k_pack_gauge(const double2 *__restrict__ U, Geom g, float4 *U32, uint4 *U16, float4 *Udf,
                              float2 *Utf, int *flag) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;

@@ -8,21 +8,25 @@
 //               all arithmetic in FP32;
 //   * FP32    -- the iterate x and the reliable-update residual
 //               r = b - D_hat x, with FP32 reconstruct-12 links;
-//   * FP64    -- the outer defect correction: r = b - D x on the full lattice
-//               in FP64, inner solve D e = r, x += e, until |r| / |b| <= tol.
+//   * FP64-class -- the outer defect correction: r = b - D x on the full
+//               lattice in double-float arithmetic (a 48-bit significand on the
+//               FP32 units), inner solve D e = r, x += e, until |r| / |b| <= tol.
 //
 // Sloppy vectors hold right-hand sides in pairs (RHS 2P and 2P+1): each
 // 16-bit pair is the same real of both members, so after conversion every
 // operation of the hopping term and of the BLAS updates is one packed FP32x2
 // instruction (fma.rn.f32x2 / add / mul) working on both members at once, and
-// a link load, its reconstruction and the neighbour indexing serve two RHS.
-// The sloppy links are FP16 reconstruct-12 with every real stored twice, so
-// that one conversion yields the (u, u) operand of the packed products.
+// a link load, its conversion and the neighbour indexing serve two RHS.
+// The sloppy links are FP16, all 18 reals, every real stored twice, so that
+// one conversion yields the (u, u) operand of the packed products (this hop
+// is bound by the FMA pipe, where a reconstruction would cost more than the
+// extra link bytes; the FP32 reliable-update hop, bound by its loads, keeps
+// reconstruct-12 links).
 //
 // Layouts (parity-compact, per pair / per RHS):
 //   sloppy: [P][6][Vh] uint4 (24 16-bit pairs) + FP16 norms [P][Vh] float2
 //   FP32:   [rhs][6][Vh] float4
-//   links:  FP16 [2 parity][4 mu][3][Vh] uint4 (rows 0-1, duplicated);
+//   links:  FP16 [2 parity][4 mu][5][Vh] uint4 (18 reals, duplicated);
 //           FP32 [2][4][3][Vh] float4 (rows 0-1)
 // A spinor's 24 reals are ordered ((spin * 3 + colour) * 2 + re/im).
 //
@@ -2050,7 +2054,7 @@ int mixed_solve(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const lqc
     return set_error(ctx, LQCD_ERR_INVALID, "the CG solver is available with LQCD_PREC_FP64 only");
   if (!ctx->gauge_su3)
     return set_error(ctx, LQCD_ERR_INVALID,
-                     "mixed precision needs SU(3) links (reconstruct-12); this gauge field was set with "
+                     "mixed precision needs SU(3) links (the FP32 copy is reconstruct-12); this gauge field was set with "
                      "lqcd_set_gauge_general: use LQCD_PREC_FP64");
   int blk = p.rhs_block > 0 ? p.rhs_block : nrhs;
   if (blk > 4096) blk = 4096;
