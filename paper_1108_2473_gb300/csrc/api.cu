@@ -341,7 +341,8 @@ int lqcd_plaquette(lqcd_ctx *ctx, double *plaq, lqcd_stream_t stream) {
 
 int lqcd_apply_dirac(lqcd_ctx *ctx, const double *in, double *out, int nrhs, int dagger, lqcd_stream_t stream) {
   LQCD_TRACE("lqcd_apply_dirac");
-  if (!ctx || !in || !out || nrhs < 0) return set_error(ctx, LQCD_ERR_INVALID, "lqcd_apply_dirac: bad argument");
+  if (!ctx || nrhs < 0 || (nrhs > 0 && (!in || !out)))
+    return set_error(ctx, LQCD_ERR_INVALID, "lqcd_apply_dirac: bad argument");
   if (!ctx->have_gauge) return set_error(ctx, LQCD_ERR_NO_GAUGE, "lqcd_apply_dirac: no gauge field");
   if (nrhs == 0) return LQCD_OK;
   cudaSetDevice(ctx->device);
@@ -394,7 +395,8 @@ int lqcd_solve_batch(lqcd_ctx *ctx, const double *b, double *x, int nrhs, const 
 
 int lqcd_point_sources(lqcd_ctx *ctx, const int64_t *sites, int n_sites, double *out, lqcd_stream_t stream) {
   LQCD_TRACE("lqcd_point_sources");
-  if (!ctx || !sites || !out || n_sites < 0) return set_error(ctx, LQCD_ERR_INVALID, "lqcd_point_sources: bad argument");
+  if (!ctx || n_sites < 0 || (n_sites > 0 && (!sites || !out)))
+    return set_error(ctx, LQCD_ERR_INVALID, "lqcd_point_sources: bad argument");
   if (n_sites == 0) return LQCD_OK;
   cudaSetDevice(ctx->device);
   cudaStream_t st = (cudaStream_t)stream;

@@ -101,7 +101,7 @@ extern "C" int lqcd_dilution_pieces(const int dims[4], int dilution) {
 extern "C" int lqcd_noise_generate(uint64_t seed, uint64_t noise_stream, uint64_t noise_index, const int dims[4],
                                    int dilution, int first_piece, int n_pieces, double *out, lqcd_stream_t stream) {
   LQCD_TRACE("lqcd_noise_generate");
-  if (!dims || !out || n_pieces < 0 || first_piece < 0)
+  if (!dims || n_pieces < 0 || first_piece < 0 || (n_pieces > 0 && !out))
     return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_noise_generate: bad argument");
   for (int i = 0; i < 4; ++i)
     if (dims[i] < 2 || (dims[i] & 1)) return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_noise_generate: bad dims");
