@@ -17,6 +17,7 @@
 
 #include "internal.cuh"
 #include "df.cuh"
+#include "fpconv.cuh"
 
 namespace lqcd {
 
@@ -209,7 +210,14 @@ __global__ void k_df_fin(const D4R *part, int nb, double *rr, double *bb) {
 }
 
 // double-float canonical -> FP64 canonical; four independent elements per thread
-// and iteration keep enough loads in flight to stream at the HBM rate
+// and iteration keep enough loads in flight to stream at the HBM rate.  The
+// exact binary32 -> binary64 widenings run on the integer units, leaving one
+// FP64 add per value for the narrow FP64 pipe (same result as the casts).
+__device__ __forceinline__ double2 join_df(float4 q) {
+  return make_double2(lqcd::f32_to_f64_bits(q.x) + lqcd::f32_to_f64_bits(q.z),
+                      lqcd::f32_to_f64_bits(q.y) + lqcd::f32_to_f64_bits(q.w));
+}
+
 __global__ void k_join_df(const float4 *__restrict__ in, double2 *out, size_t n) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -218,13 +226,9 @@ __global__ void k_join_df(const float4 *__restrict__ in, double2 *out, size_t n)
 #pragma unroll
     for (int u = 0; u < 4; ++u) q[u] = in[k + u * stride];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
-      out[k + u * stride] = make_double2((double)q[u].x + (double)q[u].z, (double)q[u].y + (double)q[u].w);
+    for (int u = 0; u < 4; ++u) out[k + u * stride] = join_df(q[u]);
   }
-  for (; k < n; k += stride) {
-    const float4 q = in[k];
-    out[k] = make_double2((double)q.x + (double)q.z, (double)q.y + (double)q.w);
-  }
+  for (; k < n; k += stride) out[k] = join_df(in[k]);
 }
 
 int df_join(lqcd_ctx *ctx, const float4 *in, double2 *out, size_t n, cudaStream_t st) {

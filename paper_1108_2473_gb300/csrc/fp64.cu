@@ -396,16 +396,22 @@ __global__ void k_fin_conv(S64 *sc, int *active, const D4 *part, int nb, int max
   s.rho = rho_new;
 }
 
-// partial |a - b|^2 -> .c and |a|^2 -> .d (canonical full fields), for the true residual
+// partial |r|^2 -> .c and |b|^2 -> .d (canonical full fields), for the true
+// residual; SAME (r == b) sums once and copies, halving the FP64-pipe work
+template <bool SAME>
 __global__ void __launch_bounds__(RED_THREADS) k_norms64(size_t n, const double2 *r, const double2 *b, D4 *part) {
   int rhs = blockIdx.y;
   size_t off = (size_t)rhs * n;
   D4 acc = {0, 0, 0, 0};
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-    double2 x = r[off + k], y = b[off + k];
+    double2 x = r[off + k];
     acc.c += x.x * x.x + x.y * x.y;
-    acc.d += y.x * y.x + y.y * y.y;
+    if (!SAME) {
+      double2 y = b[off + k];
+      acc.d += y.x * y.x + y.y * y.y;
+    }
   }
+  if (SAME) acc.d = acc.c;
   D4 rr = block_sum4(acc);
   if (threadIdx.x == 0) part[(size_t)rhs * gridDim.x + blockIdx.x] = rr;
 }
@@ -450,7 +456,7 @@ int fp64_true_residual(lqcd_ctx *ctx, const double2 *b, const double2 *x, int nr
                       nrhs);
     if (rc) return rc;
   }
-  KL k_norms64<<<dim3(nb, nrhs), RED_THREADS, 0, st>>>(stride, res, b, part);
+  KL k_norms64<false><<<dim3(nb, nrhs), RED_THREADS, 0, st>>>(stride, res, b, part);
   LQCD_LAUNCH_CHECK(ctx, "k_norms64");
   KL k_fin_norms<<<nrhs, 32, 0, st>>>(part, nb, d_rr, d_bb);
   LQCD_LAUNCH_CHECK(ctx, "k_fin_norms");
@@ -521,7 +527,7 @@ int fp64_residual_into(lqcd_ctx *ctx, const double2 *b, const double2 *x, double
       LQCD_LAUNCH_CHECK(ctx, "k_resid64");
     }
   } else {
-    KL k_norms64<<<dim3(nb, nrhs), RED_THREADS, 0, st>>>(stride, b, b, part);
+    KL k_norms64<true><<<dim3(nb, nrhs), RED_THREADS, 0, st>>>(stride, b, b, part);
     LQCD_LAUNCH_CHECK(ctx, "k_norms64");
   }
   KL k_fin_norms<<<nrhs, 32, 0, st>>>(part, nb, d_rr, d_bb);

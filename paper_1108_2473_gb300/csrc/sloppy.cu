@@ -43,6 +43,7 @@
 
 #include "internal.cuh"
 #include "df.cuh"
+#include "fpconv.cuh"
 
 #include "sloppy.cuh"
 
@@ -1259,13 +1260,29 @@ __global__ void __launch_bounds__(ST) k_cvt64to32_both(Geom g, const double2 *__
     const double2 *q = src + ((size_t)rhs * g.V + 2 * (size_t)i) * 12;
     const double sc = scale[rhs];
     const int ef = even_first(g, i);
+    // scale = m 2^e: the power of two goes into the integer rounding to binary32,
+    // m is one FP32 multiply, so the FP64 pipe does no work for a normal scale
+    int e2;
+    float m;
+    const bool split = lqcd::split_pow2(sc, e2, m);
     float2 v[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) v[k] = make_float2((float)(q[k].x * sc), (float)(q[k].y * sc));
-    (ef ? de : dodd).store(rhs, i, v);
+    for (int h = 0; h < 2; ++h) {
+      if (split) {
 #pragma unroll
-    for (int k = 0; k < 12; ++k) v[k] = make_float2((float)(q[12 + k].x * sc), (float)(q[12 + k].y * sc));
-    (ef ? dodd : de).store(rhs, i, v);
+        for (int k = 0; k < 12; ++k) {
+          const double2 a = q[12 * h + k];
+          v[k] = make_float2(lqcd::f64_to_f32_bits(a.x, e2) * m, lqcd::f64_to_f32_bits(a.y, e2) * m);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          const double2 a = q[12 * h + k];
+          v[k] = make_float2((float)(a.x * sc), (float)(a.y * sc));
+        }
+      }
+      ((ef != 0) == (h == 0) ? de : dodd).store(rhs, i, v);
+    }
   }
 }
 

@@ -53,4 +53,8 @@ def test_kappa_zero_solution_is_the_source(prec):
         got = x.cpu().numpy()
     assert rc == 0
     assert rel_err(got, b) <= 1e-10
-    assert all(s["true_rel_residual"] <= 1e-10 and s["iterations"] <= 4 for s in st)
+    # On D = 1 a sloppy iteration is exact up to rounding the direction to the
+    # sloppy type, so each one cuts the residual by about 2^-p (p = 8 significand
+    # bits for BF16, 11 for FP16): 1e-10 = 2^-33.2 takes ceil(33.2 / p) of them.
+    max_it = {"fp64": 4, "bf16": 5, "fp16": 4}[prec]
+    assert all(s["true_rel_residual"] <= 1e-10 and s["iterations"] <= max_it for s in st)
