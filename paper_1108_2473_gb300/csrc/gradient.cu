@@ -69,77 +69,80 @@ __global__ void k_adj_source(Geom g, const double2 *__restrict__ src, const doub
   for (int k = 0; k < 12; ++k) out[k] = (k >= 6) ? make_double2(-o[k].x, -o[k].y) : o[k];  // gamma5
 }
 
-// (1 + S gamma_mu) psi for a full spinor (DeGrand-Rossi), S = +-1
-template <int MU, int S>
-__device__ __forceinline__ void proj_full(const double2 p[12], double2 q[12]) {
+// Upper two spin components of (1 + S gamma_mu) v (DeGrand-Rossi), S = +-1.
+// (1 + S gamma_mu) / 2 is a Hermitian projector whose lower two components are
+// a phase times a swap of the upper two, so for any chi, phi
+//   chi^+ (1 + S gamma_mu) phi = sum_{a=0,1} conj(h(chi)_a) . h(phi)_a,
+// h = these upper components: half the spin sum of the full outer product.
+// chi = gamma5 y flips the sign of the lower spins of y (G5 = -1 here).
+template <int MU, int S, int G5>
+__device__ __forceinline__ void half_proj(const double2 *__restrict__ v, double2 h[6]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const double2 p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
-    double2 g0, g1, g2, g3;  // gamma_mu psi
+    const double2 p0 = v[c], p1 = v[3 + c];
+    double2 p2 = v[6 + c], p3 = v[9 + c];
+    if (G5 < 0) {
+      p2 = cscale(p2, -1.0);
+      p3 = cscale(p3, -1.0);
+    }
+    double2 g0, g1;  // upper components of gamma_mu v
     if (MU == 0) {
       g0 = cmuli(p3); g1 = cmuli(p2);
-      g2 = cscale(cmuli(p1), -1.0); g3 = cscale(cmuli(p0), -1.0);
     } else if (MU == 1) {
-      g0 = cscale(p3, -1.0); g1 = p2; g2 = p1; g3 = cscale(p0, -1.0);
+      g0 = cscale(p3, -1.0); g1 = p2;
     } else if (MU == 2) {
       g0 = cmuli(p2); g1 = cscale(cmuli(p3), -1.0);
-      g2 = cscale(cmuli(p0), -1.0); g3 = cmuli(p1);
     } else {
-      g0 = p2; g1 = p3; g2 = p0; g3 = p1;
+      g0 = p2; g1 = p3;
     }
-    q[c] = S > 0 ? cadd(p0, g0) : csub(p0, g0);
-    q[3 + c] = S > 0 ? cadd(p1, g1) : csub(p1, g1);
-    q[6 + c] = S > 0 ? cadd(p2, g2) : csub(p2, g2);
-    q[9 + c] = S > 0 ? cadd(p3, g3) : csub(p3, g3);
+    h[c] = S > 0 ? cadd(p0, g0) : csub(p0, g0);
+    h[3 + c] = S > 0 ? cadd(p1, g1) : csub(p1, g1);
   }
 }
 
-// out_ij += sum_a conj(a_ai) b_aj  (spin-summed colour outer product)
-__device__ __forceinline__ void outer_acc(const double2 a[12], const double2 b[12], double2 out[3][3]) {
+// out_ij += sum_{a=0,1} conj(a_ai) b_aj
+__device__ __forceinline__ void outer_acc2(const double2 a[6], const double2 b[6], double2 out[3][3]) {
 #pragma unroll
-  for (int sp = 0; sp < 4; ++sp)
+  for (int sp = 0; sp < 2; ++sp)
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) out[i][j] = cadd(out[i][j], cmulc(a[sp * 3 + i], b[sp * 3 + j]));
 }
 
-__device__ __forceinline__ void load_chi(const double2 *y, double2 v[12]) {  // chi = gamma5 y
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    double2 q = y[k];
-    v[k] = k >= 6 ? make_double2(-q.x, -q.y) : q;
-  }
-}
-
+// Link (s, MU): X = sum_r chi_r(x)^+ (1 - gamma_mu) phi_r(x+mu) and
+// Y = sum_r chi_r(x+mu)^+ (1 + gamma_mu) phi_r(x) as colour matrices, summed
+// over the right-hand sides in order; then the d/dkappa link term and dU.
 template <int MU>
-__device__ __forceinline__ void force_link(const Geom &g, int s, const int c[4], const double2 *__restrict__ U,
-                                           const double2 *__restrict__ y, const double2 *__restrict__ phi, int nrhs,
-                                           double kappa, double weight, double2 *dU, double &dk) {
-  int cn[4] = {c[0], c[1], c[2], c[3]};
-  cn[MU] = (c[MU] + 1 == g.L[MU]) ? 0 : c[MU] + 1;
-  const int sn = site_of(g, cn);
+__device__ __forceinline__ double force_link(const Geom &g, int s, const double2 *__restrict__ U,
+                                             const double2 *__restrict__ y, const double2 *__restrict__ phi,
+                                             int nrhs, double kappa, double weight, double2 *dU) {
+  int c[4];
+  c[0] = s % g.L[0];
+  int rem = s / g.L[0];
+  c[1] = rem % g.L[1];
+  rem /= g.L[1];
+  c[2] = rem % g.L[2];
+  c[3] = rem / g.L[2];
   const double sgn = (MU == 3 && c[3] == g.L[3] - 1) ? -1.0 : 1.0;
+  c[MU] = (c[MU] + 1 == g.L[MU]) ? 0 : c[MU] + 1;
+  const int sn = site_of(g, c);
   double2 X[3][3], Y[3][3];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) X[i][j] = Y[i][j] = make_double2(0.0, 0.0);
   const size_t stride = (size_t)g.V * 12;
+  const double2 *yx = y + (size_t)s * 12, *yn = y + (size_t)sn * 12;
+  const double2 *px = phi + (size_t)s * 12, *pn = phi + (size_t)sn * 12;
   for (int r = 0; r < nrhs; ++r) {
-    double2 chx[12], chn[12], pn[12], px[12], q[12];
-    load_chi(y + r * stride + (size_t)s * 12, chx);
-    load_chi(y + r * stride + (size_t)sn * 12, chn);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      pn[k] = phi[r * stride + (size_t)sn * 12 + k];
-      px[k] = phi[r * stride + (size_t)s * 12 + k];
-    }
-    // X += chi(x)^+ (1 - gamma_mu) phi(x+mu);  Y += chi(x+mu)^+ (1 + gamma_mu) phi(x)
-    proj_full<MU, -1>(pn, q);
-    outer_acc(chx, q, X);
-    proj_full<MU, +1>(px, q);
-    outer_acc(chn, q, Y);
+    double2 a[6], b[6];
+    half_proj<MU, -1, -1>(yx + r * stride, a);
+    half_proj<MU, -1, 1>(pn + r * stride, b);
+    outer_acc2(a, b, X);
+    half_proj<MU, 1, -1>(yn + r * stride, a);
+    half_proj<MU, 1, 1>(px + r * stride, b);
+    outer_acc2(a, b, Y);
   }
   const double2 *u = U + ((size_t)s * 4 + MU) * 9;
   double2 *o = dU ? dU + ((size_t)s * 4 + MU) * 9 : nullptr;
@@ -158,32 +161,32 @@ __device__ __forceinline__ void force_link(const Geom &g, int s, const int c[4],
         o[i * 3 + j] = cadd(o[i * 3 + j], make_double2(f * (gx.x + gy.x), f * (gx.y + gy.y)));
       }
     }
-  dk += weight * sgn * acc;
+  return weight * sgn * acc;
 }
 
-// one thread per site, all four links; fixed-order block sums of d loss / d kappa
-__global__ void __launch_bounds__(128) k_force(Geom g, const double2 *__restrict__ U, const double2 *__restrict__ y,
-                                               const double2 *__restrict__ phi, int nrhs, double kappa, double weight,
-                                               double2 *dU, double *dk_part) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+// One thread per link: blocks 4 k .. 4 k + 3 hold directions 0..3 of the same
+// FORCE_SITES sites, so the four read the same x-site spinors close in time;
+// fixed-order block sums of d loss / d kappa.
+constexpr int FORCE_SITES = 128;
+__global__ void __launch_bounds__(FORCE_SITES) k_force(Geom g, const double2 *__restrict__ U,
+                                                       const double2 *__restrict__ y,
+                                                       const double2 *__restrict__ phi, int nrhs, double kappa,
+                                                       double weight, double2 *dU, double *dk_part) {
+  const int mu = blockIdx.x & 3;
+  const int s = (blockIdx.x >> 2) * FORCE_SITES + threadIdx.x;
   double dk = 0.0;
   if (s < g.V) {
-    int c[4];
-    c[0] = s % g.L[0];
-    int r = s / g.L[0];
-    c[1] = r % g.L[1];
-    r /= g.L[1];
-    c[2] = r % g.L[2];
-    c[3] = r / g.L[2];
-    force_link<0>(g, s, c, U, y, phi, nrhs, kappa, weight, dU, dk);
-    force_link<1>(g, s, c, U, y, phi, nrhs, kappa, weight, dU, dk);
-    force_link<2>(g, s, c, U, y, phi, nrhs, kappa, weight, dU, dk);
-    force_link<3>(g, s, c, U, y, phi, nrhs, kappa, weight, dU, dk);
+    switch (mu) {
+      case 0: dk = force_link<0>(g, s, U, y, phi, nrhs, kappa, weight, dU); break;
+      case 1: dk = force_link<1>(g, s, U, y, phi, nrhs, kappa, weight, dU); break;
+      case 2: dk = force_link<2>(g, s, U, y, phi, nrhs, kappa, weight, dU); break;
+      default: dk = force_link<3>(g, s, U, y, phi, nrhs, kappa, weight, dU); break;
+    }
   }
-  __shared__ double sh[128];
+  __shared__ double sh[FORCE_SITES];
   sh[threadIdx.x] = dk;
   __syncthreads();
-  for (int w = 64; w > 0; w >>= 1) {
+  for (int w = FORCE_SITES / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
     __syncthreads();
   }
@@ -211,7 +214,7 @@ extern "C" int lqcd_gradient(lqcd_ctx *ctx, const double *src, const double *sol
   if (!is_device_ptr(src) || !is_device_ptr(sol))
     return set_error(ctx, LQCD_ERR_INVALID, "lqcd_gradient: src and sol must be device memory");
   int rc = LQCD_OK;
-  const int nblk = (g.V + 127) / 128;
+  const int nblk = 4 * ((g.V + FORCE_SITES - 1) / FORCE_SITES);
   Carver sizing(nullptr);
   sizing.take<double2>(field);
   sizing.take<double2>(field);
@@ -232,8 +235,8 @@ extern "C" int lqcd_gradient(lqcd_ctx *ctx, const double *src, const double *sol
   int src_rc = params->precision == LQCD_PREC_FP64 ? fp64_solve(ctx, eta, y, nrhs, *params, stats, st)
                                                    : mixed_solve(ctx, eta, y, nrhs, *params, stats, st);
   if (src_rc == LQCD_ERR_CUDA || src_rc == LQCD_ERR_OOM || src_rc == LQCD_ERR_INVALID) return src_rc;
-  KL k_force<<<nblk, 128, 0, st>>>(g, ctx->U64, y, (const double2 *)sol, nrhs, ctx->kappa, weight, (double2 *)dU,
-                                   dk_part);
+  KL k_force<<<nblk, FORCE_SITES, 0, st>>>(g, ctx->U64, y, (const double2 *)sol, nrhs, ctx->kappa, weight,
+                                           (double2 *)dU, dk_part);
   LQCD_LAUNCH_CHECK(ctx, "k_force");
   std::vector<double> h(nblk);
   LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), dk_part, nblk * sizeof(double), cudaMemcpyDeviceToHost, st));
