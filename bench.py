@@ -223,7 +223,8 @@ def gradient_step(L, h, src, x, params, dev, stream):
 def config_runs(L, h, dev, stream):
     """The truncated solver method run (400 undiluted low-precision vectors to 1e-3 plus
     20 high-precision corrections to 1e-10, on the bench field) and the uneven batch of
-    four lattices in one graph, each timed once after a warm-up."""
+    four lattices in one graph, each timed once after a warm-up; then each lattice of
+    the batch alone (mixed solve with its hop roofline, plain FP64 sample)."""
     import numpy as np
     import torch
     from lattice_inputs import eps_su3_field, haar_su3_field
@@ -280,6 +281,33 @@ def config_runs(L, h, dev, stream):
             per.append({"lattice": "x".join(map(str, dims)), "field": kind, "kappa": kappa, "rhs": n,
                         "iterations_max": max(r["iterations"] for r in s_),
                         "max_true_rel_residual": max(r["true_rel_residual"] for r in s_)})
+        # each lattice alone: autotuned mixed solve (solves/s, hop GB/s and fraction of
+        # measured HBM) and the plain single-RHS FP64 solver on a two-source sample
+        peak, _ = _peaks()
+        p64 = L.solver_params(tol=1e-10, precision=L.LQCD_PREC_FP64, rhs_block=1)
+        for rec, hk, (b, xk) in zip(per, handles, bufs):
+            n = b.shape[0]
+            L.lqcd_autotune(hk, n, solver.precision)
+            L.lqcd_solve_batch(hk, b, xk, solver)  # warm-up
+            torch.cuda.synchronize(dev)
+            L.lqcd_profile_begin(hk)
+            t0 = time.perf_counter()
+            rc_k, _ = L.lqcd_solve_batch(hk, b, xk, solver)
+            torch.cuda.synchronize(dev)
+            tk = time.perf_counter() - t0
+            pk = L.lqcd_profile_end(hk)
+            hop_gbs = pk["hop_bytes"] / (pk["hop_ms"] / 1e3) / 1e9 if pk["hop_ms"] > 0 else 0.0
+            x64 = torch.empty_like(b[:2])
+            L.lqcd_solve_batch(hk, b[:1].contiguous(), x64[:1], p64)  # warm-up
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            rc64, _ = L.lqcd_solve_batch(hk, b[:2].contiguous(), x64, p64)
+            torch.cuda.synchronize(dev)
+            r64 = 2 / (time.perf_counter() - t0)
+            rec.update({"alone_solves_per_s": n / tk, "alone_status": rc_k, "hop_GBps": hop_gbs,
+                        "hop_frac_of_hbm": hop_gbs / peak, "hop_share": pk["hop_ms"] / 1e3 / tk,
+                        "fp64_plain_solves_per_s": r64, "fp64_status": rc64, "mixed_vs_plain_fp64": n / tk / r64})
+            del x64
         out["uneven_batch"] = {"rhs": total, "s": t, "solves_per_s": total / t, "status": rc, "lattices": per}
     finally:
         L.lqcd_batch_destroy(batch)
