@@ -403,7 +403,23 @@ __global__ void __launch_bounds__(RED_THREADS) k_norms64(size_t n, const double2
   int rhs = blockIdx.y;
   size_t off = (size_t)rhs * n;
   D4 acc = {0, 0, 0, 0};
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  // four elements loaded before they are summed (in the same order as one at a time)
+  for (; k + 3 * stride < n; k += 4 * stride) {
+    double2 x[4], y[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      x[u] = r[off + k + u * stride];
+      if (!SAME) y[u] = b[off + k + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc.c += x[u].x * x[u].x + x[u].y * x[u].y;
+      if (!SAME) acc.d += y[u].x * y[u].x + y[u].y * y[u].y;
+    }
+  }
+  for (; k < n; k += stride) {
     double2 x = r[off + k];
     acc.c += x.x * x.x + x.y * x.y;
     if (!SAME) {
