@@ -977,10 +977,6 @@ static void launch_hop_pair(int variant, int G, cudaStream_t q, const lqcd_ctx *
 __device__ __forceinline__ CP scal_pair(double2 a, double2 b) {
   return CP{make_float2((float)a.x, (float)b.x), make_float2((float)a.y, (float)b.y)};
 }
-// (s * z) for complex pairs
-__device__ __forceinline__ CP cp_mul(const CP &s, const CP &z) {
-  return CP{S2(M2(s.re, z.re), M2(s.im, z.im)), F2(s.re, z.im, M2(s.im, z.re))};
-}
 // a + s * z and a - s * z
 __device__ __forceinline__ CP cp_fma(const CP &s, const CP &z, const CP &a) {
   return CP{S2(F2(s.re, z.re, a.re), M2(s.im, z.im)), F2(s.re, z.im, F2(s.im, z.re, a.im))};
@@ -1153,70 +1149,6 @@ __global__ void __launch_bounds__(ST) k_pair_copy(int vh, const int *flags, F32F
 }
 
 // ============================================ precision conversion kernels
-// dst (FP32 parity field) = scale[rhs] * src (canonical FP64 [rhs][V][12]) on parity p
-__global__ void __launch_bounds__(ST) k_cvt64to32(Geom g, int p, const double2 *__restrict__ src, F32F dst,
-                                                  const double *scale, const int *list, const int *count, int nbx) {
-  const int n_items = *count * nbx;
-  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const int rhs = list[w / nbx];
-    const int i = (w % nbx) * ST + threadIdx.x;
-    if (i >= g.Vh) continue;
-    int c[4];
-    coords_of(g, p, i, c);
-    const double2 *q = src + ((size_t)rhs * g.V + site_of(g, c)) * 12;
-    double sc = scale[rhs];
-    float2 v[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) v[k] = make_float2((float)(q[k].x * sc), (float)(q[k].y * sc));
-    dst.store(rhs, i, v);
-  }
-}
-
-// dst (FP32 parity field) = scale[rhs] * src (canonical FP32 [rhs][V][12]) on parity p
-__global__ void __launch_bounds__(ST) k_cvt32to32(Geom g, int p, const float2 *__restrict__ src, F32F dst,
-                                                  const double *scale, const int *list, const int *count, int nbx) {
-  const int n_items = *count * nbx;
-  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const int rhs = list[w / nbx];
-    const int i = (w % nbx) * ST + threadIdx.x;
-    if (i >= g.Vh) continue;
-    int c[4];
-    coords_of(g, p, i, c);
-    const float2 *q = src + ((size_t)rhs * g.V + site_of(g, c)) * 12;
-    const float sc = (float)scale[rhs];
-    float2 v[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) v[k] = make_float2(q[k].x * sc, q[k].y * sc);
-    dst.store(rhs, i, v);
-  }
-}
-
-// x (double-float canonical) += scale[rhs] * src (FP32 parity field) on parity p
-__global__ void __launch_bounds__(ST) k_accum_df(Geom g, int p, F32F src, float4 *x, const double *scale,
-                                                 const int *list, const int *count, int nbx) {
-  const int n_items = *count * nbx;
-  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const int rhs = list[w / nbx];
-    const int i = (w % nbx) * ST + threadIdx.x;
-    if (i >= g.Vh) continue;
-    int c[4];
-    coords_of(g, p, i, c);
-    float4 *q = x + ((size_t)rhs * g.V + site_of(g, c)) * 12;
-    const double scd = scale[rhs];
-    const float sh = (float)scd;
-    const dfl sc{sh, (float)(scd - (double)sh)};
-    float2 v[12];
-    src.load(rhs, i, v);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      float4 o = q[k];
-      dfl re = df_norm(dfl{o.x, o.z} + sc * dfl{v[k].x, 0.f});
-      dfl im = df_norm(dfl{o.y, o.w} + sc * dfl{v[k].y, 0.f});
-      q[k] = make_float4(re.h, im.h, re.l, im.l);
-    }
-  }
-}
-
 // Both parities at once: parity-local index i owns canonical sites 2i and 2i+1
 // (one even, one odd), so each thread's canonical data is one contiguous run.
 __device__ __forceinline__ int even_first(const Geom &g, int i) {  // is site 2i the even one?
@@ -1339,25 +1271,6 @@ __global__ void __launch_bounds__(ACC_SITES * 2) k_accum_df_both(Geom g, F32F e,
       for (int k = threadIdx.x; k < nloc * 24; k += blockDim.x) base[k] = tile[k];
     }
     __syncthreads();
-  }
-}
-
-// x (canonical FP64) += scale[rhs] * src (FP32 parity field) on parity p
-__global__ void __launch_bounds__(ST) k_accum64(Geom g, int p, F32F src, double2 *x, const double *scale,
-                                                const int *list, const int *count, int nbx) {
-  const int n_items = *count * nbx;
-  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const int rhs = list[w / nbx];
-    const int i = (w % nbx) * ST + threadIdx.x;
-    if (i >= g.Vh) continue;
-    int c[4];
-    coords_of(g, p, i, c);
-    double2 *q = x + ((size_t)rhs * g.V + site_of(g, c)) * 12;
-    double sc = scale[rhs];
-    float2 v[12];
-    src.load(rhs, i, v);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) q[k] = make_double2(q[k].x + sc * (double)v[k].x, q[k].y + sc * (double)v[k].y);
   }
 }
 
