@@ -20,7 +20,10 @@ Gamma order: 1, gamma5, gamma1, gamma2, gamma3, gamma4.
 Parity: pinned by the free-field momentum sum, the hopping expansion to
 O(kappa^4), gauge invariance, reality and charge-conjugation properties, and
 the reduction of fully (site-)diluted noise to the exact loop
-(tests/test_oracle_loops.py, tests/test_oracle_tsm.py).
+(tests/test_oracle_loops.py, tests/test_oracle_tsm.py).  The TSM correction's
+weight 1/N_HP and sign are pinned by single-site pieces (t+s+c and cubic
+dilution on 2^3 x 4), where the LP estimate is the same truncated diagonal for
+every noise vector and the TSM estimate must equal the exact loops.
 """
 from __future__ import annotations
 

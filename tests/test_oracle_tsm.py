@@ -61,3 +61,29 @@ def test_tsm_same_sets_telescopes_to_hp():
     assert np.max(np.abs((acc_lp + acc_corr) - acc_hp)) < 1e-12
     # and the LP-only estimate really is different (truncated)
     assert np.max(np.abs(acc_lp - acc_hp)) > 1e-6
+
+
+def test_tsm_with_single_site_pieces_equals_exact_loops():
+    """The weight and sign of the TSM correction (Sec. II; Bali et al.).
+
+    On 2^3 x 4 with time+spin+colour and cubic dilution every piece is one
+    (site, spin, colour) times a phase c with |c| = 1.  BiCGstab from x = 0 is
+    equivariant under b -> c b (every Krylov vector scales by c, every scalar is
+    unchanged, the relative stopping rule is scale free), so the low-precision
+    estimate is the same truncated diagonal for every noise vector of either
+    stream.  The LP mean over 3 vectors plus the (HP - LP) mean over 2 vectors
+    must then reproduce the exact loops: a correction weighted 1/n_lp instead of
+    1/n_hp, dropped, or added with the wrong sign leaves the truncation error.
+    """
+    from oracle.loops import exact_loops_dense
+    from oracle.philox import DIL_CUBE
+    U = haar_su3_field(DIMS, 0)
+    kappa = 0.125
+    scheme = DIL_TSC | DIL_CUBE
+    exact = exact_loops_dense(U, kappa)
+    tsm = tsm_loops(U, kappa, DIMS, 11, n_lp=3, n_hp=2, tol_lp=1e-2, tol_hp=1e-13, scheme=scheme)
+    scale = np.max(np.abs(exact))
+    assert np.max(np.abs(tsm - exact)) < 1e-10 * scale
+    # teeth: the low-precision estimate alone is visibly truncated
+    lp_only = stochastic_loops(U, kappa, DIMS, 11, range(3), scheme, tol=1e-2)
+    assert np.max(np.abs(lp_only - exact)) > 1e-4 * scale
