@@ -323,6 +323,105 @@ def config_runs(L, h, dev, stream):
     return out
 
 
+# ------------------------------------------- GPU idle time inside one step
+def gpu_idle(step_fn, stream, dev):
+    """One untimed step under torch.profiler (CUPTI kernel records): the step's
+    CUDA-event time, the summed device time of its kernels and copies, and the
+    difference (time the GPU waited on the host: polls, launches)."""
+    import torch
+    try:
+        from torch.profiler import profile, ProfilerActivity
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        with profile(activities=[ProfilerActivity.CUDA]) as pr:
+            a.record(stream)
+            step_fn()
+            b.record(stream)
+            b.synchronize()
+        step_ms = a.elapsed_time(b)
+        busy_us = sum(e.self_device_time_total for e in pr.key_averages())
+        n_kernels = sum(e.count for e in pr.key_averages() if e.self_device_time_total > 0)
+        return {"step_ms": step_ms, "device_busy_ms": busy_us / 1e3, "idle_ms": step_ms - busy_us / 1e3,
+                "idle_frac": 1.0 - busy_us / 1e3 / step_ms, "device_activities": n_kernels,
+                "note": "one extra step under torch.profiler, not a timed step"}
+    except Exception as ex:  # profiler unavailable: report why
+        return {"error": f"{type(ex).__name__}: {ex}"[:200]}
+
+
+# --------------------------------------------- the paper's exact-loop configuration
+def _cfg0_oracle_worker(args):
+    """Oracle FP64 even-odd BiCGstab on a chunk of the 4^4 point sources (timed)."""
+    sites, = args
+    import numpy as np
+    from lattice_inputs import haar_su3_field
+    from oracle.loops import point_source
+    from oracle.solver import solve
+    dims = (4, 4, 4, 4)
+    U = haar_su3_field(dims, 0)
+    lx, ly, lz, lt = dims
+    src = []
+    for s in sites:
+        x, y, z, t = s % lx, (s // lx) % ly, (s // (lx * ly)) % lz, s // (lx * ly * lz)
+        src += [point_source(dims, (t, z, y, x), sp, c) for sp in range(4) for c in range(3)]
+    src = np.stack(src)
+    t0 = time.perf_counter()
+    solve(U, 0.125, src, tol=1e-10)
+    return time.perf_counter() - t0, len(src)
+
+
+def cfg0_run(L, dev, with_oracle):
+    """All 3072 point-source FP64 solves on 4^4 (Haar seed 0, kappa = 0.125) and the
+    exact loops per site and per time slice: the batched FP64 solver, the plain
+    single-RHS FP64 solver, and the oracle on the host cores (all 3072 sources)."""
+    import numpy as np
+    import torch
+    from lattice_inputs import haar_su3_field
+    dims = (4, 4, 4, 4)
+    V = 256
+    U = haar_su3_field(dims, 0)
+    out = {"sources": 3072}
+    h = L.lqcd_create(dims, dev.index or 0)
+    try:
+        L.lqcd_set_gauge(h, torch.from_numpy(U.reshape(-1)).to(dev))
+        L.lqcd_set_kappa(h, 0.125)
+        src = torch.empty((3072, V, 4, 3), dtype=torch.complex128, device=dev)
+        L.lqcd_point_sources(h, list(range(V)), src)
+        x = torch.empty_like(src)
+        for name, blk in (("fp64_batched", 3072), ("fp64_plain", 1)):
+            p = L.solver_params(tol=1e-10, precision=L.LQCD_PREC_FP64, rhs_block=blk)
+            L.lqcd_solve_batch(h, src[:blk], x[:blk], p)  # warm-up
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            rc, st = L.lqcd_solve_batch(h, src, x, p)
+            torch.cuda.synchronize(dev)
+            t = time.perf_counter() - t0
+            out[name] = {"solves_per_s": 3072 / t, "s": t, "status": rc,
+                         "max_true_rel_residual": max(r["true_rel_residual"] for r in st)}
+        ps = torch.zeros((V, 6), dtype=torch.complex128, device=dev)
+        pt = torch.zeros((4, 6), dtype=torch.complex128, device=dev)
+        L.lqcd_loops_batch(h, src, x, 1.0, ps, pt)
+        got = ps.cpu().numpy().reshape(4, 4, 4, 4, 6)
+    finally:
+        L.lqcd_destroy(h)
+    if with_oracle:
+        from oracle.loops import exact_loops_dense
+        ref = exact_loops_dense(U, 0.125)
+        out["loops_max_rel_err_vs_oracle_dense"] = float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+        import multiprocessing as mp
+        nw = min(host_cores(), 16)
+        chunks = [list(range(V))[k::nw] for k in range(nw)]
+        t0 = time.perf_counter()
+        with mp.get_context("spawn").Pool(nw) as pool:
+            res = pool.map(_cfg0_oracle_worker, [(c,) for c in chunks])
+        wall = time.perf_counter() - t0
+        busy = max(r[0] for r in res)
+        out["oracle"] = {"solves_per_s": 3072 / busy, "cores": nw, "max_worker_s": busy, "wall_s": wall,
+                         "sample": "all 3072 point sources, split over the processes, FP64 numpy even-odd BiCGstab "
+                                   "to 1e-10"}
+    return out
+
+
 # ------------------------------------------------- kernels beyond the step
 def _event_ms(fn, stream, reps=10, warm=3):
     import torch
@@ -443,7 +542,10 @@ def run_ours(args, rank, world, local_rank):
     x = torch.empty_like(src)
     per_site = torch.zeros((V, 6), dtype=torch.complex128, device=dev)
     per_t = torch.zeros((DIMS[3], 6), dtype=torch.complex128, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    # a created stream: the solver captures its inner iterations into a CUDA
+    # graph there (the legacy default stream cannot be captured)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
 
     def step(r, host=False):
         if host:  # end to end: a new gauge configuration arrives from pinned host memory
@@ -466,14 +568,13 @@ def run_ours(args, rank, world, local_rank):
 
     from paper_1108_2473_gb300 import replicas
     # disjoint noise vectors per rank (replicas: no data-path collective)
-    idx = replicas.noise_indices(rank, world, args.warmup + 2 * args.steps + 1)
+    idx = replicas.noise_indices(rank, world, args.warmup + 2 * args.steps + 1 + args.prof_steps)
     for w in range(args.warmup):
         step(idx[w])
     # ---------------------------------------------------------- timed region
     clocks = Clocks(local_rank)
     barrier()
     clocks.start()
-    L.lqcd_profile_begin(h)
     launches0 = L.lqcd_launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -486,9 +587,15 @@ def run_ours(args, rank, world, local_rank):
     e1.record(stream)
     barrier()
     launches = L.lqcd_launch_count() - launches0
-    prof = L.lqcd_profile_end(h)
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
+    # the hop kernel's own CUDA-event timings come from a separate profiled pass
+    # (events around every hop launch; the solver then launches directly)
+    L.lqcd_profile_begin(h)
+    for k in range(args.prof_steps):
+        step(idx[args.warmup + k])
+    prof = L.lqcd_profile_end(h)
+    idle = gpu_idle(lambda: step(idx[args.warmup]), stream, dev)
     t_max = replicas.max_over_ranks(ms, device=dev)
     solves = nrhs * args.steps * world
     value = solves / (t_max / 1e3)
@@ -511,11 +618,11 @@ def run_ours(args, rank, world, local_rank):
     grad = gradient_step(L, h, src, x, params, dev, stream)
 
     # ------------------------------- plain single-RHS FP64 on a sample
-    n64 = max(1, args.fp64_rhs)
+    n64 = max(1, min(args.fp64_rhs, nrhs))
     xs = torch.empty((n64, V, 4, 3), dtype=torch.complex128, device=dev)
     L.lqcd_noise_generate(NOISE_SEED, L.LQCD_STREAM_LP, idx[args.warmup], DIMS, L.LQCD_DILUTE_TSC, 0, n64, src[:n64])
     p64 = L.solver_params(tol=TOL, precision=L.LQCD_PREC_FP64, rhs_block=1)
-    L.lqcd_solve_batch(h, src[:n64].contiguous(), xs, p64)  # warm-up
+    L.lqcd_solve_batch(h, src[:1].contiguous(), xs[:1], p64)  # warm-up
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     rc, st64 = L.lqcd_solve_batch(h, src[:n64].contiguous(), xs, p64)
@@ -523,6 +630,7 @@ def run_ours(args, rank, world, local_rank):
     fp64_rate = n64 / (time.perf_counter() - t0)
     extras = next_rows(L, h, per_site, dev, stream, not args.no_cpu, nrhs)
     configs = config_runs(L, h, dev, stream)
+    configs["cfg0_exact_4444"] = cfg0_run(L, dev, not args.no_cpu)
     gpu_piece_loops = None
     if not args.no_cpu:  # the same pieces the oracle baseline solves, for the loop error
         pcs = oracle_pieces(args.cpu_rhs)
@@ -542,7 +650,12 @@ def run_ours(args, rank, world, local_rank):
     # ---------------------------------------------------------- roofline
     peak, peak_kind = _peaks()
     hop_s = prof["hop_ms"] / 1e3
-    achieved = prof["hop_bytes"] / hop_s / 1e9 if hop_s > 0 else 0.0
+    # algorithmic bytes by the survey's count: 48 B of 16-bit spinor per output
+    # (site, RHS) plus FP16 reconstruct-12 links (8 x 24 B per site) once per launch
+    vh = V // 2
+    alg_bytes = 96.0 * prof["hop_site_rhs"] + prof["hop_launches"] * vh * 8 * 24.0
+    achieved = alg_bytes / hop_s / 1e9 if hop_s > 0 else 0.0
+    achieved_epi = prof["hop_bytes"] / hop_s / 1e9 if hop_s > 0 else 0.0
     traffic = None
     # the captured counters describe the BF16 kernel of variant 1 only
     if HOP_DRAM_BYTES_PER_SITE_RHS is not None and prof["hop_launches"] > 0 and args.prec == "bf16" \
@@ -551,13 +664,17 @@ def run_ours(args, rank, world, local_rank):
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
         "traffic": traffic, "peak_kind": peak_kind,
+        "bytes_model": "96 B per output (site, RHS) + 8 x 24 B reconstruct-12 links per site per launch",
+        "achieved_epilogue_inclusive": achieved_epi, "frac_epilogue_inclusive": achieved_epi / peak,
+        "profiled_steps": args.prof_steps,
         "kernel": f"k_hop_pair<{args.prec.upper()}> (sloppy Wilson hopping term on RHS pairs, all epilogues)",
-        "alg_bytes_per_launch": prof["hop_bytes"] / max(prof["hop_launches"], 1),
+        "alg_bytes_per_launch": alg_bytes / max(prof["hop_launches"], 1),
+        "site_rhs_per_launch": prof["hop_site_rhs"] / max(prof["hop_launches"], 1),
         "avg_launch_ms": prof["hop_ms"] / max(prof["hop_launches"], 1),
         "launches": prof["hop_launches"],
         "fp32_tflops": prof["hop_flops"] / hop_s / 1e12 if hop_s > 0 else 0.0,
         "fp32_frac_of_alu_peak": (prof["hop_flops"] / hop_s / 1e12) / FP32_PEAK_TFLOPS if hop_s > 0 else 0.0,
-        "hop_share_of_step": hop_s / (ms / 1e3),
+        "hop_share_of_step": hop_s / (args.prof_steps * ms / args.steps / 1e3),
     }
     # ------------------------------------------------------ CPU baseline
     cpu = None
@@ -584,12 +701,15 @@ def run_ours(args, rank, world, local_rank):
                    "plaquette": plaq, "blocks_per_sm": blocks_per_sm, "hop_variant": hop_variant},
         "mixed_vs_plain_fp64": value / world / fp64_rate,
         "fp64_plain": {"value": fp64_rate, "unit": "RHS solves/s", "sample_rhs": n64,
+                       "what": "plain single-RHS FP64 even-odd BiCGstab (one RHS per solve) on the first n of the "
+                               "step's diluted sources: the 16^3x32 plain-FP64 configuration",
                        "iterations": [s["iterations"] for s in st64]},
         "solver": {"iterations_min": min(iters), "iterations_max": max(iters), "max_true_rel_residual": max(resid)},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "RHS solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "gpu_idle": idle,
         "clocks": clk,
         "gradient": grad,
         "configs": configs,
@@ -607,7 +727,9 @@ def main():
     ap.add_argument("--prec", default="bf16", choices=["fp16", "bf16"])
     ap.add_argument("--delta", type=float, default=0.05, help="reliable-update threshold of the mixed solver")
     ap.add_argument("--nrhs", type=int, default=12 * DIMS[3], help="diluted sources per step (384 = all)")
-    ap.add_argument("--fp64-rhs", type=int, default=4)
+    ap.add_argument("--fp64-rhs", type=int, default=12 * DIMS[3],
+                    help="right-hand sides of the plain single-RHS FP64 sample (384 = one diluted vector)")
+    ap.add_argument("--prof-steps", type=int, default=1, help="steps of the profiled pass (hop roofline)")
     ap.add_argument("--cpu-rhs", type=int, default=16)
     ap.add_argument("--ref-rhs", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")

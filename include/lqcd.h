@@ -174,12 +174,16 @@ int lqcd_solve_batch(lqcd_ctx *ctx, const double *b, double *x, int nrhs,
  * branch per lattice) on `stream`, which must be a created stream (not the
  * legacy default); one graph launch advances every lattice by four iterations,
  * and each lattice's outer FP64 refinement runs between launches.  FP64 solves
- * the entries one after another.  stats: host array with one record per RHS in
- * the order of lqcd_batch_add.  Returns LQCD_OK only if every RHS converged. */
+ * the entries one after another.  stats: host array of n_stats records, one
+ * per RHS in the order of lqcd_batch_add; n_stats below the batch's RHS total
+ * is rejected with LQCD_ERR_INVALID before any work (lqcd_batch_rhs gives the
+ * total).  Returns LQCD_OK only if every RHS converged. */
 int lqcd_batch_create(lqcd_batch **out);
 int lqcd_batch_add(lqcd_batch *batch, lqcd_ctx *ctx, const double *b, double *x, int nrhs);
-int lqcd_batch_run(lqcd_batch *batch, const lqcd_solver_params *params, lqcd_solve_stats *stats,
+int lqcd_batch_run(lqcd_batch *batch, const lqcd_solver_params *params, lqcd_solve_stats *stats, int n_stats,
                    lqcd_stream_t stream);
+/* Total right-hand sides registered in the batch (host int).  Host only. */
+int lqcd_batch_rhs(const lqcd_batch *batch, int *total);
 int lqcd_batch_destroy(lqcd_batch *batch);
 
 /* Autotuner: time the reduced-precision hopping term for nrhs right-hand
@@ -327,26 +331,27 @@ int lqcd_gradient(lqcd_ctx *ctx, const double *src, const double *sol, int nrhs,
                   lqcd_stream_t stream);
 
 /* No-allocation variant of lqcd_loops_batch.  The paper has no counterpart:
- * this exists for callers that cannot allocate device memory -- code that
- * runs while a CUDA graph is being captured, where cudaMalloc/cudaFree are not
- * allowed or would synchronise the device; frameworks whose caching allocator
- * already holds the GPU's memory; latency-critical pipelines in which the
- * implicit device synchronisation of cudaFree would stall other streams.  It
+ * this exists for callers that cannot allocate device memory -- frameworks
+ * whose caching allocator already holds the GPU's memory, latency-critical
+ * pipelines in which the implicit device synchronisation of cudaFree would
+ * stall other streams, and services that run under a fixed memory budget.  It
  * needs no context (lqcd_create allocates) and calls no cudaMalloc, cudaFree or
  * allocating library routine.
  *
  * Same result as lqcd_loops_batch (accumulating into per_site / per_t) for the
- * lattice dims (host array of 4 ints, all even).  All arrays must be device
- * memory.  The per-time-slice partial sums use a fixed 768 KiB device array
- * inside the library: each GPU that loads the library holds it until the
- * process exits.  Limit: Lt * ceil(Lx*Ly*Lz / 128) <= 8192 when per_t is
- * given (24^3 x 48 needs 5184); larger lattices are rejected with
- * LQCD_ERR_INVALID.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture.  All calls on a device share the array, so
- * calls whose work overlaps on the GPU (different streams, or host threads)
- * race and must be serialised by the caller; every partial is rewritten by
- * each call, so nothing needs clearing in between. */
+ * lattice dims (host array of 4 ints, all even, volume <= 2^30, Lt <= 65535).
+ * All arrays must be device memory of the current device (or managed memory),
+ * and the stream must belong to that device; otherwise LQCD_ERR_INVALID.  The
+ * per-time-slice partial sums use a fixed 768 KiB device array inside the
+ * library: each GPU that loads the library holds it until the process exits.
+ * Limit: Lt * ceil(Lx*Ly*Lz / 128) <= 8192 when per_t is given (24^3 x 48
+ * needs 5184); larger lattices are rejected with LQCD_ERR_INVALID.  The first
+ * call on a device that passes per_t looks up that array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls on a device share the array, so calls
+ * whose work overlaps on the GPU (different streams, or host threads) race and
+ * must be serialised by the caller; every partial is rewritten by each call,
+ * so nothing needs clearing in between. */
 int lqcd_loops_batch_noalloc(const int dims[4], const double *src, const double *sol, int nrhs, double weight,
                              double *per_site, double *per_t, lqcd_stream_t stream);
 
@@ -372,7 +377,8 @@ int lqcd_profile_begin(lqcd_ctx *ctx);
 /* Stop recording and fill *out (host).  Synchronises the device. */
 int lqcd_profile_end(lqcd_ctx *ctx, lqcd_profile *out);
 
-/* Total kernel launches made by the library since it was loaded. */
+/* Total kernel launches made by the library since it was loaded (kernels run
+ * by a replay of a captured CUDA graph count once per replay). */
 long long lqcd_launch_count(void);
 
 #ifdef __cplusplus

@@ -224,6 +224,11 @@ extern "C" int lqcd_loops_batch_noalloc(const int dims[4], const double *src, co
     if (dims[i] < 2 || (dims[i] & 1))
       return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_loops_batch_noalloc: extent %d = %d must be even and >= 2",
                        i, dims[i]);
+  const long long vol = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+  if (vol > (1LL << 30) || dims[3] > 65535)
+    return set_error(nullptr, LQCD_ERR_INVALID,
+                     "lqcd_loops_batch_noalloc: volume %lld (limit 2^30) or Lt = %d (limit 65535) too large", vol,
+                     dims[3]);
   Geom g = make_geom(dims);
   int vs = g.L[0] * g.L[1] * g.L[2], lt = g.L[3];
   int nbx = (vs + LOOP_THREADS - 1) / LOOP_THREADS;
@@ -234,16 +239,43 @@ extern "C" int lqcd_loops_batch_noalloc(const int dims[4], const double *src, co
                      "scratch holds %d -- use lqcd_loops_batch",
                      need, LOOP_THREADS, LQCD_NOALLOC_MAX_PARTIALS);
   if (nrhs == 0 || (!per_site && !per_t)) return LQCD_OK;
+  // every array must be addressable by a kernel on the current device: device
+  // memory of this device (or managed memory), and the stream must belong to it
+  int cur = 0;
+  cudaError_t ce = cudaGetDevice(&cur);
+  if (ce != cudaSuccess) return cuda_error(nullptr, ce, "lqcd_loops_batch_noalloc: cudaGetDevice");
   const void *ptrs[4] = {src, sol, per_site, per_t};
-  for (const void *q : ptrs)
-    if (q && !is_device_ptr(q))
-      return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_loops_batch_noalloc: all arrays must be device memory");
+  const char *names[4] = {"src", "sol", "per_site", "per_t"};
+  for (int k = 0; k < 4; ++k) {
+    if (!ptrs[k]) continue;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptrs[k]) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_loops_batch_noalloc: %s is not device memory", names[k]);
+    }
+    if (a.type == cudaMemoryTypeManaged) continue;
+    if (a.type != cudaMemoryTypeDevice)
+      return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_loops_batch_noalloc: %s is not device memory", names[k]);
+    if (a.device != cur)
+      return set_error(nullptr, LQCD_ERR_INVALID,
+                       "lqcd_loops_batch_noalloc: %s is on device %d, the current device is %d", names[k], a.device,
+                       cur);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread) {
+    int sdev = -1;
+    ce = cudaStreamGetDevice(st, &sdev);
+    if (ce != cudaSuccess) return cuda_error(nullptr, ce, "lqcd_loops_batch_noalloc: cudaStreamGetDevice");
+    if (sdev != cur)
+      return set_error(nullptr, LQCD_ERR_INVALID,
+                       "lqcd_loops_batch_noalloc: the stream belongs to device %d, the current device is %d", sdev,
+                       cur);
+  }
   double2 *part = nullptr;
   if (per_t) {
     int rc = noalloc_scratch(&part);
     if (rc) return rc;
   }
-  cudaStream_t st = (cudaStream_t)stream;
   // every partial read by k_loops_fin is written by k_loops in the same call,
   // so the scratch needs no clearing
   KL k_loops<<<dim3(nbx, lt), LOOP_THREADS, 0, st>>>(g, (const double2 *)src, (const double2 *)sol, nrhs, weight,

@@ -1484,6 +1484,7 @@ struct SloppyState {
   // captured graph of four inner iterations, valid while graph_key matches
   cudaGraphExec_t graph = nullptr;
   std::vector<double> graph_key;
+  long long graph_kernels = 0;  // kernel launches one replay of the graph makes
 };
 
 void sloppy_free(lqcd_ctx *ctx) {
@@ -1852,13 +1853,19 @@ struct MixedRun {
   }
 };
 
-// capture `body(stream)` into an executable graph on stream st
+// capture `body(stream)` into an executable graph on stream st; *kernels
+// receives the number of kernel launches the body recorded (each replay makes
+// them; the capture itself launches nothing, so the library's launch counter
+// is set back)
 template <class F>
-static cudaError_t capture_graph(cudaStream_t st, F body, cudaGraphExec_t *exec) {
+static cudaError_t capture_graph(cudaStream_t st, F body, cudaGraphExec_t *exec, long long *kernels) {
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
+  const long long before = g_launches.load();
   body(st);
+  *kernels = g_launches.load() - before;
+  g_launches -= *kernels;
   e = cudaStreamEndCapture(st, &graph);
   if (e != cudaSuccess) return e;
   e = cudaGraphInstantiate(exec, graph, 0);
@@ -1891,11 +1898,13 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
       if (!ss->graph || ss->graph_key != key) {
         if (ss->graph) cudaGraphExecDestroy(ss->graph);
         ss->graph = nullptr;
-        cudaError_t e = capture_graph(st, [&](cudaStream_t q) { run.launch_iters(q, ITERS_PER_POLL); }, &ss->graph);
+        cudaError_t e = capture_graph(st, [&](cudaStream_t q) { run.launch_iters(q, ITERS_PER_POLL); }, &ss->graph,
+                                      &ss->graph_kernels);
         if (e != cudaSuccess) return cuda_error(ctx, e, "mixed: capture of the iteration graph");
         ss->graph_key = key;
       }
       LQCD_CUDA_TRY(ctx, cudaGraphLaunch(ss->graph, st));
+      g_launches += ss->graph_kernels;
     } else {
       run.launch_iters(st, ITERS_PER_POLL);
       LQCD_LAUNCH_CHECK(ctx, "mixed: iteration");
@@ -1915,7 +1924,7 @@ template <class SP>
 static int mixed_batch(std::vector<lqcd_ctx *> &ctxs, std::vector<const double2 *> &bs, std::vector<double2 *> &xs,
                        std::vector<int> &ns, const lqcd_solver_params &p, std::vector<lqcd_solve_stats *> &stats,
                        cudaStream_t st, std::vector<cudaStream_t> &side, cudaGraphExec_t *gexec,
-                       std::vector<double> *gkey) {
+                       std::vector<double> *gkey, long long *gkernels) {
   const size_t nl = ctxs.size();
   const double t0 = wall_ms();
   std::vector<MixedRun<SP>> runs;
@@ -1953,12 +1962,13 @@ static int mixed_batch(std::vector<lqcd_ctx *> &ctxs, std::vector<const double2 
           cudaEventRecord(ev[l], side[l]);
           cudaStreamWaitEvent(q, ev[l], 0);
         }
-      }, gexec);
+      }, gexec, gkernels);
       for (auto &ee : ev) cudaEventDestroy(ee);
       if (e != cudaSuccess) return cuda_error(ctxs[0], e, "batch: capture of the iteration graph");
       *gkey = key;
     }
     LQCD_CUDA_TRY(ctxs[0], cudaGraphLaunch(*gexec, st));
+    g_launches += *gkernels;
     for (auto &r : runs)
       if (!r.done) {
         int rc = r.request_count(st);
@@ -2018,6 +2028,7 @@ struct lqcd_batch {
   std::vector<cudaStream_t> side;
   cudaGraphExec_t graph = nullptr;
   std::vector<double> graph_key;
+  long long graph_kernels = 0;
   std::string err;
 };
 
@@ -2054,10 +2065,26 @@ int lqcd_batch_add(lqcd_batch *batch, lqcd_ctx *ctx, const double *b, double *x,
   return LQCD_OK;
 }
 
-int lqcd_batch_run(lqcd_batch *batch, const lqcd_solver_params *params, lqcd_solve_stats *stats,
+int lqcd_batch_rhs(const lqcd_batch *batch, int *total) {
+  if (!batch || !total) return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_batch_rhs: null argument");
+  long long n = 0;
+  for (auto &e : batch->entries) n += e.nrhs;
+  *total = (int)std::min<long long>(n, 0x7fffffff);
+  return LQCD_OK;
+}
+
+int lqcd_batch_run(lqcd_batch *batch, const lqcd_solver_params *params, lqcd_solve_stats *stats, int n_stats,
                    lqcd_stream_t stream) {
   LQCD_TRACE("lqcd_batch_run");
-  if (!batch || !params || !stats) return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_batch_run: null argument");
+  if (!batch || !params || (!stats && n_stats > 0))
+    return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_batch_run: null argument");
+  {
+    long long total = 0;
+    for (auto &e : batch->entries) total += e.nrhs;
+    if ((long long)n_stats < total)
+      return set_error(nullptr, LQCD_ERR_INVALID,
+                       "lqcd_batch_run: stats holds %d records, the batch has %lld right-hand sides", n_stats, total);
+  }
   if (batch->entries.empty()) return LQCD_OK;
   const lqcd_solver_params &p = *params;
   if (!(p.tol > 0.0) || p.max_iter <= 0 || p.precision < LQCD_PREC_FP64 || p.precision > LQCD_PREC_MIXED_BF16)
@@ -2101,8 +2128,10 @@ int lqcd_batch_run(lqcd_batch *batch, const lqcd_solver_params *params, lqcd_sol
       batch->side.push_back(s);
     }
     rc = p.precision == LQCD_PREC_MIXED_FP16
-             ? mixed_batch<F16P>(ctxs, bs, xs, ns, p, sts, st, batch->side, &batch->graph, &batch->graph_key)
-             : mixed_batch<BF16P>(ctxs, bs, xs, ns, p, sts, st, batch->side, &batch->graph, &batch->graph_key);
+             ? mixed_batch<F16P>(ctxs, bs, xs, ns, p, sts, st, batch->side, &batch->graph, &batch->graph_key,
+                                 &batch->graph_kernels)
+             : mixed_batch<BF16P>(ctxs, bs, xs, ns, p, sts, st, batch->side, &batch->graph, &batch->graph_key,
+                                  &batch->graph_kernels);
   }
   if (rc) {
     set_error(nullptr, rc, "lqcd_batch_run: %s", lqcd_last_error(ctxs[0]));

@@ -109,7 +109,8 @@ _SIGS = {
     "lqcd_loops_batch": (_i, [_vp, _vp, _vp, _i, _d, _vp, _vp, _vp]),
     "lqcd_batch_create": (_i, [ctypes.POINTER(_vp)]),
     "lqcd_batch_add": (_i, [_vp, _vp, _vp, _vp, _i]),
-    "lqcd_batch_run": (_i, [_vp, ctypes.POINTER(lqcd_solver_params), ctypes.POINTER(lqcd_solve_stats), _vp]),
+    "lqcd_batch_run": (_i, [_vp, ctypes.POINTER(lqcd_solver_params), ctypes.POINTER(lqcd_solve_stats), _i, _vp]),
+    "lqcd_batch_rhs": (_i, [_vp, ctypes.POINTER(_i)]),
     "lqcd_batch_destroy": (_i, [_vp]),
     "lqcd_autotune": (_i, [_vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "lqcd_loops_stochastic": (_i, [_vp, ctypes.POINTER(lqcd_stochastic_params), ctypes.POINTER(lqcd_solver_params),
@@ -181,15 +182,61 @@ def _dims(dims):
     return arr
 
 
+# lattice dims and device of every live context (recorded by lqcd_create), so
+# that array arguments can be checked against them before the C call
+_CTX = {}
+
+
+def _ctx_info(h):
+    info = _CTX.get(getattr(h, "value", h))
+    if info is None:
+        raise ValueError("unknown or destroyed lqcd context")
+    return info
+
+
+def _volume(dims):
+    v = 1
+    for d in dims:
+        v *= int(d)
+    return v
+
+
+def _fields(device, *specs):
+    """Check array arguments before a C call.  Each spec is (tensor or None,
+    complex element count, name[, host_ok]).  Every tensor's dtype
+    (complex128), contiguity and size are checked first, then that each is on
+    CUDA device `device` (any device when None) unless host memory is allowed."""
+    specs = [sp for sp in specs if sp[0] is not None]
+    for sp in specs:
+        t, count, name = sp[:3]
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name}: a torch tensor is required")
+        if t.dtype != torch.complex128:
+            raise ValueError(f"{name}: complex128 required, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name}: tensor must be contiguous")
+        if t.numel() != count:
+            raise ValueError(f"{name}: {t.numel()} complex elements, expected {count}")
+    for sp in specs:
+        t, name, host_ok = sp[0], sp[2], (sp[3] if len(sp) > 3 else False)
+        if t.is_cuda:
+            if device is not None and t.device.index != device:
+                raise ValueError(f"{name}: on cuda:{t.device.index}, the lattice is on cuda:{device}")
+        elif not host_ok:
+            raise ValueError(f"{name}: must be a CUDA tensor")
+
+
 # --------------------------------------------------------------------- calls
 def lqcd_create(dims, device=0):
     h = ctypes.c_void_p()
     rc = load().lqcd_create(ctypes.byref(h), _dims(dims), int(device))
     _check(rc, None)
+    _CTX[h.value] = (tuple(int(d) for d in dims), int(device))
     return h
 
 
 def lqcd_destroy(h):
+    _CTX.pop(getattr(h, "value", h), None)
     return load().lqcd_destroy(h)
 
 
@@ -199,11 +246,15 @@ def lqcd_last_error(h=None):
 
 def lqcd_set_gauge(h, U):
     """U: complex128 [V][4][3][3] (any shape with that element count), device or host."""
+    dims, dev = _ctx_info(h)
+    _fields(dev, (U, _volume(dims) * 36, "U", True))
     return _check(load().lqcd_set_gauge(h, _ptr(U), _stream(U)), h)
 
 
 def lqcd_set_gauge_general(h, U):
     """Arbitrary complex links (no SU(3) check; FP64 solves only)."""
+    dims, dev = _ctx_info(h)
+    _fields(dev, (U, _volume(dims) * 36, "U", True))
     return _check(load().lqcd_set_gauge_general(h, _ptr(U), _stream(U)), h)
 
 
@@ -219,6 +270,8 @@ def lqcd_plaquette(h):
 
 def lqcd_apply_dirac(h, inp, out, dagger=False):
     nrhs = inp.shape[0]
+    dims, dev = _ctx_info(h)
+    _fields(dev, (inp, nrhs * _volume(dims) * 12, "in"), (out, nrhs * _volume(dims) * 12, "out"))
     return _check(load().lqcd_apply_dirac(h, _ptr(inp), _ptr(out), nrhs, int(bool(dagger)), _stream(inp)), h)
 
 
@@ -229,6 +282,8 @@ def lqcd_solve_batch(h, b, x, params):
     and CUDA errors raise LqcdError.
     """
     nrhs = b.shape[0]
+    dims, dev = _ctx_info(h)
+    _fields(dev, (b, nrhs * _volume(dims) * 12, "b", True), (x, nrhs * _volume(dims) * 12, "x", True))
     stats = (lqcd_solve_stats * max(nrhs, 1))()
     rc = load().lqcd_solve_batch(h, _ptr(b), _ptr(x), nrhs, ctypes.byref(params), stats, _stream(b))
     if rc in (LQCD_ERR_INVALID, LQCD_ERR_CUDA, LQCD_ERR_NO_GAUGE, LQCD_ERR_OOM):
@@ -237,11 +292,14 @@ def lqcd_solve_batch(h, b, x, params):
 
 
 def lqcd_point_sources(h, sites, out):
+    dims, dev = _ctx_info(h)
+    _fields(dev, (out, 12 * len(sites) * _volume(dims) * 12, "out"))
     arr = (ctypes.c_int64 * len(sites))(*[int(s) for s in sites])
     return _check(load().lqcd_point_sources(h, arr, len(sites), _ptr(out), _stream(out)), h)
 
 
 def lqcd_noise_generate(seed, noise_stream, noise_index, dims, dilution, first_piece, n_pieces, out):
+    _fields(None, (out, int(n_pieces) * _volume(dims) * 12, "out"))
     rc = load().lqcd_noise_generate(int(seed), int(noise_stream), int(noise_index), _dims(dims), int(dilution),
                                     int(first_piece), int(n_pieces), _ptr(out), _stream(out))
     return _check(rc, None)
@@ -256,6 +314,8 @@ def lqcd_dilution_pieces(dims, dilution):
 
 def lqcd_loops_momentum(h, per_site, moms, out):
     """out[m, t, g] = sum_{x in t} exp(+i p_m.x) per_site[x, g]; moms: integer triples (n_x, n_y, n_z)."""
+    dims, dev = _ctx_info(h)
+    _fields(dev, (per_site, _volume(dims) * 6, "per_site"), (out, len(moms) * dims[3] * 6, "out"))
     flat = [int(v) for m in moms for v in m]
     arr = (_i * len(flat))(*flat)
     return _check(load().lqcd_loops_momentum(h, _ptr(per_site), len(moms), arr, _ptr(out), _stream(out)), h)
@@ -264,6 +324,10 @@ def lqcd_loops_momentum(h, per_site, moms, out):
 def lqcd_disconnected_correlator(loops_p, loops_mp, l3, out, unbiased=True):
     """D[t, A, B] from [n_vec, Lt, 6] loops at momenta p and -p (device tensors)."""
     n, lt = loops_p.shape[0], loops_p.shape[1]
+    _fields(loops_p.device.index,
+            (loops_p, n * lt * 6, "loops_p"),
+            (loops_mp, n * lt * 6, "loops_mp"),
+            (out, lt * 36, "out"))
     rc = load().lqcd_disconnected_correlator(_ptr(loops_p), _ptr(loops_mp), n, lt, int(l3), int(bool(unbiased)),
                                              _ptr(out), _stream(out))
     return _check(rc, None)
@@ -271,12 +335,16 @@ def lqcd_disconnected_correlator(loops_p, loops_mp, l3, out, unbiased=True):
 
 def lqcd_smear_ape(h, alpha, n_iter, out=None, stream=None):
     """APE-smear the context's spatial links (kept for lqcd_smear_gaussian); optional copy to out."""
+    dims, dev = _ctx_info(h)
+    _fields(dev, (out, _volume(dims) * 36, "out"))
     st = stream if (out is None and stream is not None) else _stream(out)
     return _check(load().lqcd_smear_ape(h, float(alpha), int(n_iter), _ptr(out), st), h)
 
 
 def lqcd_smear_gaussian(h, src, out, alpha=4.0, n_iter=50, ape_links=False, normalise=False):
     """out = (1 + alpha H)^n_iter src on each time slice (device tensors [n, V, 4, 3])."""
+    dims, dev = _ctx_info(h)
+    _fields(dev, (src, src.shape[0] * _volume(dims) * 12, "src"), (out, src.shape[0] * _volume(dims) * 12, "out"))
     rc = load().lqcd_smear_gaussian(h, _ptr(src), _ptr(out), src.shape[0], float(alpha), int(n_iter),
                                     int(bool(ape_links)), int(bool(normalise)), _stream(out))
     return _check(rc, h)
@@ -284,6 +352,13 @@ def lqcd_smear_gaussian(h, src, out, alpha=4.0, n_iter=50, ape_links=False, norm
 
 def lqcd_loops_batch(h, src, sol, weight=1.0, per_site=None, per_t=None):
     nrhs = src.shape[0]
+    dims, dev = _ctx_info(h)
+    V = _volume(dims)
+    _fields(dev,
+            (src, nrhs * V * 12, "src"),
+            (sol, nrhs * V * 12, "sol"),
+            (per_site, V * 6, "per_site"),
+            (per_t, dims[3] * 6, "per_t", True))
     st = _stream(src)
     return _check(load().lqcd_loops_batch(h, _ptr(src), _ptr(sol), nrhs, float(weight), _ptr(per_site),
                                           _ptr(per_t), st), h)
@@ -311,6 +386,13 @@ def lqcd_loops_batch_noalloc(dims, src, sol, weight=1.0, per_site=None, per_t=No
     on the current CUDA device.
     """
     nrhs = src.shape[0]
+    V = _volume(dims)
+    dev = src.device.index if src.is_cuda else None
+    _fields(dev,
+            (src, nrhs * V * 12, "src"),
+            (sol, nrhs * V * 12, "sol"),
+            (per_site, V * 6, "per_site"),
+            (per_t, dims[3] * 6, "per_t"))
     rc = load().lqcd_loops_batch_noalloc(_dims(dims), _ptr(src), _ptr(sol), nrhs, float(weight), _ptr(per_site),
                                          _ptr(per_t), _stream(src))
     return _check(rc, None)
@@ -325,6 +407,11 @@ def lqcd_gradient(h, src, sol, coef, params, weight=1.0, dU=None):
     import numpy as np
     c = np.ascontiguousarray(np.asarray(coef.cpu() if hasattr(coef, "cpu") else coef, dtype=np.complex128))
     nrhs = src.shape[0]
+    dims, dev = _ctx_info(h)
+    V = _volume(dims)
+    if c.size != dims[3] * 6:
+        raise ValueError(f"coef: {c.size} elements, expected Lt * 6 = {dims[3] * 6}")
+    _fields(dev, (src, nrhs * V * 12, "src"), (sol, nrhs * V * 12, "sol"), (dU, V * 36, "dU"))
     stats = (lqcd_solve_stats * max(nrhs, 1))()
     dk = ctypes.c_double(0.0)
     rc = load().lqcd_gradient(h, _ptr(src), _ptr(sol), nrhs, c.ctypes.data_as(ctypes.c_void_p), float(weight),
@@ -339,6 +426,8 @@ def lqcd_loops_stochastic(h, sparams, solver, per_site=None, per_t=None):
 
     Returns (status, [LP summary, HP summary]); argument and CUDA errors raise.
     """
+    dims, dev = _ctx_info(h)
+    _fields(dev, (per_site, _volume(dims) * 6, "per_site"), (per_t, dims[3] * 6, "per_t", True))
     summ = (lqcd_solve_stats * 2)()
     st = _stream(per_site) if per_site is not None else _stream(per_t)
     rc = load().lqcd_loops_stochastic(h, ctypes.byref(sparams), ctypes.byref(solver), _ptr(per_site), _ptr(per_t),
@@ -355,14 +444,28 @@ def lqcd_batch_create():
 
 
 def lqcd_batch_add(batch, ctx, b, x):
+    dims, dev = _ctx_info(ctx)
+    _fields(dev, (b, b.shape[0] * _volume(dims) * 12, "b"), (x, b.shape[0] * _volume(dims) * 12, "x"))
     return _check(load().lqcd_batch_add(batch, ctx, _ptr(b), _ptr(x), b.shape[0]), None)
 
 
-def lqcd_batch_run(batch, params, total_rhs, stream=None):
-    """Solve every registered entry; returns (status, [stats dicts in add order])."""
+def lqcd_batch_rhs(batch):
+    """Total right-hand sides registered in the batch."""
+    n = ctypes.c_int(0)
+    _check(load().lqcd_batch_rhs(batch, ctypes.byref(n)), None)
+    return n.value
+
+
+def lqcd_batch_run(batch, params, total_rhs=None, stream=None):
+    """Solve every registered entry; returns (status, [stats dicts in add order]).
+
+    total_rhs sizes the stats array (default: the batch's own count); the
+    library rejects a value below the batch's RHS total."""
+    if total_rhs is None:
+        total_rhs = lqcd_batch_rhs(batch)
     stats = (lqcd_solve_stats * max(total_rhs, 1))()
     st = ctypes.c_void_p(stream.cuda_stream) if stream is not None else _stream()
-    rc = load().lqcd_batch_run(batch, ctypes.byref(params), stats, st)
+    rc = load().lqcd_batch_run(batch, ctypes.byref(params), stats, int(total_rhs), st)
     if rc in (LQCD_ERR_INVALID, LQCD_ERR_CUDA, LQCD_ERR_NO_GAUGE, LQCD_ERR_OOM):
         raise LqcdError(rc, _err(None))
     return rc, [stats[k].as_dict() for k in range(total_rhs)]

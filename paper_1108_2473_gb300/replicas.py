@@ -28,16 +28,34 @@ def max_over_ranks(value: float, device=None) -> float:
     return float(t.item())
 
 
-def combine_loops(per_t: torch.Tensor, n_vectors_here: int, device=None):
+_HOST_GROUP = {}
+
+
+def host_group(force_new: bool = False):
+    """A process group that reduces CPU tensors: the default group when its
+    backend is gloo, otherwise (NCCL, as bench.py creates under torchrun) a gloo
+    group over the same ranks, created once.  Every rank must call this
+    together the first time (group creation is collective)."""
+    if not force_new and dist.get_backend() == "gloo":
+        return None
+    key = "forced" if force_new else "gloo"
+    if key not in _HOST_GROUP:
+        _HOST_GROUP[key] = dist.new_group(backend="gloo")
+    return _HOST_GROUP[key]
+
+
+def combine_loops(per_t: torch.Tensor, n_vectors_here: int, device=None, group=None):
     """Average per-time-slice loop sums over all ranks' noise vectors.
 
     per_t holds this rank's sum over its vectors; returns (total / n_total) on
-    every rank.  The reduction is done on a CPU-side copy, so no GPU
-    collective is involved.
+    every rank.  The reduction runs on a CPU-side copy through a gloo group
+    (host_group()), so no GPU collective is involved whatever backend the
+    default process group uses.
     """
     local = torch.view_as_real(per_t.detach().to("cpu", torch.complex128)).clone()
     n = torch.tensor([float(n_vectors_here)], dtype=torch.float64)
     if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
-        dist.all_reduce(local, op=dist.ReduceOp.SUM)
-        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        g = group if group is not None else host_group()
+        dist.all_reduce(local, op=dist.ReduceOp.SUM, group=g)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM, group=g)
     return torch.view_as_complex(local) / n.item()

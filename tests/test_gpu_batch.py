@@ -74,6 +74,11 @@ def test_uneven_batch_matches_single_solves_and_oracle():
             L.lqcd_batch_add(batch, h, bs[-1], xs[-1])
             refs.append(osolve(U, kappa, b, tol=1e-12)[0])
         total = sum(sp[3] for sp in specs)
+        assert L.lqcd_batch_rhs(batch) == total
+        # a stats array shorter than the batch is refused before any work
+        with pytest.raises(L.LqcdError) as e:
+            L.lqcd_batch_run(batch, L.solver_params(tol=1e-10, precision=L.LQCD_PREC_MIXED_FP16), total - 1, s)
+        assert e.value.code == L.LQCD_ERR_INVALID
         rc, st = L.lqcd_batch_run(batch, L.solver_params(tol=1e-10, precision=L.LQCD_PREC_MIXED_FP16), total, s)
         torch.cuda.synchronize()
         assert rc == 0 and len(st) == total and all(r["true_rel_residual"] <= 1e-10 for r in st)

@@ -20,16 +20,24 @@ def eps_field():
     return eps_su3_field(DIMS, 0.35, 1)
 
 
-def test_cfg1_sampled_oracle_solve_and_statistics(eps_field):
+@pytest.mark.parametrize("prec", ["fp64_plain", "mixed_bf16"])
+def test_cfg1_sampled_oracle_solve_and_statistics(eps_field, prec):
     """8 t+s+c-diluted vectors (384 pieces each): per-time-slice loops on the
     4x4 spatial sub-block (x, y < 4, z = 0) agree with the exact loops there
-    within the spread of the 8 vectors; one diluted piece matches the oracle."""
+    within the spread of the 8 vectors; one diluted piece matches the oracle.
+    fp64_plain is the configuration as stated: the plain single-right-hand-side
+    FP64 solver (one RHS per solve) for the 3072 noise pieces and the 6144
+    point sources of the sub-block; mixed_bf16 runs the same on the batched
+    mixed-precision solver."""
     U = eps_field
     lx, ly, lz, lt = DIMS
     sub = [(t, 0, y, x) for t in range(lt) for y in range(4) for x in range(4)]
     sub_idx = np.array([x + lx * (y + ly * (z + lz * t)) for (t, z, y, x) in sub])
     with lattice(DIMS, U, 0.120) as (L, h):
-        p = L.solver_params(tol=1e-10, precision=L.LQCD_PREC_MIXED_BF16)
+        if prec == "fp64_plain":
+            p = L.solver_params(tol=1e-10, precision=L.LQCD_PREC_FP64, rhs_block=1)
+        else:
+            p = L.solver_params(tol=1e-10, precision=L.LQCD_PREC_MIXED_BF16)
         src = torch.empty((384, V, 4, 3), dtype=torch.complex128, device="cuda")
         x = torch.empty_like(src)
         per = []

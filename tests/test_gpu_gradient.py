@@ -153,3 +153,41 @@ def test_loopsfn_full_size_mixed_vs_finite_differences():
         assert abs(analytic - fdl) < 1e-4 * abs(fdl) + 1e-9
     finally:
         lat.close()
+
+
+def test_dkappa_full_size_mixed_matches_oracle_sample():
+    """16^3 x 32, eps = 0.35, kappa = 0.120: d/dkappa of sum_x Tr[G] and of
+    sum_x Tr[g4 G] (real and imaginary parts) from the mixed-precision adjoint
+    solves of two t+s+c-diluted pieces, against the oracle's estimator for the
+    same pieces solved to 1e-12 (four spawned oracle processes)."""
+    import multiprocessing as mp
+    from tests import _oracle_pool
+    from oracle.philox import DIL_TSC
+    from paper_1108_2473_gb300 import lqcd as L
+    dims = (16, 16, 16, 32)
+    V = int(np.prod(dims))
+    kappa = 0.120
+    pieces = [12 * 3 + 1, 12 * 17 + 8]
+    jobs = [(dims, 0.35, 1, kappa, 99, 0, DIL_TSC, pc, g, 1e-12) for g in (0, 5) for pc in pieces]
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        pending = pool.map_async(_oracle_pool.dkappa_piece, jobs)
+        U = eps_su3_field(dims, 0.35, 1)
+        with lattice(dims, U, kappa) as (L, h):
+            s = torch.empty((len(pieces), V, 4, 3), dtype=torch.complex128, device="cuda")
+            for k, pc in enumerate(pieces):
+                L.lqcd_noise_generate(99, 0, 0, dims, L.LQCD_DILUTE_TSC, pc, 1, s[k:k + 1])
+            p = L.solver_params(tol=1e-11, precision=L.LQCD_PREC_MIXED_BF16)
+            x = torch.empty_like(s)
+            assert L.lqcd_solve_batch(h, s, x, p)[0] == 0
+            got = {}
+            for g in (0, 5):
+                c = _coef_gamma(dims[3], g)
+                dre, rc1, _ = L.lqcd_gradient(h, s, x, c, p)
+                dim, rc2, _ = L.lqcd_gradient(h, s, x, 1j * c, p)
+                assert rc1 == 0 and rc2 == 0
+                got[g] = complex(dre, dim)
+        ref = pending.get(timeout=1800)
+    ref1 = ref[0] + ref[1]
+    ref4 = ref[2] + ref[3]
+    assert abs(got[0] - ref1) < 1e-8 * abs(ref1)
+    assert abs(got[5] - ref4) < 1e-8 * max(abs(ref4), abs(ref1))

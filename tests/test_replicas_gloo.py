@@ -35,8 +35,10 @@ def _worker(rank, world, port, out):
         idx = replicas.noise_indices(rank, world, 3)
         acc = sum(_per_t_of(i) for i in idx)
         comb = replicas.combine_loops(torch.from_numpy(acc), len(idx))
+        # the path taken under an NCCL default group: a separate gloo group
+        comb2 = replicas.combine_loops(torch.from_numpy(acc), len(idx), group=replicas.host_group(force_new=True))
         tmax = replicas.max_over_ranks(1.0 + rank)
-        out.put((rank, idx, comb.numpy(), tmax))
+        out.put((rank, idx, comb.numpy(), tmax, comb2.numpy()))
     finally:
         dist.destroy_process_group()
 
@@ -59,6 +61,7 @@ def test_two_gloo_ranks_shard_and_combine():
     expect = sum(_per_t_of(i) for i in all_idx) / 6
     for r in res:
         assert np.allclose(r[2], expect, atol=1e-14, rtol=0)
+        assert np.array_equal(r[4], r[2])
         assert r[3] == 2.0  # max over ranks
 
 

@@ -1,11 +1,12 @@
 """The no-allocation loop contraction against the regular one, through the C ABI.
 
-lqcd_loops_batch_noalloc serves callers that cannot allocate device memory
-(inside stream capture, under a framework's caching allocator, or where the
-device synchronisation of cudaFree is not acceptable).  Its partial sums live
-in a fixed array inside the library that every call shares, so this test calls
-it twice in a row with different inputs: the second result must not be
-polluted by the first.  It also checks the size limit and that the call needs
+lqcd_loops_batch_noalloc serves callers that cannot allocate device memory:
+frameworks whose caching allocator already holds the GPU, pipelines that
+cannot take the device synchronisation of cudaFree, services under a fixed
+memory budget.  Its partial sums live in a fixed array inside the library that
+every call shares, so this test calls it twice in a row with different inputs:
+the second result must not be polluted by the first.  It also checks the size
+limit, the per-site-only form (no partial sums at all) and that the call needs
 no context.  This file is collected last so that a stop at its first failure
 has already run every other test.
 """
@@ -38,15 +39,37 @@ def test_noalloc_matches_loops_batch_two_calls(dims):
             assert rel_err(pt_b.cpu().numpy(), pt_a.cpu().numpy()) < 1e-14
 
 
+def test_noalloc_per_site_only_two_calls():
+    """per_t = NULL: only per-site loops, which need no partial sums."""
+    dims = (8, 4, 4, 6)
+    V = int(np.prod(dims))
+    n = 2
+    with lattice(dims) as (L, h):
+        for call in range(2):
+            src = to_dev(gaussian_spinors(dims, n, 60 + call).reshape(n, V, 4, 3))
+            sol = to_dev(gaussian_spinors(dims, n, 70 + call).reshape(n, V, 4, 3))
+            ps_a = torch.zeros((V, 6), dtype=torch.complex128, device="cuda")
+            ps_b = torch.zeros_like(ps_a)
+            L.lqcd_loops_batch(h, src, sol, 1.5, ps_a, None)
+            L.lqcd_loops_batch_noalloc(dims, src, sol, 1.5, ps_b, None)
+            torch.cuda.synchronize()
+            assert rel_err(ps_b.cpu().numpy(), ps_a.cpu().numpy()) < 1e-14
+
+
 def test_noalloc_rejects_lattice_beyond_scratch():
+    """The library's own limit check (called through the raw C entry point, so
+    that the binding's size checks do not stop the call first)."""
+    import ctypes
     from tests._gpu import require_gpu
     L = require_gpu()
     dims = (32, 32, 32, 64)  # 64 * 256 = 16384 partial blocks > 8192
-    src = torch.zeros((1, 4, 3), dtype=torch.complex128, device="cuda")
-    pt = torch.zeros((64, 6), dtype=torch.complex128, device="cuda")
-    with pytest.raises(L.LqcdError) as e:
-        L.lqcd_loops_batch_noalloc(dims, src, src, 1.0, None, pt)
-    assert e.value.code == L.LQCD_ERR_INVALID and "scratch" in str(e.value)
+    buf = torch.zeros((64, 6), dtype=torch.complex128, device="cuda")
+    p = ctypes.c_void_p(buf.data_ptr())
+    rc = L.load().lqcd_loops_batch_noalloc(L._dims(dims), p, p, 1, 1.0, None, p, L._stream(buf))
+    assert rc == L.LQCD_ERR_INVALID and "scratch" in L.lqcd_last_error(None)
+    # a volume beyond 2^30 sites is refused before any size arithmetic
+    rc = L.load().lqcd_loops_batch_noalloc(L._dims((2048, 2048, 2, 256)), p, p, 1, 1.0, p, None, L._stream(buf))
+    assert rc == L.LQCD_ERR_INVALID
 
 
 def test_noalloc_rejects_host_arrays():
