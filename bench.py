@@ -326,25 +326,35 @@ def config_runs(L, h, dev, stream):
 # ------------------------------------------- GPU idle time inside one step
 def gpu_idle(step_fn, stream, dev):
     """One untimed step under torch.profiler (CUPTI kernel records): the step's
-    CUDA-event time, the summed device time of its kernels and copies, and the
-    difference (time the GPU waited on the host: polls, launches)."""
+    CUDA-event time, the summed device time of its kernels, copies and sets,
+    and the difference (time the GPU waited on the host: polls, launches)."""
     import torch
     try:
         from torch.profiler import profile, ProfilerActivity
+        from torch.autograd import DeviceType
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
-        with profile(activities=[ProfilerActivity.CUDA]) as pr:
+        with profile(activities=[ProfilerActivity.CPU, ProfilerActivity.CUDA]) as pr:
             a.record(stream)
             step_fn()
             b.record(stream)
             b.synchronize()
         step_ms = a.elapsed_time(b)
-        busy_us = sum(e.self_device_time_total for e in pr.key_averages())
-        n_kernels = sum(e.count for e in pr.key_averages() if e.self_device_time_total > 0)
-        return {"step_ms": step_ms, "device_busy_ms": busy_us / 1e3, "idle_ms": step_ms - busy_us / 1e3,
-                "idle_frac": 1.0 - busy_us / 1e3 / step_ms, "device_activities": n_kernels,
-                "note": "one extra step under torch.profiler, not a timed step"}
+        busy_us, n = 0.0, 0
+        for e in pr.events():
+            if getattr(e, "device_type", None) == DeviceType.CUDA:
+                t = getattr(e, "device_time_total", None)
+                if t is None:
+                    t = getattr(e, "cuda_time_total", 0.0)
+                busy_us += t
+                n += 1
+        out = {"step_ms": step_ms, "device_busy_ms": busy_us / 1e3, "idle_ms": step_ms - busy_us / 1e3,
+               "idle_frac": 1.0 - busy_us / 1e3 / step_ms, "device_activities": n,
+               "note": "one extra step under torch.profiler, not a timed step"}
+        if n == 0:
+            out["error"] = "no device activity recorded"
+        return out
     except Exception as ex:  # profiler unavailable: report why
         return {"error": f"{type(ex).__name__}: {ex}"[:200]}
 

@@ -73,10 +73,17 @@ def test_noalloc_rejects_lattice_beyond_scratch():
 
 
 def test_noalloc_rejects_host_arrays():
+    """A host array is refused by the binding and, through the raw C entry
+    point, by the library itself (no kernel is launched on host memory)."""
+    import ctypes
     from tests._gpu import require_gpu
     L = require_gpu()
     dims = (4, 4, 4, 4)
     src = torch.zeros((1, 256, 4, 3), dtype=torch.complex128, device="cuda")
     pt_host = torch.zeros((4, 6), dtype=torch.complex128)
-    with pytest.raises(L.LqcdError):
+    with pytest.raises(ValueError):
         L.lqcd_loops_batch_noalloc(dims, src, src, 1.0, None, pt_host)
+    ps = ctypes.c_void_p(src.data_ptr())
+    rc = L.load().lqcd_loops_batch_noalloc(L._dims(dims), ps, ps, 1, 1.0, None, ctypes.c_void_p(pt_host.data_ptr()),
+                                           L._stream(src))
+    assert rc == L.LQCD_ERR_INVALID and "per_t" in L.lqcd_last_error(None)
