@@ -247,6 +247,7 @@ int lqcd_destroy(lqcd_ctx *ctx) {
   cudaFree(ctx->U32);
   cudaFree(ctx->U16);
   cudaFree(ctx->Utf);
+  cudaFree(ctx->Ub16);
   cudaFree(ctx->Uape);
   cudaFree(ctx->Udf);
   cudaFree(ctx->d_flag);

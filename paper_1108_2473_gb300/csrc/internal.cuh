@@ -181,6 +181,7 @@ struct lqcd_ctx {
   float4 *Udf = nullptr;      // double-float copy  [V][4][3][3] (hi.re, hi.im, lo.re, lo.im)
   uint4 *U16 = nullptr;       // FP16, all 18 reals, each twice  [2 parity][4 mu][5 uint4][Vh]
   float2 *Utf = nullptr;      // tf32-rounded FP32, [2 parity][4 mu][Vh][3][3] complex (tensor-core hop)
+  uint32_t *Ub16 = nullptr;   // BF16 link bundle of the tile hop, [2 parity][Vh][8 dir][3][3] (re, im) pairs
   double2 *Uape = nullptr;    // APE-smeared copy (spatial links smeared) [V][4][3][3], on first use
   bool have_ape = false;
   std::vector<lqcd::DevBuf> ws;  // named workspaces, grow-only

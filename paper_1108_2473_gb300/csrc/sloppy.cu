@@ -38,6 +38,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <memory>
 #include <type_traits>
 #include <vector>
 
@@ -46,6 +47,7 @@
 #include "fpconv.cuh"
 
 #include "sloppy.cuh"
+#include "tile_api.cuh"
 
 namespace lqcd {
 
@@ -937,13 +939,7 @@ __global__ void __launch_bounds__(128, MMA_MINB) k_hop_mma(Geom g, int p_out, co
   }
 }
 
-// Compiled variants of the pair hopping term, picked by the autotuner:
-//   0: one pair per block, registers as the compiler wants
-//   1: one pair per block, registers capped for four 128-thread blocks per SM
-//   2: two pairs per block (256 threads), the same register cap
-//   3: four pairs per block (512 threads), the same register cap
-//   4: SU(3) products on the tensor cores (k_hop_mma)
-constexpr int HOP_VARIANTS = 5;
+// The pair-layout variants of the hopping term (0-4; see HOP_VARIANTS below).
 template <class SP, int EPI>
 static void launch_hop_pair(int variant, int G, cudaStream_t q, const lqcd_ctx *ctx, Geom g, int p_out, SP in, SP out,
                             SP A, SP B, float cA, float cH, const int *plist, const int *pcount, D4S *part, int nbx,
@@ -1327,14 +1323,16 @@ __global__ void k_sfin_init(SState *sc, int *flags, const int *list, const int *
   flags[rhs] = f;
 }
 
-// One warp per member of a listed pair; members without FLAG_ACTIVE are skipped.
-#define PAIR_MEMBER(n)                                            \
-  if (blockIdx.x >= *pcount) return;                              \
-  const int rhs = 2 * plist[blockIdx.x] + (threadIdx.x >> 5);     \
+// One warp per member of a listed group (gs right-hand sides: 2 for the pair
+// layout, 128 for tiles); a block of 64 threads takes two members, block b of
+// group list entry b / (gs / 2).  Members without FLAG_ACTIVE are skipped.
+#define PAIR_MEMBER(n)                                                                     \
+  if (blockIdx.x / (gs >> 1) >= *pcount) return;                                           \
+  const int rhs = gs * plist[blockIdx.x / (gs >> 1)] + 2 * (blockIdx.x % (gs >> 1)) + (threadIdx.x >> 5); \
   if (rhs >= (n) || !(flags[rhs] & FLAG_ACTIVE)) return;
 
 __global__ void k_sfin_alpha(SState *sc, const int *flags, const int *plist, const int *pcount, const D4S *part,
-                             int nb, int n) {
+                             int nb, int n, int gs) {
   PAIR_MEMBER(n)
   D4S t = warp_total_s(part + (size_t)rhs * nb, nb);
   if (threadIdx.x & 31) return;
@@ -1345,7 +1343,7 @@ __global__ void k_sfin_alpha(SState *sc, const int *flags, const int *plist, con
 }
 
 __global__ void k_sfin_omega(SState *sc, const int *flags, const int *plist, const int *pcount, const D4S *part,
-                             int nb, int n) {
+                             int nb, int n, int gs) {
   PAIR_MEMBER(n)
   D4S t = warp_total_s(part + (size_t)rhs * nb, nb);
   if (threadIdx.x & 31) return;
@@ -1355,7 +1353,7 @@ __global__ void k_sfin_omega(SState *sc, const int *flags, const int *plist, con
 
 // convergence / reliable-update decision after the x, r update
 __global__ void k_sfin_conv(SState *sc, int *flags, const int *plist, const int *pcount, const D4S *part, int nb,
-                            int n, double delta2, int max_iter) {
+                            int n, double delta2, int max_iter, int gs) {
   PAIR_MEMBER(n)
   D4S t = warp_total_s(part + (size_t)rhs * nb, nb);
   if (threadIdx.x & 31) return;
@@ -1425,20 +1423,26 @@ __global__ void k_sfin_ru2(SState *sc, int *flags, const int *list, const int *c
   flags[rhs] = FLAG_ACTIVE;
 }
 
-// Deterministic compaction of the per-RHS flags into: active pairs (either
-// member active), RHS needing a reliable update, and pairs containing one.
-__global__ void k_build_lists(int n, const int *flags, int *act_pairs, int *ru_list, int *ru_pairs, int *counts) {
+// Deterministic compaction of the per-RHS flags into: active groups (any
+// member active), RHS needing a reliable update, and groups containing one.
+// A group is gs consecutive right-hand sides (2: pair layout, 128: tiles).
+__global__ void k_build_lists(int n, const int *flags, int gs, int *act_groups, int *ru_list, int *ru_groups,
+                              int *counts) {
   __shared__ int sa[1024], sr[1024], sp[1024];
-  const int np = (n + 1) / 2;
+  const int ng = (n + gs - 1) / gs;
   int tid = threadIdx.x, nt = blockDim.x;
-  int per = (np + nt - 1) / nt;
-  int b0 = tid * per, b1 = min(np, b0 + per);
+  int per = (ng + nt - 1) / nt;
+  int b0 = tid * per, b1 = min(ng, b0 + per);
   int ca = 0, cr = 0, cp = 0;
   for (int P = b0; P < b1; ++P) {
-    int f0 = flags[2 * P], f1 = (2 * P + 1 < n) ? flags[2 * P + 1] : 0;
-    ca += ((f0 | f1) & FLAG_ACTIVE) ? 1 : 0;
-    cp += ((f0 | f1) & FLAG_RU) ? 1 : 0;
-    cr += ((f0 & FLAG_RU) ? 1 : 0) + ((f1 & FLAG_RU) ? 1 : 0);
+    int any = 0, nru = 0;
+    for (int k = P * gs; k < min(n, (P + 1) * gs); ++k) {
+      any |= flags[k];
+      nru += (flags[k] & FLAG_RU) ? 1 : 0;
+    }
+    ca += (any & FLAG_ACTIVE) ? 1 : 0;
+    cp += (any & FLAG_RU) ? 1 : 0;
+    cr += nru;
   }
   sa[tid] = ca;
   sr[tid] = cr;
@@ -1454,11 +1458,13 @@ __global__ void k_build_lists(int n, const int *flags, int *act_pairs, int *ru_l
   }
   int oa = sa[tid] - ca, orr = sr[tid] - cr, op = sp[tid] - cp;
   for (int P = b0; P < b1; ++P) {
-    int f0 = flags[2 * P], f1 = (2 * P + 1 < n) ? flags[2 * P + 1] : 0;
-    if ((f0 | f1) & FLAG_ACTIVE) act_pairs[oa++] = P;
-    if ((f0 | f1) & FLAG_RU) ru_pairs[op++] = P;
-    if (f0 & FLAG_RU) ru_list[orr++] = 2 * P;
-    if (f1 & FLAG_RU) ru_list[orr++] = 2 * P + 1;
+    int any = 0;
+    for (int k = P * gs; k < min(n, (P + 1) * gs); ++k) {
+      any |= flags[k];
+      if (flags[k] & FLAG_RU) ru_list[orr++] = k;
+    }
+    if (any & FLAG_ACTIVE) act_groups[oa++] = P;
+    if (any & FLAG_RU) ru_groups[op++] = P;
   }
   if (tid == nt - 1) {
     counts[0] = sa[tid];
@@ -1473,9 +1479,10 @@ __global__ void k_build_lists(int n, const int *flags, int *act_pairs, int *ru_l
 namespace lqcd {
 
 struct SloppyState {
-  int cap = 0;             // RHS capacity (even)
-  uint4 *sd = nullptr;     // 7 sloppy pair fields
-  float2 *sn = nullptr;    // their FP16 norms
+  int cap = 0;             // RHS capacity (a multiple of the layout's group size)
+  int gran = 2;            // group size the buffers were laid out for (2: pairs, 128: tiles)
+  uint4 *sd = nullptr;     // 7 sloppy fields (pair or tile layout; same bytes per RHS)
+  float2 *sn = nullptr;    // FP16 norms of the pair layout
   float4 *f32 = nullptr;   // 5 FP32 fields
   float4 *xdf = nullptr;   // the iterate, double-float canonical [cap][V][12]
   float2 *r32 = nullptr;   // residual b - D x, FP32 canonical (seeds the next inner solve)
@@ -1502,8 +1509,6 @@ void sloppy_free(lqcd_ctx *ctx) {
   ctx->sloppy = nullptr;
 }
 
-int pack_gauge_sloppy(lqcd_ctx *, cudaStream_t) { return LQCD_OK; }  // packed by k_pack_gauge
-
 static int num_sms(int device) {
   static int cached[64] = {0};
   if (device >= 0 && device < 64 && cached[device]) return cached[device];
@@ -1523,7 +1528,10 @@ struct SmallBufs {
   size_t bytes;
   size_t size() const { return bytes; }
 };
-static SmallBufs small_layout(void *base, int cap, int nbx) {
+// partial sums per RHS: the larger of the pair kernels' blocks of ST sites and
+// the tile kernels' chunks of TCH sites
+static int part_blocks(int vh) { return std::max((vh + ST - 1) / ST, (vh + TCH - 1) / TCH); }
+static SmallBufs small_layout(void *base, int cap, int nbp) {
   Carver cv(base);
   SmallBufs b;
   b.sc = cv.take<SState>(cap);
@@ -1533,19 +1541,21 @@ static SmallBufs small_layout(void *base, int cap, int nbx) {
   b.ru_pairs = cv.take<int>(cap / 2);
   b.cyc_list = cv.take<int>(cap);
   b.cyc_pairs = cv.take<int>(cap / 2);
-  b.counts = cv.take<int>(16);  // [0] active pairs, [1] RU RHS, [2] cycle RHS, [3] RU pairs, [4] cycle pairs
+  // [0] active groups, [1] RU RHS, [2] cycle RHS, [3] RU groups, [4] cycle groups, [8] tile-hop error code
+  b.counts = cv.take<int>(16);
   b.scale = cv.take<double>(cap);
   b.unscale = cv.take<double>(cap);
-  b.part = cv.take<D4S>((size_t)cap * nbx);
+  b.part = cv.take<D4S>((size_t)cap * nbp);
   b.bytes = cv.size();
   return b;
 }
 
-static int sloppy_alloc(lqcd_ctx *ctx, int nrhs) {
+// capacity for nrhs right-hand sides in groups of gran (2 or TR)
+static int sloppy_alloc(lqcd_ctx *ctx, int nrhs, int gran = 2) {
   if (!ctx->sloppy) ctx->sloppy = new SloppyState();
   SloppyState *s = ctx->sloppy;
-  const int cap = (nrhs + 1) & ~1;
-  if (s->cap >= cap) return LQCD_OK;
+  const int cap = (nrhs + gran - 1) / gran * gran;
+  if (s->cap >= cap && s->cap % gran == 0) return LQCD_OK;
   cudaDeviceSynchronize();
   if (s->graph) {
     cudaGraphExecDestroy(s->graph);
@@ -1563,15 +1573,17 @@ static int sloppy_alloc(lqcd_ctx *ctx, int nrhs) {
   s->cap = 0;
   const Geom &g = ctx->geom;
   const size_t vh = g.Vh, pairs = cap / 2;
-  const int nbx = (g.Vh + ST - 1) / ST;
   LQCD_CUDA_TRY(ctx, cudaMalloc(&s->sd, 7 * pairs * 6 * vh * sizeof(uint4)));
   LQCD_CUDA_TRY(ctx, cudaMalloc(&s->sn, 7 * pairs * vh * sizeof(float2)));
   LQCD_CUDA_TRY(ctx, cudaMalloc(&s->f32, 5 * (size_t)cap * 6 * vh * sizeof(float4)));
   LQCD_CUDA_TRY(ctx, cudaMalloc(&s->xdf, (size_t)cap * g.V * 12 * sizeof(float4)));
   LQCD_CUDA_TRY(ctx, cudaMalloc(&s->r32, (size_t)cap * g.V * 12 * sizeof(float2)));
-  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->small, small_layout(nullptr, cap, nbx).size()));
+  LQCD_CUDA_TRY(ctx, cudaMalloc(&s->small, small_layout(nullptr, cap, part_blocks(g.Vh)).size()));
+  // padding right-hand sides of a tile are computed alongside the real ones: start them at zero
+  LQCD_CUDA_TRY(ctx, cudaMemset(s->sd, 0, 7 * pairs * 6 * vh * sizeof(uint4)));
   if (!s->h_counts) LQCD_CUDA_TRY(ctx, cudaMallocHost(&s->h_counts, 16 * sizeof(int)));
   s->cap = cap;
+  s->gran = gran;
   return LQCD_OK;
 }
 
@@ -1588,8 +1600,18 @@ template <> BF16P pair_field<BF16P>(SloppyState *st, int f, int vh) {
   return BF16P{st->sd + (size_t)f * pairs * 6 * vh, vh};
 }
 
+// Compiled variants of the sloppy hopping term, picked by the autotuner:
+//   0: pair layout, one pair per block, registers as the compiler wants
+//   1: pair layout, one pair per block, registers capped for four 128-thread blocks per SM
+//   2: pair layout, two pairs per block (256 threads), the same register cap
+//   3: pair layout, four pairs per block (512 threads), the same register cap
+//   4: pair layout, SU(3) products on the tensor cores (mma.sync, k_hop_mma)
+//   5: RHS-tile layout (BF16 only): TMA-staged neighbour tiles, tcgen05.mma into TMEM (k_thop)
+constexpr int HOP_VARIANTS = 6;
+constexpr int TILE_VARIANT = 5;
+
 // autotuned launch choice per (nrhs, precision): code = blocks_per_sm * 10 + hop variant;
-// LQCD_HOP_VARIANT=0..4 in the environment overrides the variant (for tests)
+// LQCD_HOP_VARIANT=0..5 in the environment overrides the variant (for tests)
 static int tuned_code(const lqcd_ctx *ctx, int nrhs, int precision) {
   long long key = (long long)nrhs * 8 + precision;
   int code = 80;
@@ -1598,8 +1620,97 @@ static int tuned_code(const lqcd_ctx *ctx, int nrhs, int precision) {
   const char *force = getenv("LQCD_HOP_VARIANT");
   if (force && force[0] >= '0' && force[0] < '0' + HOP_VARIANTS && force[1] == 0)
     code = code / 10 * 10 + (force[0] - '0');
+  if (precision != LQCD_PREC_MIXED_BF16 && code % 10 == TILE_VARIANT) code = code / 10 * 10 + 1;  // tiles: BF16 only
   return code;
 }
+
+// ---------------------------------------------------------- layout policies
+// The solver below is written once against these two: the pair layout (two
+// right-hand sides per 16-bit pair, FP32-unit or mma.sync hop) and the tile
+// layout (128 right-hand sides per tile, tcgen05 hop).
+template <class SP> struct PairOps {
+  using Field = SP;
+  static constexpr int GS = 2;
+  static int nb(int vh) { return (vh + ST - 1) / ST; }
+  static int field(lqcd_ctx *, SloppyState *ss, int f, int vh, Field &out) {
+    out = pair_field<SP>(ss, f, vh);
+    return LQCD_OK;
+  }
+  static void p(cudaStream_t q, int G, int vh, const SState *sc, const Field &r, const Field &rhat, const Field &pp,
+                const Field &v, const int *gl, const int *gc, int nb) {
+    KL k_pair_p<SP><<<G, ST, 0, q>>>(vh, sc, r, rhat, pp, v, gl, gc, nb);
+  }
+  static void s(cudaStream_t q, int G, int vh, const SState *sc, const Field &r, const Field &v, const Field &s_,
+                const int *gl, const int *gc, int nb) {
+    KL k_pair_s<SP><<<G, ST, 0, q>>>(vh, sc, r, v, s_, gl, gc, nb);
+  }
+  static void xr(cudaStream_t q, int G, int vh, const SState *sc, const int *flags, F32F x, const Field &pp,
+                 const Field &s_, const Field &t, const Field &r, const Field &rhat, const int *gl, const int *gc,
+                 D4S *part, int nb) {
+    KL k_pair_xr<SP><<<G, ST, 0, q>>>(vh, sc, flags, x, pp, s_, t, r, rhat, gl, gc, part, nb);
+  }
+  static void copy(cudaStream_t q, int G, int vh, const int *flags, F32F src, const Field &r, const Field &rhat,
+                   bool use_rhat, F32F x, bool zero_x, const int *gl, const int *gc, D4S *part, int nb) {
+    KL k_pair_copy<SP><<<G, ST, 0, q>>>(vh, flags, src, r, rhat, use_rhat, x, zero_x, gl, gc, part, nb);
+  }
+  template <int EPI>
+  static void hop(int variant, int G, cudaStream_t q, lqcd_ctx *ctx, int p_out, const Field &in, const Field &out,
+                  const Field &A, const Field &B, float cA, float cH, const int *gl, const int *gc, D4S *part, int nb,
+                  int nrhs, unsigned long long *prof, int *) {
+    launch_hop_pair<SP, EPI>(variant, G, q, ctx, ctx->geom, p_out, in, out, A, B, cA, cH, gl, gc, part, nb, nrhs,
+                             prof);
+  }
+};
+
+struct TileOps {
+  using Field = TileField;
+  static constexpr int GS = TR;
+  static int nb(int vh) { return (vh + TCH - 1) / TCH; }
+  static int field(lqcd_ctx *ctx, SloppyState *ss, int f, int vh, Field &out) {
+    const size_t per = (size_t)ss->cap * vh * 24;  // BF16 values per field
+    out.d = reinterpret_cast<__nv_bfloat16 *>(ss->sd) + (size_t)f * per;
+    out.ntile = ss->cap / TR;
+    out.vh = vh;
+    return tile_field_map(ctx, out);
+  }
+  static void p(cudaStream_t q, int G, int vh, const SState *sc, const Field &r, const Field &rhat, const Field &pp,
+                const Field &v, const int *gl, const int *gc, int) {
+    tile_p(q, G, vh, sc, r, rhat, pp, v, gl, gc);
+  }
+  static void s(cudaStream_t q, int G, int vh, const SState *sc, const Field &r, const Field &v, const Field &s_,
+                const int *gl, const int *gc, int) {
+    tile_s(q, G, vh, sc, r, v, s_, gl, gc);
+  }
+  static void xr(cudaStream_t q, int G, int vh, const SState *sc, const int *flags, F32F x, const Field &pp,
+                 const Field &s_, const Field &t, const Field &r, const Field &rhat, const int *gl, const int *gc,
+                 D4S *part, int) {
+    tile_xr(q, G, vh, sc, flags, x, pp, s_, t, r, rhat, gl, gc, part);
+  }
+  static void copy(cudaStream_t q, int G, int vh, const int *flags, F32F src, const Field &r, const Field &rhat,
+                   bool use_rhat, F32F x, bool zero_x, const int *gl, const int *gc, D4S *part, int) {
+    tile_copy(q, G, vh, flags, src, r, rhat, use_rhat, x, zero_x, gl, gc, part);
+  }
+  template <int EPI>
+  static void hop(int, int, cudaStream_t q, lqcd_ctx *ctx, int p_out, const Field &in, const Field &out,
+                  const Field &A, const Field &B, float cA, float cH, const int *gl, const int *gc, D4S *part, int nb,
+                  int nrhs, unsigned long long *prof, int *err) {
+    // one persistent CTA per SM (the pipeline holds ~181 KiB of shared memory)
+    tile_hop(EPI, q, num_sms(ctx->device), ctx, p_out, in, out, A, B, cA, cH, gl, gc, part, nb, nrhs, prof, err);
+  }
+};
+
+// The part of a lattice's solve that the uneven-batch driver talks to.
+struct RunIface {
+  bool done = false, inner = false;
+  virtual ~RunIface() {}
+  virtual int init() = 0;
+  virtual int cycle_start() = 0;
+  virtual void launch_iters(cudaStream_t q, int k) = 0;
+  virtual int request_count(cudaStream_t q) = 0;
+  virtual int poll() = 0;
+  virtual int finish() = 0;
+  virtual std::vector<double> graph_key() const = 0;
+};
 
 // One lattice's mixed-precision solve as a resumable state machine:
 //   cycle_start()    FP64 residual b - D x, per-RHS decisions, inner source
@@ -1607,8 +1718,9 @@ static int tuned_code(const lqcd_ctx *ctx, int nrhs, int precision) {
 //                    every kernel reads its work list and counts from device memory)
 //   poll()           after the stream has drained: is the inner solve over?
 //   cycle_end()      odd reconstruction and x += |r| e in FP64
-template <class SP>
-struct MixedRun {
+template <class Ops>
+struct MixedRun : RunIface {
+  using SF = typename Ops::Field;
   lqcd_ctx *ctx;
   const double2 *b;
   double2 *x;
@@ -1619,10 +1731,10 @@ struct MixedRun {
   double t0;
   SloppyState *ss = nullptr;
   Geom g;
-  int vh = 0, cap = 0, nbx = 0, G = 0, npairs = 0, hop_variant = 0;
+  int vh = 0, cap = 0, nbx = 0, nb = 0, G = 0, npairs = 0, hop_variant = 0;
   float kappa = 0.f, k2 = 0.f;
   double delta = 0.05, floor2 = 4e-12;  // (2e-6)^2: inner FP32 target floor, relative to |b_inner|^2
-  SP r, rhat, pp, v, s, t, tmp;
+  SF r, rhat, pp, v, s, t, tmp;
   F32F x32, b32, r32, t32, o32;
   SmallBufs sb;
   std::vector<double> rr, bb, prev_rel, hscale, hun;
@@ -1630,32 +1742,37 @@ struct MixedRun {
   std::vector<int> hl, hp, bad, hflags, keep_status;
   int cycle = 0;
   const int max_cycles = 10;
-  bool timed_out = false, done = false, inner = false;
+  bool timed_out = false;
 
-  int init() {
-    int rc = sloppy_alloc(ctx, nrhs);
+  MixedRun(lqcd_ctx *c, const double2 *b_, double2 *x_, int n, const lqcd_solver_params &p_, lqcd_solve_stats *s_,
+           cudaStream_t st_, double t0_)
+      : ctx(c), b(b_), x(x_), nrhs(n), p(p_), stats(s_), st(st_), t0(t0_) {}
+
+  int init() override {
+    int rc = sloppy_alloc(ctx, nrhs, Ops::GS);
     if (rc) return rc;
     ss = ctx->sloppy;
     g = ctx->geom;
     vh = g.Vh;
     cap = ss->cap;
     nbx = (vh + ST - 1) / ST;
+    nb = Ops::nb(vh);
     kappa = (float)ctx->kappa;
     k2 = (float)(ctx->kappa * ctx->kappa);
-    G = num_sms(ctx->device) * (tuned_code(ctx, nrhs, p.precision) / 10);
-    hop_variant = tuned_code(ctx, nrhs, p.precision) % 10;
+    const int code = tuned_code(ctx, nrhs, p.precision);
+    hop_variant = code % 10;
+    // tile path: the element-wise kernels use eight 256-thread blocks per SM
+    G = num_sms(ctx->device) * (Ops::GS == TR ? 8 : code / 10);
     npairs = (nrhs + 1) / 2;
     delta = p.delta > 0 ? p.delta : 0.05;
-    r = pair_field<SP>(ss, 0, vh);
-    rhat = pair_field<SP>(ss, 1, vh);
-    pp = pair_field<SP>(ss, 2, vh);
-    v = pair_field<SP>(ss, 3, vh);
-    s = pair_field<SP>(ss, 4, vh);
-    t = pair_field<SP>(ss, 5, vh);
-    tmp = pair_field<SP>(ss, 6, vh);
-    auto f32 = [&](int k) { F32F f; f.d = ss->f32 + (size_t)k * cap * 6 * vh; f.vh = vh; return f; };
+    SF *f[7] = {&r, &rhat, &pp, &v, &s, &t, &tmp};
+    for (int k = 0; k < 7; ++k) {
+      rc = Ops::field(ctx, ss, k, vh, *f[k]);
+      if (rc) return rc;
+    }
+    auto f32 = [&](int k) { F32F ff; ff.d = ss->f32 + (size_t)k * cap * 6 * vh; ff.vh = vh; return ff; };
     x32 = f32(0); b32 = f32(1); r32 = f32(2); t32 = f32(3); o32 = f32(4);
-    sb = small_layout(ss->small, cap, nbx);
+    sb = small_layout(ss->small, cap, part_blocks(vh));
     rr.assign(nrhs, 0.0);
     bb.assign(nrhs, 0.0);
     prev_rel.assign(nrhs, 1e300);
@@ -1668,20 +1785,22 @@ struct MixedRun {
     for (int k = 0; k < nrhs; ++k) stats[k] = lqcd_solve_stats{0, LQCD_OK, 0.0, 0, 0};
     const size_t n = (size_t)nrhs * g.V * 12;
     LQCD_CUDA_TRY(ctx, cudaMemsetAsync(ss->xdf, 0, n * sizeof(float4), st));
+    LQCD_CUDA_TRY(ctx, cudaMemsetAsync(sb.counts, 0, 16 * sizeof(int), st));
     return LQCD_OK;
   }
 
   // the FP64 solution from the double-float iterate
-  int finish() { return df_join(ctx, ss->xdf, x, (size_t)nrhs * g.V * 12, st); }
+  int finish() override { return df_join(ctx, ss->xdf, x, (size_t)nrhs * g.V * 12, st); }
 
   // key of the captured iteration graph: everything its kernels capture by value
-  std::vector<double> graph_key() const {
+  std::vector<double> graph_key() const override {
     return {(double)nrhs, (double)p.precision, (double)p.max_iter, delta, (double)kappa, (double)G, (double)hop_variant,
-            (double)(uintptr_t)ss->sd, (double)(uintptr_t)ss->f32, (double)(uintptr_t)ss->small,
-            (double)(uintptr_t)ctx->U16, (double)(uintptr_t)ctx->U32, (double)(uintptr_t)ss->xdf};
+            (double)Ops::GS, (double)(uintptr_t)ss->sd, (double)(uintptr_t)ss->f32, (double)(uintptr_t)ss->small,
+            (double)(uintptr_t)ctx->U16, (double)(uintptr_t)ctx->U32, (double)(uintptr_t)ctx->Ub16,
+            (double)(uintptr_t)ss->xdf, (double)cap};
   }
 
-  int cycle_start() {
+  int cycle_start() override {
     // at x = 0 the residual is b itself (FP64 norms only); later: double-float
     // b - D x for the right-hand sides corrected in the previous cycle (the
     // others' iterates, and so their residuals, have not changed)
@@ -1719,7 +1838,7 @@ struct MixedRun {
       hs[k].status = status;
       if (status == LQCD_OK && rel > p.tol) {
         hl.push_back(k);
-        if (hp.empty() || hp.back() != k / 2) hp.push_back(k / 2);
+        if (hp.empty() || hp.back() != k / Ops::GS) hp.push_back(k / Ops::GS);
         hscale[k] = 1.0 / std::sqrt(rr[k]);
         hun[k] = std::sqrt(rr[k]);
         hs[k].target2 = 0.25 * p.tol * p.tol * bb[k] / rr[k];
@@ -1747,20 +1866,20 @@ struct MixedRun {
     }
     KL k_hop32<EPI_AXPY><<<G, ST, 0, st>>>(g, 0, ctx->U32, o32, b32, b32, b32, 1.f, 0.f, kappa, sb.cyc_list,
                                            counts + 2, nullptr, nbx);
-    KL k_pair_copy<SP><<<G, ST, 0, st>>>(vh, sb.flags, b32, r, r, false, x32, true, sb.cyc_pairs, counts + 4, sb.part,
-                                         nbx);
-    KL k_sfin_init<<<(int)hl.size(), 32, 0, st>>>(sb.sc, sb.flags, sb.cyc_list, counts + 2, sb.part, nbx, floor2);
-    KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, sb.flags, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
+    Ops::copy(st, G, vh, sb.flags, b32, r, r, false, x32, true, sb.cyc_pairs, counts + 4, sb.part, nb);
+    KL k_sfin_init<<<(int)hl.size(), 32, 0, st>>>(sb.sc, sb.flags, sb.cyc_list, counts + 2, sb.part, nb, floor2);
+    KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, sb.flags, Ops::GS, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
     LQCD_LAUNCH_CHECK(ctx, "mixed: cycle setup");
     inner = true;
     return LQCD_OK;
   }
 
   // Enqueue k inner iterations on stream q (RHS that finish simply drop out of the lists).
-  void launch_iters(cudaStream_t q, int k) {
+  void launch_iters(cudaStream_t q, int k) override {
     int *counts = sb.counts;
     const float4 *L32 = ctx->U32;
     unsigned long long *prof = ctx->prof_on ? ctx->d_prof : nullptr;
+    int *herr = counts + 8;
     if (ctx->prof_on) ctx->prof_prec = p.precision;
     auto ev_begin = [&]() {
       if (!ctx->prof_on) return;
@@ -1777,54 +1896,56 @@ struct MixedRun {
       ctx->prof_used += 2;
       ctx->prof_hop_launches++;
     };
+    const int gs = Ops::GS;
     for (int it = 0; it < k; ++it) {
-      KL k_pair_p<SP><<<G, ST, 0, q>>>(vh, sb.sc, r, rhat, pp, v, sb.act_pairs, counts, nbx);
+      Ops::p(q, G, vh, sb.sc, r, rhat, pp, v, sb.act_pairs, counts, nb);
       ev_begin();
-      launch_hop_pair<SP, EPI_PLAIN>(hop_variant, G, q, ctx, g, 1, pp, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
-                                                    nullptr, nbx, nrhs, prof);
+      Ops::template hop<EPI_PLAIN>(hop_variant, G, q, ctx, 1, pp, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
+                                   nullptr, nb, nrhs, prof, herr);
       ev_end();
       ev_begin();
-      launch_hop_pair<SP, EPI_DOTR>(hop_variant, G, q, ctx, g, 0, tmp, v, pp, rhat, 1.f, -k2, sb.act_pairs, counts,
-                                                   sb.part, nbx, nrhs, prof);
+      Ops::template hop<EPI_DOTR>(hop_variant, G, q, ctx, 0, tmp, v, pp, rhat, 1.f, -k2, sb.act_pairs, counts, sb.part,
+                                  nb, nrhs, prof, herr);
       ev_end();
-      KL k_sfin_alpha<<<npairs, 64, 0, q>>>(sb.sc, sb.flags, sb.act_pairs, counts, sb.part, nbx, nrhs);
-      KL k_pair_s<SP><<<G, ST, 0, q>>>(vh, sb.sc, r, v, s, sb.act_pairs, counts, nbx);
+      KL k_sfin_alpha<<<cap / 2, 64, 0, q>>>(sb.sc, sb.flags, sb.act_pairs, counts, sb.part, nb, nrhs, gs);
+      Ops::s(q, G, vh, sb.sc, r, v, s, sb.act_pairs, counts, nb);
       ev_begin();
-      launch_hop_pair<SP, EPI_PLAIN>(hop_variant, G, q, ctx, g, 1, s, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
-                                                    nullptr, nbx, nrhs, prof);
+      Ops::template hop<EPI_PLAIN>(hop_variant, G, q, ctx, 1, s, tmp, tmp, tmp, 0.f, 1.f, sb.act_pairs, counts,
+                                   nullptr, nb, nrhs, prof, herr);
       ev_end();
       ev_begin();
-      launch_hop_pair<SP, EPI_TS>(hop_variant, G, q, ctx, g, 0, tmp, t, s, s, 1.f, -k2, sb.act_pairs, counts, sb.part,
-                                                 nbx, nrhs, prof);
+      Ops::template hop<EPI_TS>(hop_variant, G, q, ctx, 0, tmp, t, s, s, 1.f, -k2, sb.act_pairs, counts, sb.part, nb,
+                                nrhs, prof, herr);
       ev_end();
-      KL k_sfin_omega<<<npairs, 64, 0, q>>>(sb.sc, sb.flags, sb.act_pairs, counts, sb.part, nbx, nrhs);
-      KL k_pair_xr<SP><<<G, ST, 0, q>>>(vh, sb.sc, sb.flags, x32, pp, s, t, r, rhat, sb.act_pairs, counts, sb.part,
-                                        nbx);
-      KL k_sfin_conv<<<npairs, 64, 0, q>>>(sb.sc, sb.flags, sb.act_pairs, counts, sb.part, nbx, nrhs,
-                                           delta * delta, p.max_iter);
-      KL k_build_lists<<<1, 1024, 0, q>>>(nrhs, sb.flags, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
+      KL k_sfin_omega<<<cap / 2, 64, 0, q>>>(sb.sc, sb.flags, sb.act_pairs, counts, sb.part, nb, nrhs, gs);
+      Ops::xr(q, G, vh, sb.sc, sb.flags, x32, pp, s, t, r, rhat, sb.act_pairs, counts, sb.part, nb);
+      KL k_sfin_conv<<<cap / 2, 64, 0, q>>>(sb.sc, sb.flags, sb.act_pairs, counts, sb.part, nb, nrhs,
+                                            delta * delta, p.max_iter, gs);
+      KL k_build_lists<<<1, 1024, 0, q>>>(nrhs, sb.flags, gs, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
       // reliable update in FP32: r32 = b32 - x32 + kappa^2 H_eo H_oe x32
       KL k_hop32<EPI_PLAIN><<<G, ST, 0, q>>>(g, 1, L32, x32, t32, t32, t32, 0.f, 0.f, 1.f, sb.ru_list, counts + 1,
                                              nullptr, nbx);
       KL k_hop32<EPI_RES><<<G, ST, 0, q>>>(g, 0, L32, t32, r32, b32, x32, 1.f, -1.f, k2, sb.ru_list, counts + 1,
                                            sb.part, nbx);
       KL k_sfin_ru<<<nrhs, 32, 0, q>>>(sb.sc, sb.flags, sb.ru_list, counts + 1, sb.part, nbx, p.max_iter);
-      KL k_build_lists<<<1, 1024, 0, q>>>(nrhs, sb.flags, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
-      KL k_pair_copy<SP><<<G, ST, 0, q>>>(vh, sb.flags, r32, r, rhat, true, x32, false, sb.ru_pairs, counts + 3,
-                                          sb.part, nbx);
-      KL k_sfin_ru2<<<nrhs, 32, 0, q>>>(sb.sc, sb.flags, sb.ru_list, counts + 1, sb.part, nbx);
-      KL k_build_lists<<<1, 1024, 0, q>>>(nrhs, sb.flags, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
+      KL k_build_lists<<<1, 1024, 0, q>>>(nrhs, sb.flags, gs, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
+      Ops::copy(q, G, vh, sb.flags, r32, r, rhat, true, x32, false, sb.ru_pairs, counts + 3, sb.part, nb);
+      KL k_sfin_ru2<<<nrhs, 32, 0, q>>>(sb.sc, sb.flags, sb.ru_list, counts + 1, sb.part, nb);
+      KL k_build_lists<<<1, 1024, 0, q>>>(nrhs, sb.flags, gs, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
     }
   }
 
-  // enqueue the read-back of the active count (after the iterations on q)
-  int request_count(cudaStream_t q) {
-    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(ss->h_counts, sb.counts, 2 * sizeof(int), cudaMemcpyDeviceToHost, q));
+  // enqueue the read-back of the active count and the tile hop's error code
+  int request_count(cudaStream_t q) override {
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(ss->h_counts, sb.counts, 9 * sizeof(int), cudaMemcpyDeviceToHost, q));
     return LQCD_OK;
   }
 
   // with the stream drained: finish the cycle if no RHS is active any more
-  int poll() {
+  int poll() override {
+    if (ss->h_counts[8] != 0)
+      return set_error(ctx, LQCD_ERR_CUDA,
+                       "mixed: the tensor-core hop stopped after a bounded wait ran out (code %d)", ss->h_counts[8]);
     bool any = ss->h_counts[0] > 0;
     if (any && p.timeout_ms > 0 && wall_ms() - t0 > p.timeout_ms) {
       timed_out = true;
@@ -1853,6 +1974,14 @@ struct MixedRun {
   }
 };
 
+static RunIface *make_run(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const lqcd_solver_params &p,
+                          lqcd_solve_stats *stats, cudaStream_t st, double t0) {
+  if (p.precision == LQCD_PREC_MIXED_FP16) return new MixedRun<PairOps<F16P>>(ctx, b, x, nrhs, p, stats, st, t0);
+  if (tuned_code(ctx, nrhs, p.precision) % 10 == TILE_VARIANT)
+    return new MixedRun<TileOps>(ctx, b, x, nrhs, p, stats, st, t0);
+  return new MixedRun<PairOps<BF16P>>(ctx, b, x, nrhs, p, stats, st, t0);
+}
+
 // capture `body(stream)` into an executable graph on stream st; *kernels
 // receives the number of kernel launches the body recorded (each replay makes
 // them; the capture itself launches nothing, so the library's launch counter
@@ -1878,27 +2007,27 @@ constexpr int ITERS_PER_POLL = 4;
 // Single lattice: the four-iteration sequence is captured once into a CUDA
 // graph and replayed (launched directly while profiling, so every hop launch
 // gets its own events).
-template <class SP>
 static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const lqcd_solver_params &p,
                        lqcd_solve_stats *stats, cudaStream_t st, double t0) {
-  MixedRun<SP> run{ctx, b, x, nrhs, p, stats, st, t0};
-  int rc = run.init();
+  std::unique_ptr<RunIface> run(make_run(ctx, b, x, nrhs, p, stats, st, t0));
+  int rc = run->init();
   if (rc) return rc;
   SloppyState *ss = ctx->sloppy;
   // the legacy default stream cannot be captured: launch directly there
   const bool use_graph = !ctx->prof_on && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
-  while (!run.done) {
-    if (!run.inner) {
-      rc = run.cycle_start();
+  while (!run->done) {
+    if (!run->inner) {
+      rc = run->cycle_start();
       if (rc) return rc;
       continue;
     }
     if (use_graph) {
-      std::vector<double> key = run.graph_key();
+      std::vector<double> key = run->graph_key();
       if (!ss->graph || ss->graph_key != key) {
         if (ss->graph) cudaGraphExecDestroy(ss->graph);
         ss->graph = nullptr;
-        cudaError_t e = capture_graph(st, [&](cudaStream_t q) { run.launch_iters(q, ITERS_PER_POLL); }, &ss->graph,
+        RunIface *rp = run.get();
+        cudaError_t e = capture_graph(st, [&](cudaStream_t q) { rp->launch_iters(q, ITERS_PER_POLL); }, &ss->graph,
                                       &ss->graph_kernels);
         if (e != cudaSuccess) return cuda_error(ctx, e, "mixed: capture of the iteration graph");
         ss->graph_key = key;
@@ -1906,47 +2035,45 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
       LQCD_CUDA_TRY(ctx, cudaGraphLaunch(ss->graph, st));
       g_launches += ss->graph_kernels;
     } else {
-      run.launch_iters(st, ITERS_PER_POLL);
+      run->launch_iters(st, ITERS_PER_POLL);
       LQCD_LAUNCH_CHECK(ctx, "mixed: iteration");
     }
-    rc = run.request_count(st);
+    rc = run->request_count(st);
     if (rc) return rc;
     LQCD_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-    rc = run.poll();
+    rc = run->poll();
     if (rc) return rc;
   }
-  return run.finish();
+  return run->finish();
 }
 
 // Uneven batch: all lattices' iterations in one captured graph (one branch
 // per lattice); one graph launch advances every lattice by four iterations.
-template <class SP>
 static int mixed_batch(std::vector<lqcd_ctx *> &ctxs, std::vector<const double2 *> &bs, std::vector<double2 *> &xs,
                        std::vector<int> &ns, const lqcd_solver_params &p, std::vector<lqcd_solve_stats *> &stats,
                        cudaStream_t st, std::vector<cudaStream_t> &side, cudaGraphExec_t *gexec,
                        std::vector<double> *gkey, long long *gkernels) {
   const size_t nl = ctxs.size();
   const double t0 = wall_ms();
-  std::vector<MixedRun<SP>> runs;
-  runs.reserve(nl);
-  for (size_t l = 0; l < nl; ++l) runs.push_back(MixedRun<SP>{ctxs[l], bs[l], xs[l], ns[l], p, stats[l], st, t0});
+  std::vector<std::unique_ptr<RunIface>> runs;
+  for (size_t l = 0; l < nl; ++l) runs.emplace_back(make_run(ctxs[l], bs[l], xs[l], ns[l], p, stats[l], st, t0));
   for (auto &r : runs) {
-    int rc = r.init();
+    int rc = r->init();
     if (rc) return rc;
   }
   for (;;) {
     bool any = false;
     for (auto &r : runs) {
-      while (!r.done && !r.inner) {
-        int rc = r.cycle_start();
+      while (!r->done && !r->inner) {
+        int rc = r->cycle_start();
         if (rc) return rc;
       }
-      any = any || !r.done;
+      any = any || !r->done;
     }
     if (!any) break;
     std::vector<double> key;
     for (auto &r : runs) {
-      std::vector<double> k = r.graph_key();
+      std::vector<double> k = r->graph_key();
       key.insert(key.end(), k.begin(), k.end());
     }
     if (!*gexec || *gkey != key) {
@@ -1958,7 +2085,7 @@ static int mixed_batch(std::vector<lqcd_ctx *> &ctxs, std::vector<const double2 
         cudaEventRecord(ev[nl], q);
         for (size_t l = 0; l < nl; ++l) {
           cudaStreamWaitEvent(side[l], ev[nl], 0);
-          runs[l].launch_iters(side[l], ITERS_PER_POLL);
+          runs[l]->launch_iters(side[l], ITERS_PER_POLL);
           cudaEventRecord(ev[l], side[l]);
           cudaStreamWaitEvent(q, ev[l], 0);
         }
@@ -1970,19 +2097,19 @@ static int mixed_batch(std::vector<lqcd_ctx *> &ctxs, std::vector<const double2 
     LQCD_CUDA_TRY(ctxs[0], cudaGraphLaunch(*gexec, st));
     g_launches += *gkernels;
     for (auto &r : runs)
-      if (!r.done) {
-        int rc = r.request_count(st);
+      if (!r->done) {
+        int rc = r->request_count(st);
         if (rc) return rc;
       }
     LQCD_CUDA_TRY(ctxs[0], cudaStreamSynchronize(st));
     for (auto &r : runs)
-      if (!r.done && r.inner) {
-        int rc = r.poll();
+      if (!r->done && r->inner) {
+        int rc = r->poll();
         if (rc) return rc;
       }
   }
   for (auto &r : runs) {
-    int rc = r.finish();
+    int rc = r->finish();
     if (rc) return rc;
   }
   return LQCD_OK;
@@ -2003,9 +2130,7 @@ int mixed_solve(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const lqc
   int worst = LQCD_OK;
   for (int k0 = 0; k0 < nrhs; k0 += blk) {
     int nk = std::min(blk, nrhs - k0);
-    int rc = p.precision == LQCD_PREC_MIXED_FP16
-                 ? mixed_block<F16P>(ctx, b + k0 * full, x + k0 * full, nk, p, stats + k0, st, t0)
-                 : mixed_block<BF16P>(ctx, b + k0 * full, x + k0 * full, nk, p, stats + k0, st, t0);
+    int rc = mixed_block(ctx, b + k0 * full, x + k0 * full, nk, p, stats + k0, st, t0);
     if (rc) return rc;
     for (int k = 0; k < nk; ++k)
       if (worst == LQCD_OK && stats[k0 + k].status != LQCD_OK) worst = stats[k0 + k].status;
@@ -2127,11 +2252,8 @@ int lqcd_batch_run(lqcd_batch *batch, const lqcd_solver_params *params, lqcd_sol
       LQCD_CUDA_TRY(ctxs[0], cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
       batch->side.push_back(s);
     }
-    rc = p.precision == LQCD_PREC_MIXED_FP16
-             ? mixed_batch<F16P>(ctxs, bs, xs, ns, p, sts, st, batch->side, &batch->graph, &batch->graph_key,
-                                 &batch->graph_kernels)
-             : mixed_batch<BF16P>(ctxs, bs, xs, ns, p, sts, st, batch->side, &batch->graph, &batch->graph_key,
-                                  &batch->graph_kernels);
+    rc = mixed_batch(ctxs, bs, xs, ns, p, sts, st, batch->side, &batch->graph, &batch->graph_key,
+                     &batch->graph_kernels);
   }
   if (rc) {
     set_error(nullptr, rc, "lqcd_batch_run: %s", lqcd_last_error(ctxs[0]));
@@ -2150,22 +2272,24 @@ int lqcd_batch_run(lqcd_batch *batch, const lqcd_solver_params *params, lqcd_sol
 // ================================================================ autotuner
 namespace lqcd {
 
+// one hop timing: reps launches after two warm-up launches, ms per launch
+template <class F>
+static float time_hop(F launch, cudaEvent_t e0, cudaEvent_t e1, int reps, cudaError_t *err) {
+  for (int rep = 0; rep < 2; ++rep) launch();
+  cudaEventRecord(e0);
+  for (int rep = 0; rep < reps; ++rep) launch();
+  cudaEventRecord(e1);
+  *err = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  return ms / reps;
+}
+
 template <class SP>
 static int autotune_hop(lqcd_ctx *ctx, int nrhs, int precision, int *best, int *best_variant) {
-  int rc = sloppy_alloc(ctx, nrhs);
-  if (rc) return rc;
-  SloppyState *ss = ctx->sloppy;
   const Geom &g = ctx->geom;
-  const int vh = g.Vh, cap = ss->cap, nbx = (vh + ST - 1) / ST, npairs = (nrhs + 1) / 2;
-  SmallBufs sb = small_layout(ss->small, cap, nbx);
-  SP in = pair_field<SP>(ss, 2, vh), out = pair_field<SP>(ss, 6, vh);
-  // zero data: timing does not depend on the values
-  LQCD_CUDA_TRY(ctx, cudaMemset(ss->sd, 0, 7 * (size_t)(cap / 2) * 6 * vh * sizeof(uint4)));
-  LQCD_CUDA_TRY(ctx, cudaMemset(ss->sn, 0, 7 * (size_t)(cap / 2) * vh * sizeof(float2)));
-  std::vector<int> pl(npairs);
-  for (int k = 0; k < npairs; ++k) pl[k] = k;
-  LQCD_CUDA_TRY(ctx, cudaMemcpy(sb.act_pairs, pl.data(), npairs * sizeof(int), cudaMemcpyHostToDevice));
-  LQCD_CUDA_TRY(ctx, cudaMemcpy(sb.counts, &npairs, sizeof(int), cudaMemcpyHostToDevice));
+  const int vh = g.Vh, npairs = (nrhs + 1) / 2;
+  const bool tiles = std::is_same<SP, BF16P>::value;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -2174,36 +2298,72 @@ static int autotune_hop(lqcd_ctx *ctx, int nrhs, int precision, int *best, int *
   float best_ms = 1e30f;
   int best_code = 80;
   const int nsm = num_sms(ctx->device);
-  for (int variant = 0; variant < HOP_VARIANTS; ++variant)
-    for (int c : cand) {
-      const int G = nsm * c;
-      for (int rep = 0; rep < 2; ++rep)  // warm-up
-        launch_hop_pair<SP, EPI_PLAIN>(variant, G, (cudaStream_t)0, ctx, g, 1, in, out, out,
-                                       out, 0.f, 1.f, (const int *)sb.act_pairs, (const int *)sb.counts,
-                                       (D4S *)nullptr, nbx, nrhs, (unsigned long long *)nullptr);
-      cudaEventRecord(e0);
-      for (int rep = 0; rep < 5; ++rep)
-        launch_hop_pair<SP, EPI_PLAIN>(variant, G, (cudaStream_t)0, ctx, g, 1, in, out, out,
-                                       out, 0.f, 1.f, (const int *)sb.act_pairs, (const int *)sb.counts,
-                                       (D4S *)nullptr, nbx, nrhs, (unsigned long long *)nullptr);
-      cudaEventRecord(e1);
-      cudaError_t e = cudaEventSynchronize(e1);
-      if (e != cudaSuccess) {
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        return cuda_error(ctx, e, "lqcd_autotune");
+  cudaError_t err = cudaSuccess;
+  // pair layout: variants 0-4 x launch grids (zero data: timing does not depend on the values)
+  int rc = sloppy_alloc(ctx, nrhs, 2);
+  if (rc) return rc;
+  SloppyState *ss = ctx->sloppy;
+  const int nbx = (vh + ST - 1) / ST;
+  {
+    SmallBufs sb = small_layout(ss->small, ss->cap, part_blocks(vh));
+    SP in = pair_field<SP>(ss, 2, vh), out = pair_field<SP>(ss, 6, vh);
+    LQCD_CUDA_TRY(ctx, cudaMemset(ss->sd, 0, 7 * (size_t)(ss->cap / 2) * 6 * vh * sizeof(uint4)));
+    LQCD_CUDA_TRY(ctx, cudaMemset(ss->sn, 0, 7 * (size_t)(ss->cap / 2) * vh * sizeof(float2)));
+    std::vector<int> pl(npairs);
+    for (int k = 0; k < npairs; ++k) pl[k] = k;
+    LQCD_CUDA_TRY(ctx, cudaMemcpy(sb.act_pairs, pl.data(), npairs * sizeof(int), cudaMemcpyHostToDevice));
+    LQCD_CUDA_TRY(ctx, cudaMemcpy(sb.counts, &npairs, sizeof(int), cudaMemcpyHostToDevice));
+    for (int variant = 0; variant < TILE_VARIANT; ++variant)
+      for (int c : cand) {
+        const int G = nsm * c;
+        const float ms = time_hop([&]() {
+          launch_hop_pair<SP, EPI_PLAIN>(variant, G, (cudaStream_t)0, ctx, g, 1, in, out, out, out, 0.f, 1.f,
+                                         (const int *)sb.act_pairs, (const int *)sb.counts, (D4S *)nullptr, nbx, nrhs,
+                                         (unsigned long long *)nullptr);
+        }, e0, e1, 5, &err);
+        if (err != cudaSuccess) break;
+        if (verbose)
+          fprintf(stderr, "lqcd_autotune: nrhs %d variant %d blocks/SM %d: %.4f ms per hop\n", nrhs, variant, c, ms);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_code = c * 10 + variant;
+        }
       }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (verbose) fprintf(stderr, "lqcd_autotune: nrhs %d variant %d blocks/SM %d: %.4f ms per hop\n", nrhs, variant, c,
-                           ms / 5);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best_code = c * 10 + variant;
-      }
+  }
+  // tile layout (BF16): one persistent CTA per SM
+  if (tiles && err == cudaSuccess) {
+    rc = sloppy_alloc(ctx, nrhs, TR);
+    if (rc) return rc;
+    ss = ctx->sloppy;
+    SmallBufs sb = small_layout(ss->small, ss->cap, part_blocks(vh));
+    TileField in, out;
+    rc = TileOps::field(ctx, ss, 2, vh, in);
+    if (!rc) rc = TileOps::field(ctx, ss, 6, vh, out);
+    if (rc) return rc;
+    const int nt = ss->cap / TR;
+    std::vector<int> tl(nt);
+    for (int k = 0; k < nt; ++k) tl[k] = k;
+    LQCD_CUDA_TRY(ctx, cudaMemset(ss->sd, 0, 7 * (size_t)(ss->cap / 2) * 6 * vh * sizeof(uint4)));
+    LQCD_CUDA_TRY(ctx, cudaMemcpy(sb.act_pairs, tl.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
+    LQCD_CUDA_TRY(ctx, cudaMemcpy(sb.counts, &nt, sizeof(int), cudaMemcpyHostToDevice));
+    LQCD_CUDA_TRY(ctx, cudaMemset(sb.counts + 8, 0, sizeof(int)));
+    const float ms = time_hop([&]() {
+      tile_hop(EPI_PLAIN, (cudaStream_t)0, nsm, ctx, 1, in, out, out, out, 0.f, 1.f, sb.act_pairs, sb.counts,
+               nullptr, TileOps::nb(vh), nrhs, nullptr, sb.counts + 8);
+    }, e0, e1, 5, &err);
+    int herr = 0;
+    if (err == cudaSuccess) cudaMemcpy(&herr, sb.counts + 8, sizeof(int), cudaMemcpyDeviceToHost);
+    if (verbose)
+      fprintf(stderr, "lqcd_autotune: nrhs %d variant %d (tiles of %d) 1 block/SM: %.4f ms per hop (error code %d)\n",
+              nrhs, TILE_VARIANT, TR, ms, herr);
+    if (err == cudaSuccess && herr == 0 && ms < best_ms) {
+      best_ms = ms;
+      best_code = 10 + TILE_VARIANT;
     }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_error(ctx, err, "lqcd_autotune");
   long long key = (long long)nrhs * 8 + precision;
   bool found = false;
   for (auto &kv : ctx->tuned)
