@@ -108,6 +108,11 @@ int tile_field_map(lqcd_ctx *ctx, TileField &f) {
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(ctx, LQCD_ERR_CUDA, "tile path: cuTensorMapEncodeTiled failed (%d)", (int)r);
+  const cuuint32_t sbox[2] = {32, 24};
+  r = enc(&f.smap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)f.d, dim, stride, sbox, estr,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(ctx, LQCD_ERR_CUDA, "tile path: cuTensorMapEncodeTiled (store) failed (%d)", (int)r);
   return LQCD_OK;
 }
 
@@ -141,7 +146,7 @@ int tile_hop(int epi, cudaStream_t q, int G, lqcd_ctx *ctx, int p_out, const Til
       if (e != cudaSuccess) return cuda_error(ctx, e, "tile hop: shared-memory attribute");          \
       attr_set[E] = true;                                                                            \
     }                                                                                                \
-    KL k_thop<E><<<G, T_THREADS, T_SMEM, q>>>(in.map, a);                                            \
+    KL k_thop<E><<<G, T_THREADS, T_SMEM, q>>>(in.map, out.smap, a);                                 \
     break;
   switch (epi) {
     THOP_CASE(EPI_PLAIN)

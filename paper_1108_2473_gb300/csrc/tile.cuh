@@ -48,8 +48,10 @@ constexpr int TN = 32;    // MMA N: 24 output reals, padded
 constexpr int T_A_HALF = 8 * 3072;             // one 64-RHS half of a stage: 8 neighbours x [24][64] BF16
 constexpr int T_A_BYTES = 2 * T_A_HALF;        // 48 KiB
 constexpr int T_W_BYTES = (TK / 8) * 512;      // 12 KiB: 24 K-chunks x 4 N-groups x 128 B
+constexpr int T_O_WARP = 24 * 32 * 2;          // one epilogue warp's share of an output block: 1.5 KiB
+constexpr int T_O_BYTES = 4 * T_O_WARP;        // one output block (site, tile): 6 KiB
 constexpr int T_THREADS = 320;                 // 10 warps
-constexpr int T_SMEM = 1024 + TNS * (T_A_BYTES + T_W_BYTES) + 256;
+constexpr int T_SMEM = 1024 + TNS * (T_A_BYTES + T_W_BYTES) + 2 * T_O_BYTES + 256;
 constexpr int T_TMEM_COLS = 64;                // two FP32 accumulators of TN columns
 
 // error codes written by the tile hop when a bounded wait runs out
@@ -185,26 +187,39 @@ __device__ __forceinline__ int neighbour(const Geom &g, const int c[4], int d) {
   return site_of(g, cn) >> 1;
 }
 
-// Work of one CTA: units [u0, u1) of (active tile, chunk of TCH sites), taken
-// in order; every role walks the same sequence of (tile, site) items.
+// Work of one CTA: units u = blockIdx.x, blockIdx.x + gridDim.x, ... of
+// (active tile, chunk of TCH sites), tile-major; every role walks the same
+// sequence of (tile, site) items.  The grid-stride order keeps the whole GPU
+// on a window of gridDim.x consecutive chunks of one tile, so that the eight
+// uses of a neighbour block fall close together in time and hit in L2.
 struct TItems {
-  int u0, u1, nch, vh;
+  int u0, u1, ustep, nch, vh;
   __device__ void init(int count, int nch_, int vh_) {
     nch = nch_;
     vh = vh_;
-    const long long U = (long long)count * nch;
-    u0 = (int)(U * blockIdx.x / gridDim.x);
-    u1 = (int)(U * (blockIdx.x + 1) / gridDim.x);
+    u0 = blockIdx.x;
+    u1 = count * nch;
+    ustep = gridDim.x;
   }
 };
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(x),
+               "r"(y), "r"(src)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 template <int EPI>
-__global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ CUtensorMap tin, THopArgs a) {
+__global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ CUtensorMap tin,
+                                                       const __grid_constant__ CUtensorMap tout, THopArgs a) {
   extern __shared__ __align__(1024) unsigned char t_smem_raw[];
   unsigned char *base = (unsigned char *)(((uintptr_t)t_smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char *sA = base;                                  // TNS x 48 KiB
   unsigned char *sW = base + TNS * T_A_BYTES;                // TNS x 12 KiB
-  uint64_t *bars = (uint64_t *)(sW + TNS * T_W_BYTES);       // full[TNS], empty[TNS], accf[2], acce[2], drain
+  unsigned char *sO = sW + TNS * T_W_BYTES;                  // 2 x 6 KiB output staging [acc][warp][24][32]
+  uint64_t *bars = (uint64_t *)(sO + 2 * T_O_BYTES);         // full[TNS], empty[TNS], accf[2], acce[2], drain
   uint64_t *full = bars, *empty = bars + TNS, *accf = bars + 2 * TNS, *acce = bars + 2 * TNS + 2;
   uint64_t *drain = bars + 2 * TNS + 4;
   uint32_t *tslot = (uint32_t *)(drain + 1);
@@ -249,7 +264,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
       int q = 0;
       int last_q[TNS];
       for (int s = 0; s < TNS; ++s) last_q[s] = -1;
-      for (int u = it.u0; u < it.u1 && !*abort; ++u) {
+      for (int u = it.u0; u < it.u1 && !*abort; u += it.ustep) {
         const int T = a.tlist[u / it.nch], ch = u % it.nch;
         const int j0 = ch * TCH, j1 = min(j0 + TCH, it.vh);
         if (a.prof) atomicAdd(a.prof + EPI, (unsigned long long)(j1 - j0) * (unsigned long long)min(TR, a.nrhs - T * TR));
@@ -282,7 +297,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
     if (lane == 0) {
       int q = 0;
       bool issued = false;
-      for (int u = it.u0; u < it.u1 && !*abort; ++u) {
+      for (int u = it.u0; u < it.u1 && !*abort; u += it.ustep) {
         const int ch = u % it.nch;
         const int j0 = ch * TCH, j1 = min(j0 + TCH, it.vh);
         for (int j = j0; j < j1; ++j, ++q) {
@@ -327,7 +342,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
       pi = a.spin.pi[d][s];
     }
     int q = 0;
-    for (int u = it.u0; u < it.u1 && !*abort; ++u) {
+    for (int u = it.u0; u < it.u1 && !*abort; u += it.ustep) {
       const int ch = u % it.nch;
       const int j0 = ch * TCH, j1 = min(j0 + TCH, it.vh);
       for (int j = j0; j < j1; ++j, ++q) {
@@ -371,10 +386,15 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int row = 32 * (warp & 3) + lane;  // TMEM lane = right-hand side within the tile
-    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
+    // One thread per right-hand side = TMEM lane; every step is warp-uniform
+    // (the accumulator wait is agreed on with __all_sync).  Each warp stages
+    // its 32 right-hand sides of the BF16 result in shared memory ([24][32])
+    // and writes them with one 2-d TMA store (box 32 x 24).
+    const int quarter = warp & 3;
+    const int row = 32 * quarter + lane;
+    const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
     int q = 0;
-    for (int u = it.u0; u < it.u1 && !*abort; ++u) {
+    for (int u = it.u0; u < it.u1 && !*abort; u += it.ustep) {
       const int T = a.tlist[u / it.nch], ch = u % it.nch;
       const int j0 = ch * TCH, j1 = min(j0 + TCH, it.vh);
       const int rhs = T * TR + row;
@@ -382,7 +402,20 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
       bool ok = true;
       for (int j = j0; j < j1; ++j, ++q) {
         const int acc = q & 1;
-        if (!mbar_wait(accf + acc, (q >> 1) & 1, abort)) {
+        const size_t e0 = (size_t)(T * g.Vh + j) * 24 * TR;
+        // epilogue operands: issued before the accumulator wait, so that they
+        // arrive while the MMA of this item completes
+        __nv_bfloat16 ar[24], br[24];
+        if (EPI != EPI_PLAIN) {
+#pragma unroll
+          for (int k = 0; k < 24; ++k) ar[k] = a.A[e0 + (size_t)k * TR + row];
+        }
+        if (EPI == EPI_DOTR) {
+#pragma unroll
+          for (int k = 0; k < 24; ++k) br[k] = a.B[e0 + (size_t)k * TR + row];
+        }
+        const bool got = mbar_wait(accf + acc, (q >> 1) & 1, abort);
+        if (!__all_sync(0xffffffffu, got)) {
           atomicCAS(a.err, 0, THOP_ERR_EPI);
           *abort = 1;
           ok = false;
@@ -393,40 +426,47 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
         tc_ld24(tmem + lane_off + acc * TN, v);
         tc_fence_before();
         mbar_arrive(acce + acc);
-        const size_t e0 = (size_t)(T * g.Vh + j) * 24 * TR + row;
 #pragma unroll
         for (int k = 0; k < 24; ++k) v[k] *= a.cH;
         if (EPI != EPI_PLAIN) {
-          float av[24];
 #pragma unroll
-          for (int k = 0; k < 24; ++k) av[k] = __bfloat162float(a.A[e0 + (size_t)k * TR]);
-#pragma unroll
-          for (int k = 0; k < 24; ++k) v[k] = fmaf(a.cA, av[k], v[k]);
+          for (int k = 0; k < 24; ++k) v[k] = fmaf(a.cA, __bfloat162float(ar[k]), v[k]);
           if (EPI == EPI_TS) {  // <out, A> and |out|^2
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
-              sre = fmaf(v[2 * k], av[2 * k], fmaf(v[2 * k + 1], av[2 * k + 1], sre));
-              sim = fmaf(v[2 * k], av[2 * k + 1], fmaf(-v[2 * k + 1], av[2 * k], sim));
+              const float a0 = __bfloat162float(ar[2 * k]), a1 = __bfloat162float(ar[2 * k + 1]);
+              sre = fmaf(v[2 * k], a0, fmaf(v[2 * k + 1], a1, sre));
+              sim = fmaf(v[2 * k], a1, fmaf(-v[2 * k + 1], a0, sim));
               snn = fmaf(v[2 * k], v[2 * k], fmaf(v[2 * k + 1], v[2 * k + 1], snn));
             }
           }
         }
-#pragma unroll
-        for (int k = 0; k < 24; ++k) a.out[e0 + (size_t)k * TR] = __float2bfloat16_rn(v[k]);
         if (EPI == EPI_DOTR) {  // <B, out>
 #pragma unroll
           for (int k = 0; k < 12; ++k) {
-            const float br = __bfloat162float(a.B[e0 + (size_t)(2 * k) * TR]);
-            const float bi = __bfloat162float(a.B[e0 + (size_t)(2 * k + 1) * TR]);
-            sre = fmaf(br, v[2 * k], fmaf(bi, v[2 * k + 1], sre));
-            sim = fmaf(br, v[2 * k + 1], fmaf(-bi, v[2 * k], sim));
+            const float b0 = __bfloat162float(br[2 * k]), b1 = __bfloat162float(br[2 * k + 1]);
+            sre = fmaf(b0, v[2 * k], fmaf(b1, v[2 * k + 1], sre));
+            sim = fmaf(b0, v[2 * k + 1], fmaf(-b1, v[2 * k], sim));
           }
         }
+        // this warp's staging buffer for accumulator acc is free once its TMA
+        // store of two items ago has read it
+        if (lane == 0) bulk_wait_read1();
+        __syncwarp();
+        unsigned char *ob = sO + acc * T_O_BYTES + quarter * T_O_WARP;
+        __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(ob);
+#pragma unroll
+        for (int k = 0; k < 24; ++k) o[k * 32 + lane] = __float2bfloat16_rn(v[k]);
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) tma_store_2d(&tout, 32 * quarter, (T * g.Vh + j) * 24, s_u32(ob));
       }
       if (!ok) break;
       if (EPI == EPI_DOTR || EPI == EPI_TS)
         a.part[(size_t)rhs * it.nch + ch] = D4S{(double)sre, (double)sim, 0.0, (double)snn};
     }
+    // every output store has completed before the CTA exits
+    if (lane == 0) bulk_wait_all();
   }
   tc_fence_before();
   __syncthreads();

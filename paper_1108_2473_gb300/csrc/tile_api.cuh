@@ -12,11 +12,13 @@ constexpr int TR = 128;  // right-hand sides per tile (the MMA M of the tensor-c
 constexpr int TCH = 64;  // sites per reduction chunk of the tile kernels
 
 // One BF16 sloppy field in 128-RHS tiles: [ntile][vh][24][128] BF16, with the
-// TMA tensor map the tensor-core hop reads it through (built by tile_field_map).
+// TMA tensor maps of the tensor-core hop (built by tile_field_map): `map`
+// loads a neighbour half (64 RHS x 24 rows, 128-byte swizzle), `smap` stores an
+// epilogue warp's share of an output block (32 RHS x 24 rows, no swizzle).
 struct TileField {
   __nv_bfloat16 *d = nullptr;
   int ntile = 0, vh = 0;
-  CUtensorMap map;
+  CUtensorMap map, smap;
 };
 
 int tile_field_map(lqcd_ctx *ctx, TileField &f);
