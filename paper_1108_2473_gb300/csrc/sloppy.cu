@@ -1475,6 +1475,36 @@ __global__ void k_build_lists(int n, const int *flags, int gs, int *act_groups, 
 
 }  // namespace lqcd
 
+// ==================================================== device-side loop control
+// The inner iterations of one outer cycle run as a CUDA-graph WHILE node
+// (conditional node) whose condition these kernels set on the device:
+// continue while any group is active, the tile hop reported no error, the
+// cycle's wall-clock budget is not spent and the iteration guard is not hit.
+//   counts[0] active groups, [8] tile-hop error code, [9] set when the budget
+//   ran out, [10] loop iterations run; clk[0] start (globaltimer ns), clk[1]
+//   budget in ns (written by the host before each launch).
+namespace lqcd {
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__global__ void k_loop_init(cudaGraphConditionalHandle h, int *counts, unsigned long long *clk) {
+  clk[0] = globaltimer_ns();
+  counts[9] = 0;
+  counts[10] = 0;
+  cudaGraphSetConditional(h, (counts[0] > 0 && counts[8] == 0 && clk[1] > 0) ? 1u : 0u);
+}
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, int *counts, const unsigned long long *clk, int max_loops) {
+  const int it = ++counts[10];
+  const bool late = globaltimer_ns() - clk[0] > clk[1];
+  if (late && counts[0] > 0) counts[9] = 1;
+  cudaGraphSetConditional(h, (counts[0] > 0 && counts[8] == 0 && !late && it < max_loops) ? 1u : 0u);
+}
+
+}  // namespace lqcd
+
 // ======================================================== host-side driver
 namespace lqcd {
 
@@ -1525,6 +1555,7 @@ struct SmallBufs {
   int *flags, *act_pairs, *ru_list, *ru_pairs, *cyc_list, *cyc_pairs, *counts;
   double *scale, *unscale;
   D4S *part;
+  unsigned long long *clk;  // loop start and budget (ns)
   size_t bytes;
   size_t size() const { return bytes; }
 };
@@ -1541,8 +1572,10 @@ static SmallBufs small_layout(void *base, int cap, int nbp) {
   b.ru_pairs = cv.take<int>(cap / 2);
   b.cyc_list = cv.take<int>(cap);
   b.cyc_pairs = cv.take<int>(cap / 2);
-  // [0] active groups, [1] RU RHS, [2] cycle RHS, [3] RU groups, [4] cycle groups, [8] tile-hop error code
+  // [0] active groups, [1] RU RHS, [2] cycle RHS, [3] RU groups, [4] cycle groups, [8] tile-hop error
+  // code, [9] loop stopped by the time budget, [10] loop iterations (see k_loop_cond)
   b.counts = cv.take<int>(16);
+  b.clk = cv.take<unsigned long long>(2);
   b.scale = cv.take<double>(cap);
   b.unscale = cv.take<double>(cap);
   b.part = cv.take<D4S>((size_t)cap * nbp);
@@ -1702,7 +1735,11 @@ struct TileOps {
 // The part of a lattice's solve that the uneven-batch driver talks to.
 struct RunIface {
   bool done = false, inner = false;
+  long long loop_kernels = 0;  // kernel launches per WHILE-loop iteration (set at capture)
   virtual ~RunIface() {}
+  virtual int *dev_counts() = 0;
+  virtual unsigned long long *dev_clock() = 0;
+  virtual int max_loops() const = 0;
   virtual int init() = 0;
   virtual int cycle_start() = 0;
   virtual void launch_iters(cudaStream_t q, int k) = 0;
@@ -1743,10 +1780,14 @@ struct MixedRun : RunIface {
   int cycle = 0;
   const int max_cycles = 10;
   bool timed_out = false;
+  unsigned long long budget_ns = ~0ull;  // host copy of the value sent to the device (pinned lifetime: the run)
 
   MixedRun(lqcd_ctx *c, const double2 *b_, double2 *x_, int n, const lqcd_solver_params &p_, lqcd_solve_stats *s_,
            cudaStream_t st_, double t0_)
       : ctx(c), b(b_), x(x_), nrhs(n), p(p_), stats(s_), st(st_), t0(t0_) {}
+  int *dev_counts() override { return sb.counts; }
+  unsigned long long *dev_clock() override { return sb.clk; }
+  int max_loops() const override { return p.max_iter + 1; }
 
   int init() override {
     int rc = sloppy_alloc(ctx, nrhs, Ops::GS);
@@ -1854,6 +1895,13 @@ struct MixedRun : RunIface {
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.cyc_list, hl.data(), hl.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.cyc_pairs, hp.data(), hp.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(counts, hc, sizeof(hc), cudaMemcpyHostToDevice, st));
+    // wall-clock budget left for this cycle's inner loop, in ns (the loop's own check)
+    budget_ns = ~0ull;
+    if (p.timeout_ms > 0) {
+      const double left = p.timeout_ms - (wall_ms() - t0);
+      budget_ns = left > 0 ? (unsigned long long)(left * 1e6) : 0ull;
+    }
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.clk + 1, &budget_ns, sizeof(budget_ns), cudaMemcpyHostToDevice, st));
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.scale, hscale.data(), cap * sizeof(double), cudaMemcpyHostToDevice, st));
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.unscale, hun.data(), cap * sizeof(double), cudaMemcpyHostToDevice, st));
     LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(sb.sc, hs.data(), cap * sizeof(SState), cudaMemcpyHostToDevice, st));
@@ -1935,9 +1983,10 @@ struct MixedRun : RunIface {
     }
   }
 
-  // enqueue the read-back of the active count and the tile hop's error code
+  // enqueue the read-back of the active count, the tile hop's error code and
+  // the device loop's budget flag and iteration count
   int request_count(cudaStream_t q) override {
-    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(ss->h_counts, sb.counts, 9 * sizeof(int), cudaMemcpyDeviceToHost, q));
+    LQCD_CUDA_TRY(ctx, cudaMemcpyAsync(ss->h_counts, sb.counts, 11 * sizeof(int), cudaMemcpyDeviceToHost, q));
     return LQCD_OK;
   }
 
@@ -1947,6 +1996,10 @@ struct MixedRun : RunIface {
       return set_error(ctx, LQCD_ERR_CUDA,
                        "mixed: the tensor-core hop stopped after a bounded wait ran out (code %d)", ss->h_counts[8]);
     bool any = ss->h_counts[0] > 0;
+    if (any && ss->h_counts[9]) {  // the device loop stopped on the time budget
+      timed_out = true;
+      any = false;
+    }
     if (any && p.timeout_ms > 0 && wall_ms() - t0 > p.timeout_ms) {
       timed_out = true;
       any = false;
@@ -2002,11 +2055,55 @@ static cudaError_t capture_graph(cudaStream_t st, F body, cudaGraphExec_t *exec,
   return e;
 }
 
-constexpr int ITERS_PER_POLL = 4;
+constexpr int ITERS_PER_POLL = 4;  // inner iterations per host poll when launching directly (profiling)
 
-// Single lattice: the four-iteration sequence is captured once into a CUDA
-// graph and replayed (launched directly while profiling, so every hop launch
-// gets its own events).
+// Append to graph g, for one lattice: k_loop_init -> WHILE node whose body is
+// one inner iteration followed by k_loop_cond.  The body is recorded by
+// capturing launch_iters on st into the conditional node's child graph.
+static cudaError_t add_cycle_loop(cudaGraph_t g, RunIface *run, cudaStream_t st) {
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, 0);
+  if (e != cudaSuccess) return e;
+  int *counts = run->dev_counts();
+  unsigned long long *clk = run->dev_clock();
+  void *init_args[] = {&h, &counts, &clk};
+  cudaKernelNodeParams kp = {};
+  kp.func = (void *)k_loop_init;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(1);
+  kp.kernelParams = init_args;
+  cudaGraphNode_t init_node, loop_node;
+  e = cudaGraphAddKernelNode(&init_node, g, nullptr, 0, &kp);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  e = cudaGraphAddNode(&loop_node, g, &init_node, nullptr, 1, &cp);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  const long long before = g_launches.load();
+  run->launch_iters(st, 1);
+  KL k_loop_cond<<<1, 1, 0, st>>>(h, counts, clk, run->max_loops());
+  run->loop_kernels = g_launches.load() - before;
+  g_launches -= run->loop_kernels;  // recording launches nothing
+  return cudaStreamEndCapture(st, &body);
+}
+
+// the library's launch counter after a replay: the init kernel plus the kernels
+// of every loop iteration the device ran (read back in h_counts[10])
+static void count_loop_launches(RunIface *run, const SloppyState *ss) {
+  g_launches += 1 + run->loop_kernels * (long long)ss->h_counts[10];
+}
+
+// Single lattice: each outer cycle's inner loop is one launch of a CUDA graph
+// holding a WHILE node (the device decides when to stop), captured once per
+// configuration; the host synchronises once per cycle.  While profiling the
+// iterations are launched directly, four per host poll, so that every hop
+// launch gets its own events.
 static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const lqcd_solver_params &p,
                        lqcd_solve_stats *stats, cudaStream_t st, double t0) {
   std::unique_ptr<RunIface> run(make_run(ctx, b, x, nrhs, p, stats, st, t0));
@@ -2026,14 +2123,20 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
       if (!ss->graph || ss->graph_key != key) {
         if (ss->graph) cudaGraphExecDestroy(ss->graph);
         ss->graph = nullptr;
-        RunIface *rp = run.get();
-        cudaError_t e = capture_graph(st, [&](cudaStream_t q) { rp->launch_iters(q, ITERS_PER_POLL); }, &ss->graph,
-                                      &ss->graph_kernels);
-        if (e != cudaSuccess) return cuda_error(ctx, e, "mixed: capture of the iteration graph");
+        cudaGraph_t g = nullptr;
+        LQCD_CUDA_TRY(ctx, cudaGraphCreate(&g, 0));
+        cudaError_t e = add_cycle_loop(g, run.get(), st);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ss->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+          ss->graph = nullptr;
+          return cuda_error(ctx, e, "mixed: capture of the inner-loop graph");
+        }
         ss->graph_key = key;
+        ss->graph_kernels = run->loop_kernels;
       }
+      run->loop_kernels = ss->graph_kernels;
       LQCD_CUDA_TRY(ctx, cudaGraphLaunch(ss->graph, st));
-      g_launches += ss->graph_kernels;
     } else {
       run->launch_iters(st, ITERS_PER_POLL);
       LQCD_LAUNCH_CHECK(ctx, "mixed: iteration");
@@ -2041,18 +2144,23 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
     rc = run->request_count(st);
     if (rc) return rc;
     LQCD_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (use_graph) count_loop_launches(run.get(), ss);
     rc = run->poll();
     if (rc) return rc;
   }
   return run->finish();
 }
 
-// Uneven batch: all lattices' iterations in one captured graph (one branch
-// per lattice); one graph launch advances every lattice by four iterations.
+// Uneven batch: one CUDA graph with a branch per lattice (k_loop_init -> WHILE
+// node), so that one launch runs every lattice's inner loop of the current
+// outer cycle concurrently; each lattice's outer refinement runs between
+// launches.
 static int mixed_batch(std::vector<lqcd_ctx *> &ctxs, std::vector<const double2 *> &bs, std::vector<double2 *> &xs,
                        std::vector<int> &ns, const lqcd_solver_params &p, std::vector<lqcd_solve_stats *> &stats,
                        cudaStream_t st, std::vector<cudaStream_t> &side, cudaGraphExec_t *gexec,
                        std::vector<double> *gkey, long long *gkernels) {
+  (void)side;
+  (void)gkernels;
   const size_t nl = ctxs.size();
   const double t0 = wall_ms();
   std::vector<std::unique_ptr<RunIface>> runs;
@@ -2061,6 +2169,7 @@ static int mixed_batch(std::vector<lqcd_ctx *> &ctxs, std::vector<const double2 
     int rc = r->init();
     if (rc) return rc;
   }
+  std::vector<long long> per_iter(nl, 0);
   for (;;) {
     bool any = false;
     for (auto &r : runs) {
@@ -2079,29 +2188,31 @@ static int mixed_batch(std::vector<lqcd_ctx *> &ctxs, std::vector<const double2 
     if (!*gexec || *gkey != key) {
       if (*gexec) cudaGraphExecDestroy(*gexec);
       *gexec = nullptr;
-      std::vector<cudaEvent_t> ev(nl + 1);
-      for (auto &e : ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-      cudaError_t e = capture_graph(st, [&](cudaStream_t q) {
-        cudaEventRecord(ev[nl], q);
-        for (size_t l = 0; l < nl; ++l) {
-          cudaStreamWaitEvent(side[l], ev[nl], 0);
-          runs[l]->launch_iters(side[l], ITERS_PER_POLL);
-          cudaEventRecord(ev[l], side[l]);
-          cudaStreamWaitEvent(q, ev[l], 0);
-        }
-      }, gexec, gkernels);
-      for (auto &ee : ev) cudaEventDestroy(ee);
-      if (e != cudaSuccess) return cuda_error(ctxs[0], e, "batch: capture of the iteration graph");
+      cudaGraph_t g = nullptr;
+      LQCD_CUDA_TRY(ctxs[0], cudaGraphCreate(&g, 0));
+      cudaError_t e = cudaSuccess;
+      for (size_t l = 0; l < nl && e == cudaSuccess; ++l) {
+        e = add_cycle_loop(g, runs[l].get(), st);
+        per_iter[l] = runs[l]->loop_kernels;
+      }
+      if (e == cudaSuccess) e = cudaGraphInstantiate(gexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        *gexec = nullptr;
+        return cuda_error(ctxs[0], e, "batch: capture of the inner-loop graph");
+      }
       *gkey = key;
     }
     LQCD_CUDA_TRY(ctxs[0], cudaGraphLaunch(*gexec, st));
-    g_launches += *gkernels;
-    for (auto &r : runs)
-      if (!r->done) {
-        int rc = r->request_count(st);
-        if (rc) return rc;
-      }
+    for (auto &r : runs) {
+      int rc = r->request_count(st);
+      if (rc) return rc;
+    }
     LQCD_CUDA_TRY(ctxs[0], cudaStreamSynchronize(st));
+    for (size_t l = 0; l < nl; ++l) {
+      runs[l]->loop_kernels = per_iter[l];
+      count_loop_launches(runs[l].get(), ctxs[l]->sloppy);
+    }
     for (auto &r : runs)
       if (!r->done && r->inner) {
         int rc = r->poll();

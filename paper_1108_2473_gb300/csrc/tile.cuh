@@ -51,7 +51,8 @@ constexpr int T_W_BYTES = (TK / 8) * 512;      // 12 KiB: 24 K-chunks x 4 N-grou
 constexpr int T_O_WARP = 24 * 32 * 2;          // one epilogue warp's share of an output block: 1.5 KiB
 constexpr int T_O_BYTES = 4 * T_O_WARP;        // one output block (site, tile): 6 KiB
 constexpr int T_THREADS = 320;                 // 10 warps
-constexpr int T_SMEM = 1024 + TNS * (T_A_BYTES + T_W_BYTES) + 2 * T_O_BYTES + 256;
+constexpr int T_L_BYTES = 8 * 9 * 4;           // one site's link bundle: 288 B
+constexpr int T_SMEM = 1024 + TNS * (T_A_BYTES + T_W_BYTES) + 2 * T_O_BYTES + TNS * T_L_BYTES + 256;
 constexpr int T_TMEM_COLS = 64;                // two FP32 accumulators of TN columns
 
 // error codes written by the tile hop when a bounded wait runs out
@@ -127,6 +128,11 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
           dst),
       "l"(map), "r"(x), "r"(y), "r"(s_u32(bar))
       : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(s_u32(bar))
+               : "memory");
 }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -219,9 +225,11 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
   unsigned char *sA = base;                                  // TNS x 48 KiB
   unsigned char *sW = base + TNS * T_A_BYTES;                // TNS x 12 KiB
   unsigned char *sO = sW + TNS * T_W_BYTES;                  // 2 x 6 KiB output staging [acc][warp][24][32]
-  uint64_t *bars = (uint64_t *)(sO + 2 * T_O_BYTES);         // full[TNS], empty[TNS], accf[2], acce[2], drain
-  uint64_t *full = bars, *empty = bars + TNS, *accf = bars + 2 * TNS, *acce = bars + 2 * TNS + 2;
-  uint64_t *drain = bars + 2 * TNS + 4;
+  unsigned char *sL = sO + 2 * T_O_BYTES;                    // TNS x 288 B link bundles
+  uint64_t *bars = (uint64_t *)(sL + TNS * T_L_BYTES);       // full, empty, lfull [TNS]; accf, acce [2]; drain
+  uint64_t *full = bars, *empty = bars + TNS, *lfull = bars + 2 * TNS;
+  uint64_t *accf = bars + 3 * TNS, *acce = bars + 3 * TNS + 2;
+  uint64_t *drain = bars + 3 * TNS + 4;
   uint32_t *tslot = (uint32_t *)(drain + 1);
   volatile int *abort = (volatile int *)(tslot + 1);
 
@@ -237,6 +245,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
     for (int s = 0; s < TNS; ++s) {
       mbar_init(full + s, 1 + 128);
       mbar_init(empty + s, 1);
+      mbar_init(lfull + s, 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf + b, 1);
@@ -277,6 +286,9 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
           }
           int c[4];
           coords_of(g, a.p_out, j, c);
+          // the site's link bundle for the W builders, then the neighbour tiles
+          mbar_arrive_tx(lfull + s, T_L_BYTES);
+          bulk_load(s_u32(sL + s * T_L_BYTES), a.links + (size_t)(a.p_out * g.Vh + j) * 72, T_L_BYTES, lfull + s);
           mbar_arrive_tx(full + s, T_A_BYTES);
           const uint32_t dst = s_u32(sA + s * T_A_BYTES);
 #pragma unroll
@@ -290,7 +302,10 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
       }
       // copies in flight must land before the CTA exits (normally already consumed)
       for (int s = 0; s < TNS; ++s)
-        if (last_q[s] >= 0) mbar_wait(full + s, (last_q[s] / TNS) & 1, abort);
+        if (last_q[s] >= 0) {
+          mbar_wait(full + s, (last_q[s] / TNS) & 1, abort);
+          mbar_wait(lfull + s, (last_q[s] / TNS) & 1, abort);
+        }
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -347,18 +362,19 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
       const int j0 = ch * TCH, j1 = min(j0 + TCH, it.vh);
       for (int j = j0; j < j1; ++j, ++q) {
         const int st = q % TNS;
-        if (q >= TNS && !mbar_wait(empty + st, ((q / TNS) - 1) & 1, abort)) {
+        if ((q >= TNS && !mbar_wait(empty + st, ((q / TNS) - 1) & 1, abort)) ||
+            !mbar_wait(lfull + st, (q / TNS) & 1, abort)) {
           atomicCAS(a.err, 0, THOP_ERR_W);
           *abort = 1;
           break;
         }
         if (active) {
           unsigned char *W = sW + st * T_W_BYTES;
-          const uint32_t *L = a.links + ((size_t)(a.p_out * g.Vh + j) * 8 + d) * 9 + c * 3;
+          const uint32_t *L = reinterpret_cast<const uint32_t *>(sL + st * T_L_BYTES) + d * 9 + c * 3;
           const int nr = (s * 3 + c) * 2;
 #pragma unroll
           for (int cc = 0; cc < 3; ++cc) {
-            const uint32_t w = __ldg(L + cc);
+            const uint32_t w = L[cc];
             // identity block: z = C[c][cc]
             const int kd = d * 24 + (s * 3 + cc) * 2;
             const uint32_t cr = w & 0xffffu, ci = w >> 16;
@@ -393,6 +409,24 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
     const int quarter = warp & 3;
     const int row = 32 * quarter + lane;
     const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
+    // epilogue operands (A, B) of item q + 1 are loaded while item q completes
+    uint32_t na[12], nb[12];
+    auto load_ops = [&](int T, int j) {
+      const size_t e0 = (size_t)(T * g.Vh + j) * 24 * TR + row;
+      if (EPI != EPI_PLAIN) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+          na[k] = (uint32_t)__bfloat16_as_ushort(a.A[e0 + (size_t)(2 * k) * TR]) |
+                  ((uint32_t)__bfloat16_as_ushort(a.A[e0 + (size_t)(2 * k + 1) * TR]) << 16);
+      }
+      if (EPI == EPI_DOTR) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+          nb[k] = (uint32_t)__bfloat16_as_ushort(a.B[e0 + (size_t)(2 * k) * TR]) |
+                  ((uint32_t)__bfloat16_as_ushort(a.B[e0 + (size_t)(2 * k + 1) * TR]) << 16);
+      }
+    };
+    if (it.u0 < it.u1) load_ops(a.tlist[it.u0 / it.nch], (it.u0 % it.nch) * TCH);
     int q = 0;
     for (int u = it.u0; u < it.u1 && !*abort; u += it.ustep) {
       const int T = a.tlist[u / it.nch], ch = u % it.nch;
@@ -402,17 +436,16 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
       bool ok = true;
       for (int j = j0; j < j1; ++j, ++q) {
         const int acc = q & 1;
-        const size_t e0 = (size_t)(T * g.Vh + j) * 24 * TR;
-        // epilogue operands: issued before the accumulator wait, so that they
-        // arrive while the MMA of this item completes
-        __nv_bfloat16 ar[24], br[24];
-        if (EPI != EPI_PLAIN) {
+        uint32_t ca[12], cb[12];
 #pragma unroll
-          for (int k = 0; k < 24; ++k) ar[k] = a.A[e0 + (size_t)k * TR + row];
+        for (int k = 0; k < 12; ++k) {
+          ca[k] = na[k];
+          cb[k] = nb[k];
         }
-        if (EPI == EPI_DOTR) {
-#pragma unroll
-          for (int k = 0; k < 24; ++k) br[k] = a.B[e0 + (size_t)k * TR + row];
+        // next item: the following site of this unit, else the first site of the next unit
+        if (EPI != EPI_PLAIN) {
+          if (j + 1 < j1) load_ops(T, j + 1);
+          else if (u + it.ustep < it.u1) load_ops(a.tlist[(u + it.ustep) / it.nch], ((u + it.ustep) % it.nch) * TCH);
         }
         const bool got = mbar_wait(accf + acc, (q >> 1) & 1, abort);
         if (!__all_sync(0xffffffffu, got)) {
@@ -430,11 +463,11 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
         for (int k = 0; k < 24; ++k) v[k] *= a.cH;
         if (EPI != EPI_PLAIN) {
 #pragma unroll
-          for (int k = 0; k < 24; ++k) v[k] = fmaf(a.cA, __bfloat162float(ar[k]), v[k]);
-          if (EPI == EPI_TS) {  // <out, A> and |out|^2
-#pragma unroll
-            for (int k = 0; k < 12; ++k) {
-              const float a0 = __bfloat162float(ar[2 * k]), a1 = __bfloat162float(ar[2 * k + 1]);
+          for (int k = 0; k < 12; ++k) {
+            const float a0 = __uint_as_float(ca[k] << 16), a1 = __uint_as_float(ca[k] & 0xffff0000u);
+            v[2 * k] = fmaf(a.cA, a0, v[2 * k]);
+            v[2 * k + 1] = fmaf(a.cA, a1, v[2 * k + 1]);
+            if (EPI == EPI_TS) {  // <out, A> and |out|^2
               sre = fmaf(v[2 * k], a0, fmaf(v[2 * k + 1], a1, sre));
               sim = fmaf(v[2 * k], a1, fmaf(-v[2 * k + 1], a0, sim));
               snn = fmaf(v[2 * k], v[2 * k], fmaf(v[2 * k + 1], v[2 * k + 1], snn));
@@ -444,7 +477,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
         if (EPI == EPI_DOTR) {  // <B, out>
 #pragma unroll
           for (int k = 0; k < 12; ++k) {
-            const float b0 = __bfloat162float(br[2 * k]), b1 = __bfloat162float(br[2 * k + 1]);
+            const float b0 = __uint_as_float(cb[k] << 16), b1 = __uint_as_float(cb[k] & 0xffff0000u);
             sre = fmaf(b0, v[2 * k], fmaf(b1, v[2 * k + 1], sre));
             sim = fmaf(b0, v[2 * k + 1], fmaf(-b1, v[2 * k], sim));
           }
