@@ -58,11 +58,19 @@ def _peaks():
 # FP32 ALU peak of the hopping term: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per output (site, RHS) of
-# k_hop_pair<BF16P, *, 4, 1>, from one ncu --set full capture on 16^3x32 with 48 RHS
-# (pair fields larger than L2): PLAIN 145.6, DOTR 285.8, TS 208.7; the solver runs them
-# 2 : 1 : 1 over the same pairs.  Scaled to a launch by the (site, RHS) it processes.
-HOP_DRAM_BYTES_PER_SITE_RHS = (2 * 145.6 + 285.8 + 208.7) / 4
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per output (site, RHS) of the
+# hop kernel each variant runs, from ncu captures of that kernel (profiles/): the solver
+# runs the PLAIN, DOTR and TS epilogues 2 : 1 : 1 over the same right-hand sides.  Scaled
+# to a launch by the (site, RHS) it processes; None where no capture of the current
+# kernel exists.
+HOP_DRAM_BYTES_PER_SITE_RHS = {
+    # k_hop_pair<BF16P, *, 4, 1>, 16^3x32, 48 RHS: PLAIN 145.6, DOTR 285.8, TS 208.7
+    1: (2 * 145.6 + 285.8 + 208.7) / 4,
+}
+HOP_KERNEL = {0: "k_hop_pair<*, *, 1, 1> (pair layout, FFMA2)", 1: "k_hop_pair<*, *, 4, 1> (pair layout, FFMA2)",
+              2: "k_hop_pair<*, *, 2, 2> (pair layout, FFMA2)", 3: "k_hop_pair<*, *, 1, 4> (pair layout, FFMA2)",
+              4: "k_hop_mma (pair layout, mma.sync tf32)",
+              5: "k_thop (128-RHS tiles, TMA-staged neighbours, tcgen05.mma into TMEM)"}
 
 
 class Clocks:
@@ -325,13 +333,14 @@ def config_runs(L, h, dev, stream):
 
 # ------------------------------------------- GPU idle time inside one step
 def gpu_idle(step_fn, stream, dev):
-    """One untimed step under torch.profiler (CUPTI kernel records): the step's
-    CUDA-event time, the summed device time of its kernels, copies and sets,
-    and the difference (time the GPU waited on the host: polls, launches)."""
+    """One untimed step under torch.profiler (CUPTI activity records): the step's
+    CUDA-event time, the summed duration of the kernels, copies and sets it ran
+    (read from the exported trace), and the difference -- time the GPU waited on
+    the host (polls, launches, synchronisations)."""
+    import tempfile
     import torch
     try:
         from torch.profiler import profile, ProfilerActivity
-        from torch.autograd import DeviceType
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize(dev)
@@ -341,13 +350,15 @@ def gpu_idle(step_fn, stream, dev):
             b.record(stream)
             b.synchronize()
         step_ms = a.elapsed_time(b)
+        with tempfile.NamedTemporaryFile(suffix=".json") as f:
+            pr.export_chrome_trace(f.name)
+            with open(f.name) as fh:
+                trace = json.load(fh)
+        ev = trace.get("traceEvents", trace) if isinstance(trace, dict) else trace
         busy_us, n = 0.0, 0
-        for e in pr.events():
-            if getattr(e, "device_type", None) == DeviceType.CUDA:
-                t = getattr(e, "device_time_total", None)
-                if t is None:
-                    t = getattr(e, "cuda_time_total", 0.0)
-                busy_us += t
+        for e in ev:
+            if isinstance(e, dict) and e.get("ph") == "X" and e.get("cat") in ("kernel", "gpu_memcpy", "gpu_memset"):
+                busy_us += float(e.get("dur", 0.0))
                 n += 1
         out = {"step_ms": step_ms, "device_busy_ms": busy_us / 1e3, "idle_ms": step_ms - busy_us / 1e3,
                "idle_frac": 1.0 - busy_us / 1e3 / step_ms, "device_activities": n,
@@ -667,17 +678,17 @@ def run_ours(args, rank, world, local_rank):
     achieved = alg_bytes / hop_s / 1e9 if hop_s > 0 else 0.0
     achieved_epi = prof["hop_bytes"] / hop_s / 1e9 if hop_s > 0 else 0.0
     traffic = None
-    # the captured counters describe the BF16 kernel of variant 1 only
-    if HOP_DRAM_BYTES_PER_SITE_RHS is not None and prof["hop_launches"] > 0 and args.prec == "bf16" \
-            and hop_variant == 1:
-        traffic = HOP_DRAM_BYTES_PER_SITE_RHS * prof["hop_site_rhs"] / prof["hop_launches"]
+    # the captured counters describe the BF16 kernels only
+    if hop_variant in HOP_DRAM_BYTES_PER_SITE_RHS and prof["hop_launches"] > 0 and args.prec == "bf16":
+        traffic = HOP_DRAM_BYTES_PER_SITE_RHS[hop_variant] * prof["hop_site_rhs"] / prof["hop_launches"]
     roofline = {
         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
         "traffic": traffic, "peak_kind": peak_kind,
         "bytes_model": "96 B per output (site, RHS) + 8 x 24 B reconstruct-12 links per site per launch",
         "achieved_epilogue_inclusive": achieved_epi, "frac_epilogue_inclusive": achieved_epi / peak,
         "profiled_steps": args.prof_steps,
-        "kernel": f"k_hop_pair<{args.prec.upper()}> (sloppy Wilson hopping term on RHS pairs, all epilogues)",
+        "kernel": f"{HOP_KERNEL.get(hop_variant, hop_variant)}, {args.prec.upper()} sloppy Wilson hopping term, "
+                  f"all epilogues",
         "alg_bytes_per_launch": alg_bytes / max(prof["hop_launches"], 1),
         "site_rhs_per_launch": prof["hop_site_rhs"] / max(prof["hop_launches"], 1),
         "avg_launch_ms": prof["hop_ms"] / max(prof["hop_launches"], 1),
