@@ -331,45 +331,6 @@ def config_runs(L, h, dev, stream):
     return out
 
 
-# ------------------------------------------- GPU idle time inside one step
-def gpu_idle(step_fn, stream, dev):
-    """One untimed step under torch.profiler (CUPTI activity records): the step's
-    CUDA-event time, the summed duration of the kernels, copies and sets it ran
-    (read from the exported trace), and the difference -- time the GPU waited on
-    the host (polls, launches, synchronisations)."""
-    import tempfile
-    import torch
-    try:
-        from torch.profiler import profile, ProfilerActivity
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        with profile(activities=[ProfilerActivity.CPU, ProfilerActivity.CUDA]) as pr:
-            a.record(stream)
-            step_fn()
-            b.record(stream)
-            b.synchronize()
-        step_ms = a.elapsed_time(b)
-        with tempfile.NamedTemporaryFile(suffix=".json") as f:
-            pr.export_chrome_trace(f.name)
-            with open(f.name) as fh:
-                trace = json.load(fh)
-        ev = trace.get("traceEvents", trace) if isinstance(trace, dict) else trace
-        busy_us, n = 0.0, 0
-        for e in ev:
-            if isinstance(e, dict) and e.get("ph") == "X" and e.get("cat") in ("kernel", "gpu_memcpy", "gpu_memset"):
-                busy_us += float(e.get("dur", 0.0))
-                n += 1
-        out = {"step_ms": step_ms, "device_busy_ms": busy_us / 1e3, "idle_ms": step_ms - busy_us / 1e3,
-               "idle_frac": 1.0 - busy_us / 1e3 / step_ms, "device_activities": n,
-               "note": "one extra step under torch.profiler, not a timed step"}
-        if n == 0:
-            out["error"] = "no device activity recorded"
-        return out
-    except Exception as ex:  # profiler unavailable: report why
-        return {"error": f"{type(ex).__name__}: {ex}"[:200]}
-
-
 # --------------------------------------------- the paper's exact-loop configuration
 def _cfg0_oracle_worker(args):
     """Oracle FP64 even-odd BiCGstab on a chunk of the 4^4 point sources (timed)."""
@@ -616,7 +577,6 @@ def run_ours(args, rank, world, local_rank):
     for k in range(args.prof_steps):
         step(idx[args.warmup + k])
     prof = L.lqcd_profile_end(h)
-    idle = gpu_idle(lambda: step(idx[args.warmup]), stream, dev)
     t_max = replicas.max_over_ranks(ms, device=dev)
     solves = nrhs * args.steps * world
     value = solves / (t_max / 1e3)
@@ -634,6 +594,11 @@ def run_ours(args, rank, world, local_rank):
 
     if rank != 0:
         L.lqcd_destroy(h)
+        return
+    if args.skip_extras:  # profiling runs: the timed steps only
+        L.lqcd_destroy(h)
+        print(json.dumps({"metric": METRIC, "value": value, "unit": "RHS solves/s", "ms_per_step": t_max / args.steps,
+                          "note": "--skip-extras: timed steps only, no extra rows"}), flush=True)
         return
     # the gradient row on the last step's sources and solutions (before they are reused)
     grad = gradient_step(L, h, src, x, params, dev, stream)
@@ -730,7 +695,6 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "RHS solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "gpu_idle": idle,
         "clocks": clk,
         "gradient": grad,
         "configs": configs,
@@ -754,6 +718,8 @@ def main():
     ap.add_argument("--cpu-rhs", type=int, default=16)
     ap.add_argument("--ref-rhs", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="stop after the timed steps and the end-to-end leg (for launch-list profiling)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     rank = int(os.environ.get("RANK", "0"))

@@ -98,11 +98,11 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 int tile_field_map(lqcd_ctx *ctx, TileField &f) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
   if (!enc) return set_error(ctx, LQCD_ERR_CUDA, "tile path: cuTensorMapEncodeTiled is unavailable");
-  // 2-d view: [ntile * Vh * 24 rows][128 RHS] BF16, rows of 256 bytes; boxes of
-  // 64 RHS x 24 rows (one neighbour half), 128-byte swizzle
-  const cuuint64_t dim[2] = {(cuuint64_t)TR, (cuuint64_t)f.ntile * f.vh * 24};
-  const cuuint64_t stride[1] = {(cuuint64_t)TR * 2};
-  const cuuint32_t box[2] = {64, 24};
+  // 2-d view: [ntile * Vh * 48 rows][64 RHS] BF16, rows of 128 bytes; boxes of
+  // 64 RHS x 48 rows (one neighbour block, both halves), 128-byte swizzle
+  const cuuint64_t dim[2] = {64, (cuuint64_t)f.ntile * f.vh * 48};
+  const cuuint64_t stride[1] = {128};
+  const cuuint32_t box[2] = {64, 48};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(&f.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)f.d, dim, stride, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -125,6 +125,7 @@ int tile_hop(int epi, cudaStream_t q, int G, lqcd_ctx *ctx, int p_out, const Til
   a.p_out = p_out;
   a.links = ctx->Ub16;
   a.out = out.d;
+  a.in = in.d;
   a.A = A.d;
   a.B = B.d;
   a.cA = cA;
@@ -146,7 +147,7 @@ int tile_hop(int epi, cudaStream_t q, int G, lqcd_ctx *ctx, int p_out, const Til
       if (e != cudaSuccess) return cuda_error(ctx, e, "tile hop: shared-memory attribute");          \
       attr_set[E] = true;                                                                            \
     }                                                                                                \
-    KL k_thop<E><<<G, T_THREADS, T_SMEM, q>>>(in.map, out.smap, a);                                 \
+    KL k_thop<E><<<G, T_THREADS, T_SMEM, q>>>(in.map, a);                                           \
     break;
   switch (epi) {
     THOP_CASE(EPI_PLAIN)
@@ -185,17 +186,18 @@ __device__ __forceinline__ uint4 f_to_bf8(const float f[8]) {
   }
   return make_uint4(u[0], u[1], u[2], u[3]);
 }
-// rows 2c (re) and 2c + 1 (im) of RHS group g at (tile T, site j)
+// real k of the 8 right-hand sides 8g .. 8g+7 at (tile T, site j), in uint4 units;
+// real k + 1 (the imaginary part when k is even) is 64 elements = 8 uint4 further
 __device__ __forceinline__ size_t trow(int T, int vh, int j, int k, int g) {
-  return ((((size_t)T * vh + j) * 24 + k) * TR + 8 * g) / 8;  // in uint4 units
+  return tile_elem(T, vh, j, k, 8 * g) / 8;
 }
 __device__ __forceinline__ void load_c8(const uint4 *f, size_t re_idx, float re[8], float im[8]) {
   bf8_to_f(f[re_idx], re);
-  bf8_to_f(f[re_idx + TR / 8], im);
+  bf8_to_f(f[re_idx + 8], im);
 }
 __device__ __forceinline__ void store_c8(uint4 *f, size_t re_idx, const float re[8], const float im[8]) {
   f[re_idx] = f_to_bf8(re);
-  f[re_idx + TR / 8] = f_to_bf8(im);
+  f[re_idx + 8] = f_to_bf8(im);
 }
 __device__ __forceinline__ float2 sc2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 

@@ -3,10 +3,9 @@
 // of the operator D = 1 - kappa H).
 //
 // Layout.  A 16-bit (BF16) sloppy field holds its right-hand sides in tiles of
-// TR = 128: [tile][Vh][24 reals][128 RHS], so the 128 right-hand sides of one
-// site and one real are 256 contiguous bytes, and one site's block of a tile
-// (24 x 128 values, 6 KiB) is contiguous.  The 24 reals are ordered
-// ((spin * 3 + colour) * 2 + re/im).
+// TR = 128: [tile][Vh][2 halves][24 reals][64 RHS] (tile_elem), so one site's
+// block of a tile (24 x 128 values, 6 KiB) is contiguous: 48 rows of 128 bytes,
+// one TMA box.  The 24 reals are ordered ((spin * 3 + colour) * 2 + re/im).
 //
 // Hopping term on the tensor cores.  For an output site x of parity p,
 //   (H in)(x) = sum_{d=0..7} [P_d (x) C_d(x)] in(n_d(x)),
@@ -21,16 +20,22 @@
 //
 // Data flow per (site, tile) item, warp-specialised inside one persistent CTA
 // per SM, TNS-stage shared-memory ring:
-//   * warp 0 (one thread): TMA -- 16 tiled loads (8 neighbours x 2 halves of 64
-//     right-hand sides, [24 rows][128 B] boxes with the 128-byte swizzle) into
-//     the stage's A buffer, which is then the MN-major SW128 canonical layout;
+//   * warp 0: TMA -- T_NT tiled loads (one [48 rows][128 B] box per neighbour,
+//     128-byte swizzle) and one bulk copy of the site's link bundle into the
+//     stage; the A buffer is [neighbour][half][24 rows][64 RHS], eight MN-major
+//     SW128 blocks, which the MMAs address with per-step descriptors;
+//   * warps 10-13: the other 8 - T_NT neighbour blocks by cp.async (16 bytes
+//     per request, written to the same swizzled positions), so that the TMA
+//     engine and the load/store units share the ~48 KiB an item needs;
 //   * warps 2-5: build W (K-major, no swizzle) from the site's eight BF16 colour
-//     matrices; entries of zero spin blocks are written once at start;
+//     matrices into a ring of two W buffers; entries of zero spin blocks are
+//     written once at start;
 //   * warp 1 (one thread): the twelve MMAs into one of two TMEM accumulators,
 //     then tcgen05.commit to free the stage and to hand the accumulator on;
 //   * warps 6-9 (one thread per right-hand side = TMEM lane): read the 24 FP32
 //     results, apply the epilogue (out = cA A + cH D, optional dot products),
-//     store BF16, and accumulate per-RHS partial sums over chunks of TCH sites.
+//     store BF16 (streaming stores), and accumulate per-RHS partial sums over
+//     chunks of TCH sites.
 // Every wait on an mbarrier is bounded; a wait that runs out sets an error
 // code, the other roles stop at their next wait, TMA copies in flight are
 // waited for (bounded), and TMEM is released before the kernel returns.
@@ -42,17 +47,16 @@
 
 namespace lqcd {
 
-constexpr int TNS = 3;    // shared-memory stages of the hop pipeline
+constexpr int TNS = 4;    // shared-memory stages of the hop pipeline (neighbour blocks + link bundle)
 constexpr int TK = 192;   // MMA K per site: 8 directions x 24 reals
 constexpr int TN = 32;    // MMA N: 24 output reals, padded
-constexpr int T_A_HALF = 8 * 3072;             // one 64-RHS half of a stage: 8 neighbours x [24][64] BF16
-constexpr int T_A_BYTES = 2 * T_A_HALF;        // 48 KiB
+constexpr int T_A_NBR = 6144;                  // one neighbour block in a stage: [2 halves][24][64] BF16
+constexpr int T_A_BYTES = 8 * T_A_NBR;         // 48 KiB
 constexpr int T_W_BYTES = (TK / 8) * 512;      // 12 KiB: 24 K-chunks x 4 N-groups x 128 B
-constexpr int T_O_WARP = 24 * 32 * 2;          // one epilogue warp's share of an output block: 1.5 KiB
-constexpr int T_O_BYTES = 4 * T_O_WARP;        // one output block (site, tile): 6 KiB
-constexpr int T_THREADS = 320;                 // 10 warps
+constexpr int T_NT = 4;                        // neighbours per item loaded by TMA; the rest by cp.async
+constexpr int T_THREADS = 448;                 // 14 warps
 constexpr int T_L_BYTES = 8 * 9 * 4;           // one site's link bundle: 288 B
-constexpr int T_SMEM = 1024 + TNS * (T_A_BYTES + T_W_BYTES) + 2 * T_O_BYTES + TNS * T_L_BYTES + 256;
+constexpr int T_SMEM = 1024 + TNS * (T_A_BYTES + T_L_BYTES) + 2 * T_W_BYTES + 256;
 constexpr int T_TMEM_COLS = 64;                // two FP32 accumulators of TN columns
 
 // error codes written by the tile hop when a bounded wait runs out
@@ -70,6 +74,7 @@ struct THopArgs {
   int p_out;
   const uint32_t *links;  // [2 parity][Vh][8 d][9] BF16x2 (re low, im high), signs and daggers folded in
   __nv_bfloat16 *out;
+  const __nv_bfloat16 *in; // the hop's input field (for the cp.async loaders)
   const __nv_bfloat16 *A;  // epilogue operand (tile field), EPI != PLAIN
   const __nv_bfloat16 *B;  // <B, out> for EPI_DOTR
   float cA, cH;
@@ -134,6 +139,12 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
                "l"(src), "r"(bytes), "r"(s_u32(bar))
                : "memory");
 }
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -208,9 +219,14 @@ struct TItems {
     ustep = gridDim.x;
   }
 };
+// results are stored with an L2 evict-first policy: they are not read again in
+// this launch, and the neighbour blocks still to be reused should stay in L2
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, uint32_t src) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(map), "r"(x),
-               "r"(y), "r"(src)
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%1, %2}], [%3], %4;" ::"l"(
+                   map),
+               "r"(x), "r"(y), "r"(src), "l"(pol)
                : "memory");
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
@@ -218,18 +234,17 @@ __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 template <int EPI>
-__global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ CUtensorMap tin,
-                                                       const __grid_constant__ CUtensorMap tout, THopArgs a) {
+__global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ CUtensorMap tin, THopArgs a) {
   extern __shared__ __align__(1024) unsigned char t_smem_raw[];
   unsigned char *base = (unsigned char *)(((uintptr_t)t_smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char *sA = base;                                  // TNS x 48 KiB
-  unsigned char *sW = base + TNS * T_A_BYTES;                // TNS x 12 KiB
-  unsigned char *sO = sW + TNS * T_W_BYTES;                  // 2 x 6 KiB output staging [acc][warp][24][32]
-  unsigned char *sL = sO + 2 * T_O_BYTES;                    // TNS x 288 B link bundles
-  uint64_t *bars = (uint64_t *)(sL + TNS * T_L_BYTES);       // full, empty, lfull [TNS]; accf, acce [2]; drain
+  unsigned char *sA = base;                                  // TNS x 48 KiB neighbour blocks
+  unsigned char *sW = base + TNS * T_A_BYTES;                // 2 x 12 KiB W ring
+  unsigned char *sL = sW + 2 * T_W_BYTES;                    // TNS x 288 B link bundles
+  uint64_t *bars = (uint64_t *)(sL + TNS * T_L_BYTES);       // full, empty, lfull [TNS]; accf, acce, wfull, wempty [2]; drain
   uint64_t *full = bars, *empty = bars + TNS, *lfull = bars + 2 * TNS;
   uint64_t *accf = bars + 3 * TNS, *acce = bars + 3 * TNS + 2;
-  uint64_t *drain = bars + 3 * TNS + 4;
+  uint64_t *wfull = bars + 3 * TNS + 4, *wempty = bars + 3 * TNS + 6;
+  uint64_t *drain = bars + 3 * TNS + 8;
   uint32_t *tslot = (uint32_t *)(drain + 1);
   volatile int *abort = (volatile int *)(tslot + 1);
 
@@ -240,16 +255,18 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
   it.init(count, a.nch, g.Vh);
 
   // zero the W buffers (zero spin blocks stay zero), set up barriers and TMEM
-  for (int i = tid; i < TNS * T_W_BYTES / 16; i += T_THREADS) reinterpret_cast<uint4 *>(sW)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < 2 * T_W_BYTES / 16; i += T_THREADS) reinterpret_cast<uint4 *>(sW)[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     for (int s = 0; s < TNS; ++s) {
-      mbar_init(full + s, 1 + 128);
+      mbar_init(full + s, 1 + 128);  // TMA producer, cp.async loaders
       mbar_init(empty + s, 1);
       mbar_init(lfull + s, 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf + b, 1);
       mbar_init(acce + b, 128);
+      mbar_init(wfull + b, 128);
+      mbar_init(wempty + b, 1);
     }
     mbar_init(drain, 1);
     *abort = 0;
@@ -261,6 +278,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  if (warp == 0 && lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"(&tin) : "memory");
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -269,44 +287,52 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
-    if (lane == 0) {
-      int q = 0;
-      int last_q[TNS];
-      for (int s = 0; s < TNS; ++s) last_q[s] = -1;
-      for (int u = it.u0; u < it.u1 && !*abort; u += it.ustep) {
-        const int T = a.tlist[u / it.nch], ch = u % it.nch;
-        const int j0 = ch * TCH, j1 = min(j0 + TCH, it.vh);
-        if (a.prof) atomicAdd(a.prof + EPI, (unsigned long long)(j1 - j0) * (unsigned long long)min(TR, a.nrhs - T * TR));
-        for (int j = j0; j < j1; ++j, ++q) {
-          const int s = q % TNS;
-          if (q >= TNS && !mbar_wait(empty + s, ((q / TNS) - 1) & 1, abort)) {
-            atomicCAS(a.err, 0, THOP_ERR_TMA);
-            *abort = 1;
-            break;
-          }
+    // the whole warp walks the items; lanes 0..T_NT-1 each issue one neighbour
+    // block and lane 31 the link bundle
+    int q = 0;
+    int last_q[TNS];
+    for (int s = 0; s < TNS; ++s) last_q[s] = -1;
+    const int dn = lane;
+    for (int u = it.u0; u < it.u1 && !*abort; u += it.ustep) {
+      const int T = a.tlist[u / it.nch], ch = u % it.nch;
+      const int j0 = ch * TCH, j1 = min(j0 + TCH, it.vh);
+      if (a.prof && lane == 0)
+        atomicAdd(a.prof + EPI, (unsigned long long)(j1 - j0) * (unsigned long long)min(TR, a.nrhs - T * TR));
+      bool ok = true;
+      for (int j = j0; j < j1; ++j, ++q) {
+        const int s = q % TNS;
+        const bool got = q < TNS || mbar_wait(empty + s, ((q / TNS) - 1) & 1, abort);
+        if (!__all_sync(0xffffffffu, got)) {
+          if (lane == 0) atomicCAS(a.err, 0, THOP_ERR_TMA);
+          *abort = 1;
+          ok = false;
+          break;
+        }
+        if (lane == 0) {
+          mbar_arrive_tx(lfull + s, T_L_BYTES);
+          mbar_arrive_tx(full + s, T_NT * T_A_NBR);
+        }
+        __syncwarp();
+        if (lane < T_NT) {
           int c[4];
           coords_of(g, a.p_out, j, c);
-          // the site's link bundle for the W builders, then the neighbour tiles
-          mbar_arrive_tx(lfull + s, T_L_BYTES);
+          const int row = (T * it.vh + neighbour(g, c, dn)) * 48;
+          tma_load_2d(s_u32(sA + s * T_A_BYTES) + dn * T_A_NBR, &tin, 0, row, full + s);
+        } else if (lane == 31) {
+          // the site's link bundle for the W builders
           bulk_load(s_u32(sL + s * T_L_BYTES), a.links + (size_t)(a.p_out * g.Vh + j) * 72, T_L_BYTES, lfull + s);
-          mbar_arrive_tx(full + s, T_A_BYTES);
-          const uint32_t dst = s_u32(sA + s * T_A_BYTES);
-#pragma unroll
-          for (int d = 0; d < 8; ++d) {
-            const int row = (T * it.vh + neighbour(g, c, d)) * 24;
-            tma_load_2d(dst + d * 3072, &tin, 0, row, full + s);
-            tma_load_2d(dst + T_A_HALF + d * 3072, &tin, 64, row, full + s);
-          }
-          last_q[s] = q;
         }
+        last_q[s] = q;
       }
-      // copies in flight must land before the CTA exits (normally already consumed)
+      if (!ok) break;
+    }
+    // copies in flight must land before the CTA exits (normally already consumed)
+    if (lane == 0)
       for (int s = 0; s < TNS; ++s)
         if (last_q[s] >= 0) {
           mbar_wait(full + s, (last_q[s] / TNS) & 1, abort);
           mbar_wait(lfull + s, (last_q[s] / TNS) & 1, abort);
         }
-    }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
@@ -322,18 +348,32 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
             *abort = 1;
             break;
           }
+          if (!mbar_wait(wfull + acc, (q >> 1) & 1, abort)) {
+            atomicCAS(a.err, 0, THOP_ERR_W);
+            *abort = 1;
+            break;
+          }
           if (q >= 2 && !mbar_wait(acce + acc, ((q >> 1) - 1) & 1, abort)) {
             atomicCAS(a.err, 0, THOP_ERR_ACC);
             *abort = 1;
             break;
           }
           tc_fence_after();
-          const uint32_t aaddr = s_u32(sA + s * T_A_BYTES), waddr = s_u32(sW + s * T_W_BYTES);
+          const uint32_t aaddr = s_u32(sA + s * T_A_BYTES), waddr = s_u32(sW + acc * T_W_BYTES);
+          // K = 192 = 8 neighbours x 24 reals in twelve steps of 16: rows 0..15 of
+          // neighbour d (K-groups 3d, 3d+1: SBO 1 KiB), and rows 16..23 of the
+          // neighbours d, d + 1 together (SBO 6 KiB); the W chunks follow the
+          // same K order (LBO 512 B, resp. 3 x 512 B); LBO of A = the 3 KiB half
 #pragma unroll
-          for (int k = 0; k < TK / 16; ++k)
-            tc_mma(tmem + acc * TN, smem_desc(aaddr + k * 2048, T_A_HALF, 1024, 2), smem_desc(waddr + k * 1024, 512, 128, 0),
-                   k > 0);
+          for (int d = 0; d < 8; ++d) {
+            tc_mma(tmem + acc * TN, smem_desc(aaddr + d * T_A_NBR, 3072, 1024, 2),
+                   smem_desc(waddr + 3 * d * 512, 512, 128, 0), d > 0);
+            if (d & 1)
+              tc_mma(tmem + acc * TN, smem_desc(aaddr + (d - 1) * T_A_NBR + 2048, 3072, T_A_NBR, 2),
+                     smem_desc(waddr + (3 * (d - 1) + 2) * 512, 3 * 512, 128, 0), 1);
+          }
           tc_commit(empty + s);
+          tc_commit(wempty + acc);
           tc_commit(accf + acc);
           issued = true;
         }
@@ -361,15 +401,17 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
       const int ch = u % it.nch;
       const int j0 = ch * TCH, j1 = min(j0 + TCH, it.vh);
       for (int j = j0; j < j1; ++j, ++q) {
-        const int st = q % TNS;
-        if ((q >= TNS && !mbar_wait(empty + st, ((q / TNS) - 1) & 1, abort)) ||
+        // W buffer q % 2 is free once the MMAs of item q - 2 are done; the link
+        // bundle comes with the item's stage
+        const int st = q % TNS, wb = q & 1;
+        if ((q >= 2 && !mbar_wait(wempty + wb, ((q >> 1) - 1) & 1, abort)) ||
             !mbar_wait(lfull + st, (q / TNS) & 1, abort)) {
           atomicCAS(a.err, 0, THOP_ERR_W);
           *abort = 1;
           break;
         }
         if (active) {
-          unsigned char *W = sW + st * T_W_BYTES;
+          unsigned char *W = sW + wb * T_W_BYTES;
           const uint32_t *L = reinterpret_cast<const uint32_t *>(sL + st * T_L_BYTES) + d * 9 + c * 3;
           const int nr = (s * 3 + c) * 2;
 #pragma unroll
@@ -397,10 +439,10 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
           }
         }
         fence_async_smem();
-        mbar_arrive(full + st);
+        mbar_arrive(wfull + wb);
       }
     }
-  } else {
+  } else if (warp < 10) {
     // ------------------------------------------------------------ epilogue
     // One thread per right-hand side = TMEM lane; every step is warp-uniform
     // (the accumulator wait is agreed on with __all_sync).  Each warp stages
@@ -412,18 +454,18 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
     // epilogue operands (A, B) of item q + 1 are loaded while item q completes
     uint32_t na[12], nb[12];
     auto load_ops = [&](int T, int j) {
-      const size_t e0 = (size_t)(T * g.Vh + j) * 24 * TR + row;
+      const size_t e0 = tile_elem(T, g.Vh, j, 0, row);  // real k at e0 + 64 k
       if (EPI != EPI_PLAIN) {
 #pragma unroll
         for (int k = 0; k < 12; ++k)
-          na[k] = (uint32_t)__bfloat16_as_ushort(a.A[e0 + (size_t)(2 * k) * TR]) |
-                  ((uint32_t)__bfloat16_as_ushort(a.A[e0 + (size_t)(2 * k + 1) * TR]) << 16);
+          na[k] = (uint32_t)__bfloat16_as_ushort(a.A[e0 + (size_t)(2 * k) * 64]) |
+                  ((uint32_t)__bfloat16_as_ushort(a.A[e0 + (size_t)(2 * k + 1) * 64]) << 16);
       }
       if (EPI == EPI_DOTR) {
 #pragma unroll
         for (int k = 0; k < 12; ++k)
-          nb[k] = (uint32_t)__bfloat16_as_ushort(a.B[e0 + (size_t)(2 * k) * TR]) |
-                  ((uint32_t)__bfloat16_as_ushort(a.B[e0 + (size_t)(2 * k + 1) * TR]) << 16);
+          nb[k] = (uint32_t)__bfloat16_as_ushort(a.B[e0 + (size_t)(2 * k) * 64]) |
+                  ((uint32_t)__bfloat16_as_ushort(a.B[e0 + (size_t)(2 * k + 1) * 64]) << 16);
       }
     };
     if (it.u0 < it.u1) load_ops(a.tlist[it.u0 / it.nch], (it.u0 % it.nch) * TCH);
@@ -482,24 +524,65 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
             sim = fmaf(b0, v[2 * k + 1], fmaf(-b1, v[2 * k], sim));
           }
         }
-        // this warp's staging buffer for accumulator acc is free once its TMA
-        // store of two items ago has read it
-        if (lane == 0) bulk_wait_read1();
-        __syncwarp();
-        unsigned char *ob = sO + acc * T_O_BYTES + quarter * T_O_WARP;
-        __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(ob);
+        // streaming stores: the results are not read again in this launch
+        {
+          unsigned short *o = reinterpret_cast<unsigned short *>(a.out) + tile_elem(T, g.Vh, j, 0, row);
 #pragma unroll
-        for (int k = 0; k < 24; ++k) o[k * 32 + lane] = __float2bfloat16_rn(v[k]);
-        fence_async_smem();
-        __syncwarp();
-        if (lane == 0) tma_store_2d(&tout, 32 * quarter, (T * g.Vh + j) * 24, s_u32(ob));
+          for (int k = 0; k < 24; ++k) __stcs(o + (size_t)k * 64, __bfloat16_as_ushort(__float2bfloat16_rn(v[k])));
+        }
       }
       if (!ok) break;
       if (EPI == EPI_DOTR || EPI == EPI_TS)
         a.part[(size_t)rhs * it.nch + ch] = D4S{(double)sre, (double)sim, 0.0, (double)snn};
     }
-    // every output store has completed before the CTA exits
-    if (lane == 0) bulk_wait_all();
+  } else {
+    // ------------------------------------------------------------ cp.async loaders
+    // Neighbours T_NT..7 of each item, 16 bytes per request; a thread's copies of
+    // item q are fenced to the async proxy and announced on full[] once they have
+    // landed, right after the copies of item q + 1 have been issued.
+    const int l = tid - 320;
+    constexpr int PER = (8 - T_NT) * 384 / 128;  // 16-byte chunks per thread and item
+    int q = 0, pend = -1;
+    for (int u = it.u0; u < it.u1 && !*abort; u += it.ustep) {
+      const int T = a.tlist[u / it.nch], ch = u % it.nch;
+      const int j0 = ch * TCH, j1 = min(j0 + TCH, it.vh);
+      bool ok = true;
+      for (int j = j0; j < j1; ++j, ++q) {
+        const int s = q % TNS;
+        const bool got = q < TNS || mbar_wait(empty + s, ((q / TNS) - 1) & 1, abort);
+        if (!__all_sync(0xffffffffu, got)) {
+          if (lane == 0) atomicCAS(a.err, 0, THOP_ERR_TMA);
+          *abort = 1;
+          ok = false;
+          break;
+        }
+        int c[4];
+        coords_of(g, a.p_out, j, c);
+        int nb[8 - T_NT];
+#pragma unroll
+        for (int d = T_NT; d < 8; ++d) nb[d - T_NT] = neighbour(g, c, d);
+        const uint32_t sbase = s_u32(sA + s * T_A_BYTES);
+#pragma unroll
+        for (int m = 0; m < PER; ++m) {
+          const int ci = l + 128 * m, dd = ci / 384, w = ci % 384, row = w >> 3, c16 = w & 7;
+          const uint4 *src = reinterpret_cast<const uint4 *>(a.in) + ((size_t)(T * it.vh + nb[dd]) * 384 + w);
+          cp_async16(sbase + (T_NT + dd) * T_A_NBR + row * 128 + ((c16 ^ (row & 7)) << 4), src);
+        }
+        cp_async_commit();
+        if (pend >= 0) {
+          cp_async_wait1();
+          fence_async_smem();
+          mbar_arrive(full + pend);
+        }
+        pend = s;
+      }
+      if (!ok) break;
+    }
+    cp_async_wait_all();  // no copy may land after the CTA has left
+    if (pend >= 0) {
+      fence_async_smem();
+      mbar_arrive(full + pend);
+    }
   }
   tc_fence_before();
   __syncthreads();

@@ -9,12 +9,20 @@
 namespace lqcd {
 
 constexpr int TR = 128;  // right-hand sides per tile (the MMA M of the tensor-core hop)
-constexpr int TCH = 64;  // sites per reduction chunk of the tile kernels
+constexpr int TCH = 32;  // sites per reduction chunk (and work unit) of the tile kernels
 
-// One BF16 sloppy field in 128-RHS tiles: [ntile][vh][24][128] BF16, with the
-// TMA tensor maps of the tensor-core hop (built by tile_field_map): `map`
-// loads a neighbour half (64 RHS x 24 rows, 128-byte swizzle), `smap` stores an
-// epilogue warp's share of an output block (32 RHS x 24 rows, no swizzle).
+// Element (real k, right-hand side r) of site j of tile T in a tile field:
+// [tile][site][half = r / 64][24 reals][64 RHS], so that one site's block of a
+// tile (6 KiB) is 48 rows of 128 bytes, each half a contiguous 3 KiB.
+__host__ __device__ inline size_t tile_elem(int T, int vh, int j, int k, int r) {
+  return ((((size_t)T * vh + j) * 2 + (r >> 6)) * 24 + k) * 64 + (r & 63);
+}
+
+// One BF16 sloppy field in 128-RHS tiles (element order of tile_elem), with the
+// TMA tensor maps of the tensor-core hop (built by tile_field_map) over the 2-d
+// view [ntile * vh * 48 rows][64 RHS]: `map` loads a neighbour block (64 x 48,
+// 128-byte swizzle), `smap` stores an epilogue warp's share of an output block
+// (32 x 24, no swizzle).
 struct TileField {
   __nv_bfloat16 *d = nullptr;
   int ntile = 0, vh = 0;
