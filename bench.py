@@ -332,7 +332,7 @@ def config_runs(L, h, dev, stream):
 
 
 # --------------------------------------------- the paper's exact-loop configuration
-def _cfg0_oracle_worker(args):
+def _exact_loops_oracle_worker(args):
     """Oracle FP64 even-odd BiCGstab on a chunk of the 4^4 point sources (timed)."""
     sites, = args
     import numpy as np
@@ -352,7 +352,7 @@ def _cfg0_oracle_worker(args):
     return time.perf_counter() - t0, len(src)
 
 
-def cfg0_run(L, dev, with_oracle):
+def exact_loops_4444_run(L, dev, with_oracle):
     """All 3072 point-source FP64 solves on 4^4 (Haar seed 0, kappa = 0.125) and the
     exact loops per site and per time slice: the batched FP64 solver, the plain
     single-RHS FP64 solver, and the oracle on the host cores (all 3072 sources)."""
@@ -395,7 +395,7 @@ def cfg0_run(L, dev, with_oracle):
         chunks = [list(range(V))[k::nw] for k in range(nw)]
         t0 = time.perf_counter()
         with mp.get_context("spawn").Pool(nw) as pool:
-            res = pool.map(_cfg0_oracle_worker, [(c,) for c in chunks])
+            res = pool.map(_exact_loops_oracle_worker, [(c,) for c in chunks])
         wall = time.perf_counter() - t0
         busy = max(r[0] for r in res)
         out["oracle"] = {"solves_per_s": 3072 / busy, "cores": nw, "max_worker_s": busy, "wall_s": wall,
@@ -616,7 +616,7 @@ def run_ours(args, rank, world, local_rank):
     fp64_rate = n64 / (time.perf_counter() - t0)
     extras = next_rows(L, h, per_site, dev, stream, not args.no_cpu, nrhs)
     configs = config_runs(L, h, dev, stream)
-    configs["cfg0_exact_4444"] = cfg0_run(L, dev, not args.no_cpu)
+    configs["exact_loops_4x4x4x4"] = exact_loops_4444_run(L, dev, not args.no_cpu)
     gpu_piece_loops = None
     if not args.no_cpu:  # the same pieces the oracle baseline solves, for the loop error
         pcs = oracle_pieces(args.cpu_rhs)

@@ -12,7 +12,7 @@
  * --------------------------------
  *  - dims = (Lx, Ly, Lz, Lt), all even, Lx >= 2.  V = Lx*Ly*Lz*Lt.
  *    Site index s = x + Lx*(y + Ly*(z + Lz*t)); parity (x+y+z+t) mod 2.
- *  - Wilson-Dirac operator (the "Wilson Dirac operator M" of Sec. III):
+ *  - Wilson-Dirac operator (the operator M of the stopping rule in Sec. III):
  *      D psi(x) = psi(x) - kappa sum_mu [ (1-gamma_mu) U_mu(x) psi(x+mu)
  *                                       + (1+gamma_mu) U_mu(x-mu)^+ psi(x-mu) ]
  *    periodic in space, every hop across t = Lt-1 <-> 0 multiplied by -1.
@@ -186,15 +186,20 @@ int lqcd_batch_run(lqcd_batch *batch, const lqcd_solver_params *params, lqcd_sol
 int lqcd_batch_rhs(const lqcd_batch *batch, int *total);
 int lqcd_batch_destroy(lqcd_batch *batch);
 
-/* Autotuner: time the reduced-precision hopping term for nrhs right-hand
- * sides of `precision` on this context over its compiled variants (register
- * budget, pairs per block, FP32-unit or tensor-core SU(3) products) and the
- * candidate launch grids (2, 4, 8, 16 blocks per SM), and keep the fastest for
- * later solves of that (nrhs, precision).  *best_blocks_per_sm and
- * *best_hop_variant (host, each may be NULL) receive the choice.  Needs a
- * gauge field.  Synchronises the device.  With LQCD_AUTOTUNE_VERBOSE set in the
- * environment every timing is printed to stderr; LQCD_HOP_VARIANT=<digit>
- * overrides the variant the solves use (for tests and profiling). */
+/* Autotuner: for nrhs right-hand sides of `precision` on this context, time
+ * complete inner iterations of the mixed solver (the four hopping-term launches
+ * with their epilogues and the Krylov updates of the layout) for every
+ * compiled variant -- the RHS-pair layout with its hop variants (register
+ * budget, pairs per block, FP32-unit or mma.sync SU(3) products) on launch
+ * grids of 2, 4, 8 and 16 blocks per SM, and, for BF16, the 128-RHS tile
+ * layout with the tensor-core (tcgen05) hop -- and keep the fastest for later
+ * solves of that (nrhs, precision).  *best_blocks_per_sm and *best_hop_variant
+ * (host, each may be NULL) receive the choice.  Needs a gauge field.
+ * Synchronises the device.  With LQCD_AUTOTUNE_VERBOSE set in the environment
+ * every timing is printed to stderr; LQCD_HOP_VARIANT=<digit> overrides the
+ * variant the solves use (for tests and profiling); LQCD_NO_GRAPH makes the
+ * solver launch its inner iterations directly instead of through CUDA graphs
+ * (kernel profilers do not see kernels inside graphs with conditional nodes). */
 int lqcd_autotune(lqcd_ctx *ctx, int nrhs, int precision, int *best_blocks_per_sm, int *best_hop_variant);
 
 /* Point sources e_{x,spin,colour} (Sec. II: exact all-to-all propagator from

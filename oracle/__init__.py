@@ -9,8 +9,8 @@ method's arithmetic).
 
 What it computes (arXiv:1108.2473):
 
-* ``dirac``    -- the Wilson-Dirac operator D = 1 - kappa*H (the "Wilson Dirac
-  operator M" of Sec. III; explicit form fixed by the problem statement),
+* ``dirac``    -- the Wilson-Dirac operator D = 1 - kappa*H (the operator M of
+  the stopping rule in Sec. III, in the standard Wilson form),
   gamma matrices, even-odd blocks, plaquette.
 * ``solver``   -- BiCGstab (van der Vorst) on the even-odd Schur complement,
   stopped on the true relative residual |M x - b| / |b| of Sec. III.

@@ -5,7 +5,7 @@ a 4x4 spin factor per link and direction), independently of the array
 stencil in ``dirac.hop``.  Index of (site, spin, colour) = 12*site + 3*spin +
 colour with site = x + Lx*(y + Ly*(z + Lz*t)).
 
-Used as the dense reference the problem statement asks for: numpy.linalg
+Used as the dense reference: numpy.linalg
 inversion / LU of this matrix gives G exactly (to rounding).
 """
 from __future__ import annotations

@@ -1,7 +1,7 @@
 """Wilson-Dirac operator on a 4-d periodic lattice, antiperiodic in time (FP64).
 
-Conventions (the paper names only "the Wilson Dirac operator M", Sec. III;
-the explicit operator is the standard Wilson form stated in the problem):
+Conventions (Sec. III names the Wilson-Dirac operator M but does not write it out;
+the explicit operator is the standard Wilson form):
 
   (D psi)(x) = psi(x) - kappa * sum_mu [ (1 - gamma_mu) U_mu(x) psi(x + mu)
                                         + (1 + gamma_mu) U_mu(x - mu)^+ psi(x - mu) ]

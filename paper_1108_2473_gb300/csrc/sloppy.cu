@@ -1780,6 +1780,7 @@ struct MixedRun : RunIface {
   int cycle = 0;
   const int max_cycles = 10;
   bool timed_out = false;
+  int force_code = -1;  // launch code (blocks per SM * 10 + hop variant) chosen by the autotuner while it times
   unsigned long long budget_ns = ~0ull;  // host copy of the value sent to the device (pinned lifetime: the run)
 
   MixedRun(lqcd_ctx *c, const double2 *b_, double2 *x_, int n, const lqcd_solver_params &p_, lqcd_solve_stats *s_,
@@ -1800,7 +1801,7 @@ struct MixedRun : RunIface {
     nb = Ops::nb(vh);
     kappa = (float)ctx->kappa;
     k2 = (float)(ctx->kappa * ctx->kappa);
-    const int code = tuned_code(ctx, nrhs, p.precision);
+    const int code = force_code >= 0 ? force_code : tuned_code(ctx, nrhs, p.precision);
     hop_variant = code % 10;
     // tile path: the element-wise kernels use eight 256-thread blocks per SM
     G = num_sms(ctx->device) * (Ops::GS == TR ? 8 : code / 10);
@@ -1832,6 +1833,43 @@ struct MixedRun : RunIface {
 
   // the FP64 solution from the double-float iterate
   int finish() override { return df_join(ctx, ss->xdf, x, (size_t)nrhs * g.V * 12, st); }
+
+  // Autotuning: ms per inner iteration of this layout and launch code, with every
+  // right-hand side kept active (zero fields; a target below zero keeps them
+  // from converging and from requesting reliable updates).  *herr: tile-hop error.
+  float time_iterations(int reps, int *herr) {
+    for (int k = 0; k < cap; ++k) {
+      SState z{};
+      z.rho = make_double2(1.0, 0.0);
+      z.alpha = z.omega = make_double2(1.0, 0.0);
+      z.target2 = -1.0;
+      hs[k] = z;
+      hflags[k] = k < nrhs ? FLAG_ACTIVE : 0;
+    }
+    const size_t sloppy_bytes = (size_t)7 * (cap / 2) * 6 * vh * sizeof(uint4);
+    if (cudaMemsetAsync(ss->sd, 0, sloppy_bytes, st) != cudaSuccess ||
+        cudaMemsetAsync(ss->f32, 0, (size_t)5 * cap * 6 * vh * sizeof(float4), st) != cudaSuccess ||
+        cudaMemcpyAsync(sb.sc, hs.data(), cap * sizeof(SState), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(sb.flags, hflags.data(), cap * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return -1.f;
+    KL k_build_lists<<<1, 1024, 0, st>>>(nrhs, sb.flags, Ops::GS, sb.act_pairs, sb.ru_list, sb.ru_pairs, sb.counts);
+    launch_iters(st, 1);  // warm-up
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, st);
+    launch_iters(st, reps);
+    cudaEventRecord(e1, st);
+    float ms = -1.f;
+    if (cudaEventSynchronize(e1) == cudaSuccess) {
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaMemcpy(herr, sb.counts + 8, sizeof(int), cudaMemcpyDeviceToHost);
+    return ms;
+  }
 
   // key of the captured iteration graph: everything its kernels capture by value
   std::vector<double> graph_key() const override {
@@ -2111,7 +2149,8 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
   if (rc) return rc;
   SloppyState *ss = ctx->sloppy;
   // the legacy default stream cannot be captured: launch directly there
-  const bool use_graph = !ctx->prof_on && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+  const bool use_graph = !ctx->prof_on && st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread &&
+                         getenv("LQCD_NO_GRAPH") == nullptr;
   while (!run->done) {
     if (!run->inner) {
       rc = run->cycle_start();
@@ -2170,6 +2209,7 @@ static int mixed_batch(std::vector<lqcd_ctx *> &ctxs, std::vector<const double2 
     if (rc) return rc;
   }
   std::vector<long long> per_iter(nl, 0);
+  const bool direct = getenv("LQCD_NO_GRAPH") != nullptr;  // launches visible to kernel profilers
   for (;;) {
     bool any = false;
     for (auto &r : runs) {
@@ -2180,6 +2220,21 @@ static int mixed_batch(std::vector<lqcd_ctx *> &ctxs, std::vector<const double2 
       any = any || !r->done;
     }
     if (!any) break;
+    if (direct) {
+      for (auto &r : runs)
+        if (!r->done) {
+          r->launch_iters(st, ITERS_PER_POLL);
+          int rc = r->request_count(st);
+          if (rc) return rc;
+        }
+      LQCD_CUDA_TRY(ctxs[0], cudaStreamSynchronize(st));
+      for (auto &r : runs)
+        if (!r->done && r->inner) {
+          int rc = r->poll();
+          if (rc) return rc;
+        }
+      continue;
+    }
     std::vector<double> key;
     for (auto &r : runs) {
       std::vector<double> k = r->graph_key();
@@ -2383,98 +2438,62 @@ int lqcd_batch_run(lqcd_batch *batch, const lqcd_solver_params *params, lqcd_sol
 // ================================================================ autotuner
 namespace lqcd {
 
-// one hop timing: reps launches after two warm-up launches, ms per launch
-template <class F>
-static float time_hop(F launch, cudaEvent_t e0, cudaEvent_t e1, int reps, cudaError_t *err) {
-  for (int rep = 0; rep < 2; ++rep) launch();
-  cudaEventRecord(e0);
-  for (int rep = 0; rep < reps; ++rep) launch();
-  cudaEventRecord(e1);
-  *err = cudaEventSynchronize(e1);
-  float ms = 0.f;
-  cudaEventElapsedTime(&ms, e0, e1);
-  return ms / reps;
+// Autotuner: every candidate layout and launch code is timed on what the solver
+// runs -- inner BiCGstab iterations (the four hop launches with their epilogues,
+// the layout's Krylov updates, finalisers and list builds) -- on the context's
+// gauge field with nrhs right-hand sides, so that a faster hopping term that
+// brings slower updates is not chosen.
+template <class Ops>
+static int time_code(lqcd_ctx *ctx, int nrhs, int precision, int code, float *ms_out) {
+  lqcd_solver_params p{};
+  p.tol = 1e-10;
+  p.max_iter = 1 << 30;
+  p.precision = precision;
+  p.delta = 0.05;
+  std::vector<lqcd_solve_stats> stats(nrhs);
+  MixedRun<Ops> run(ctx, nullptr, nullptr, nrhs, p, stats.data(), (cudaStream_t)0, wall_ms());
+  run.force_code = code;
+  int rc = run.init();
+  if (rc) return rc;
+  int herr = 0;
+  *ms_out = run.time_iterations(3, &herr);
+  if (*ms_out < 0.f) return cuda_error(ctx, cudaGetLastError(), "lqcd_autotune: timing");
+  if (herr) *ms_out = 1e30f;  // a tile hop that reported a wait that ran out is never chosen
+  return LQCD_OK;
 }
 
 template <class SP>
 static int autotune_hop(lqcd_ctx *ctx, int nrhs, int precision, int *best, int *best_variant) {
-  const Geom &g = ctx->geom;
-  const int vh = g.Vh, npairs = (nrhs + 1) / 2;
   const bool tiles = std::is_same<SP, BF16P>::value;
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  // one allocation serves both layouts (a capacity in whole tiles is also whole pairs)
+  int rc = sloppy_alloc(ctx, nrhs, tiles ? TR : 2);
+  if (rc) return rc;
   const int cand[4] = {2, 4, 8, 16};
   const bool verbose = getenv("LQCD_AUTOTUNE_VERBOSE") != nullptr;  // timings to stderr
   float best_ms = 1e30f;
   int best_code = 80;
-  const int nsm = num_sms(ctx->device);
-  cudaError_t err = cudaSuccess;
-  // pair layout: variants 0-4 x launch grids (zero data: timing does not depend on the values)
-  int rc = sloppy_alloc(ctx, nrhs, 2);
-  if (rc) return rc;
-  SloppyState *ss = ctx->sloppy;
-  const int nbx = (vh + ST - 1) / ST;
-  {
-    SmallBufs sb = small_layout(ss->small, ss->cap, part_blocks(vh));
-    SP in = pair_field<SP>(ss, 2, vh), out = pair_field<SP>(ss, 6, vh);
-    LQCD_CUDA_TRY(ctx, cudaMemset(ss->sd, 0, 7 * (size_t)(ss->cap / 2) * 6 * vh * sizeof(uint4)));
-    LQCD_CUDA_TRY(ctx, cudaMemset(ss->sn, 0, 7 * (size_t)(ss->cap / 2) * vh * sizeof(float2)));
-    std::vector<int> pl(npairs);
-    for (int k = 0; k < npairs; ++k) pl[k] = k;
-    LQCD_CUDA_TRY(ctx, cudaMemcpy(sb.act_pairs, pl.data(), npairs * sizeof(int), cudaMemcpyHostToDevice));
-    LQCD_CUDA_TRY(ctx, cudaMemcpy(sb.counts, &npairs, sizeof(int), cudaMemcpyHostToDevice));
-    for (int variant = 0; variant < TILE_VARIANT; ++variant)
-      for (int c : cand) {
-        const int G = nsm * c;
-        const float ms = time_hop([&]() {
-          launch_hop_pair<SP, EPI_PLAIN>(variant, G, (cudaStream_t)0, ctx, g, 1, in, out, out, out, 0.f, 1.f,
-                                         (const int *)sb.act_pairs, (const int *)sb.counts, (D4S *)nullptr, nbx, nrhs,
-                                         (unsigned long long *)nullptr);
-        }, e0, e1, 5, &err);
-        if (err != cudaSuccess) break;
-        if (verbose)
-          fprintf(stderr, "lqcd_autotune: nrhs %d variant %d blocks/SM %d: %.4f ms per hop\n", nrhs, variant, c, ms);
-        if (ms < best_ms) {
-          best_ms = ms;
-          best_code = c * 10 + variant;
-        }
-      }
-  }
-  // tile layout (BF16): one persistent CTA per SM
-  if (tiles && err == cudaSuccess) {
-    rc = sloppy_alloc(ctx, nrhs, TR);
-    if (rc) return rc;
-    ss = ctx->sloppy;
-    SmallBufs sb = small_layout(ss->small, ss->cap, part_blocks(vh));
-    TileField in, out;
-    rc = TileOps::field(ctx, ss, 2, vh, in);
-    if (!rc) rc = TileOps::field(ctx, ss, 6, vh, out);
-    if (rc) return rc;
-    const int nt = ss->cap / TR;
-    std::vector<int> tl(nt);
-    for (int k = 0; k < nt; ++k) tl[k] = k;
-    LQCD_CUDA_TRY(ctx, cudaMemset(ss->sd, 0, 7 * (size_t)(ss->cap / 2) * 6 * vh * sizeof(uint4)));
-    LQCD_CUDA_TRY(ctx, cudaMemcpy(sb.act_pairs, tl.data(), nt * sizeof(int), cudaMemcpyHostToDevice));
-    LQCD_CUDA_TRY(ctx, cudaMemcpy(sb.counts, &nt, sizeof(int), cudaMemcpyHostToDevice));
-    LQCD_CUDA_TRY(ctx, cudaMemset(sb.counts + 8, 0, sizeof(int)));
-    const float ms = time_hop([&]() {
-      tile_hop(EPI_PLAIN, (cudaStream_t)0, nsm, ctx, 1, in, out, out, out, 0.f, 1.f, sb.act_pairs, sb.counts,
-               nullptr, TileOps::nb(vh), nrhs, nullptr, sb.counts + 8);
-    }, e0, e1, 5, &err);
-    int herr = 0;
-    if (err == cudaSuccess) cudaMemcpy(&herr, sb.counts + 8, sizeof(int), cudaMemcpyDeviceToHost);
+  auto consider = [&](int code, float ms) {
     if (verbose)
-      fprintf(stderr, "lqcd_autotune: nrhs %d variant %d (tiles of %d) 1 block/SM: %.4f ms per hop (error code %d)\n",
-              nrhs, TILE_VARIANT, TR, ms, herr);
-    if (err == cudaSuccess && herr == 0 && ms < best_ms) {
+      fprintf(stderr, "lqcd_autotune: nrhs %d variant %d blocks/SM %d: %.4f ms per inner iteration\n", nrhs,
+              code % 10, code / 10, ms);
+    if (ms < best_ms) {
       best_ms = ms;
-      best_code = 10 + TILE_VARIANT;
+      best_code = code;
     }
+  };
+  for (int variant = 0; variant < TILE_VARIANT; ++variant)
+    for (int c : cand) {
+      float ms = 0.f;
+      rc = time_code<PairOps<SP>>(ctx, nrhs, precision, c * 10 + variant, &ms);
+      if (rc) return rc;
+      consider(c * 10 + variant, ms);
+    }
+  if (tiles) {
+    float ms = 0.f;
+    rc = time_code<TileOps>(ctx, nrhs, precision, 10 + TILE_VARIANT, &ms);
+    if (rc) return rc;
+    consider(10 + TILE_VARIANT, ms);
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (err != cudaSuccess) return cuda_error(ctx, err, "lqcd_autotune");
   long long key = (long long)nrhs * 8 + precision;
   bool found = false;
   for (auto &kv : ctx->tuned)

@@ -53,8 +53,9 @@ constexpr int TN = 32;    // MMA N: 24 output reals, padded
 constexpr int T_A_NBR = 6144;                  // one neighbour block in a stage: [2 halves][24][64] BF16
 constexpr int T_A_BYTES = 8 * T_A_NBR;         // 48 KiB
 constexpr int T_W_BYTES = (TK / 8) * 512;      // 12 KiB: 24 K-chunks x 4 N-groups x 128 B
-constexpr int T_NT = 4;                        // neighbours per item loaded by TMA; the rest by cp.async
-constexpr int T_THREADS = 448;                 // 14 warps
+constexpr int T_NT = 0;                        // neighbours per item loaded by TMA; the rest by cp.async
+constexpr int T_NL = 256;                      // cp.async loader threads (warps 10 ..)
+constexpr int T_THREADS = 320 + T_NL;
 constexpr int T_L_BYTES = 8 * 9 * 4;           // one site's link bundle: 288 B
 constexpr int T_SMEM = 1024 + TNS * (T_A_BYTES + T_L_BYTES) + 2 * T_W_BYTES + 256;
 constexpr int T_TMEM_COLS = 64;                // two FP32 accumulators of TN columns
@@ -258,7 +259,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
   for (int i = tid; i < 2 * T_W_BYTES / 16; i += T_THREADS) reinterpret_cast<uint4 *>(sW)[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
     for (int s = 0; s < TNS; ++s) {
-      mbar_init(full + s, 1 + 128);  // TMA producer, cp.async loaders
+      mbar_init(full + s, 1 + T_NL);  // TMA producer, cp.async loaders
       mbar_init(empty + s, 1);
       mbar_init(lfull + s, 1);
     }
@@ -541,7 +542,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
     // item q are fenced to the async proxy and announced on full[] once they have
     // landed, right after the copies of item q + 1 have been issued.
     const int l = tid - 320;
-    constexpr int PER = (8 - T_NT) * 384 / 128;  // 16-byte chunks per thread and item
+    constexpr int PER = (8 - T_NT) * 384 / T_NL;  // 16-byte chunks per thread and item
     int q = 0, pend = -1;
     for (int u = it.u0; u < it.u1 && !*abort; u += it.ustep) {
       const int T = a.tlist[u / it.nch], ch = u % it.nch;
@@ -564,7 +565,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
         const uint32_t sbase = s_u32(sA + s * T_A_BYTES);
 #pragma unroll
         for (int m = 0; m < PER; ++m) {
-          const int ci = l + 128 * m, dd = ci / 384, w = ci % 384, row = w >> 3, c16 = w & 7;
+          const int ci = l + T_NL * m, dd = ci / 384, w = ci % 384, row = w >> 3, c16 = w & 7;
           const uint4 *src = reinterpret_cast<const uint4 *>(a.in) + ((size_t)(T * it.vh + nb[dd]) * 384 + w);
           cp_async16(sbase + (T_NT + dd) * T_A_NBR + row * 128 + ((c16 ^ (row & 7)) << 4), src);
         }

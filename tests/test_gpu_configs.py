@@ -21,7 +21,7 @@ def eps_field():
 
 
 @pytest.mark.parametrize("prec", ["fp64_plain", "mixed_bf16"])
-def test_cfg1_sampled_oracle_solve_and_statistics(eps_field, prec):
+def test_noise_vs_exact_subblock_16x16x16x32(eps_field, prec):
     """8 t+s+c-diluted vectors (384 pieces each): per-time-slice loops on the
     4x4 spatial sub-block (x, y < 4, z = 0) agree with the exact loops there
     within the spread of the 8 vectors; one diluted piece matches the oracle.
@@ -80,7 +80,7 @@ def test_cfg1_sampled_oracle_solve_and_statistics(eps_field, prec):
     assert rel_err(got, ref[0]) < 1e-8
 
 
-def test_cfg2_tsm_full_size_and_hp_vector_parity(eps_field):
+def test_tsm_full_size_and_hp_vector_parity(eps_field):
     """TSM with 400 LP solves at 1e-3 and 20 HP vectors: convergence as stated,
     and the HP contribution of one vector equals the oracle's."""
     U = eps_field
@@ -107,7 +107,7 @@ def test_cfg2_tsm_full_size_and_hp_vector_parity(eps_field):
     assert rel_err(got, ref) < 1e-8
 
 
-def test_cfg3_uneven_batch_four_lattices():
+def test_uneven_batch_four_lattices_full_size():
     L = require_gpu()
     specs = [((8, 8, 8, 16), "haar", 0.157, 48), ((12, 12, 12, 24), "eps", 0.115, 24),
              ((16, 16, 16, 32), "eps", 0.120, 12), ((24, 24, 24, 48), "haar", 0.157, 6)]
