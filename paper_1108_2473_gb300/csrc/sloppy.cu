@@ -1639,7 +1639,8 @@ template <> BF16P pair_field<BF16P>(SloppyState *st, int f, int vh) {
 //   2: pair layout, two pairs per block (256 threads), the same register cap
 //   3: pair layout, four pairs per block (512 threads), the same register cap
 //   4: pair layout, SU(3) products on the tensor cores (mma.sync, k_hop_mma)
-//   5: RHS-tile layout (BF16 only): TMA-staged neighbour tiles, tcgen05.mma into TMEM (k_thop)
+//   5: RHS-tile layout (BF16 only): neighbour tiles written to TMEM by loader warps, tcgen05.mma
+//      with A from TMEM (k_thop)
 constexpr int HOP_VARIANTS = 6;
 constexpr int TILE_VARIANT = 5;
 
@@ -1699,12 +1700,12 @@ struct TileOps {
   using Field = TileField;
   static constexpr int GS = TR;
   static int nb(int vh) { return (vh + TCH - 1) / TCH; }
-  static int field(lqcd_ctx *ctx, SloppyState *ss, int f, int vh, Field &out) {
+  static int field(lqcd_ctx *, SloppyState *ss, int f, int vh, Field &out) {
     const size_t per = (size_t)ss->cap * vh * 24;  // BF16 values per field
     out.d = reinterpret_cast<__nv_bfloat16 *>(ss->sd) + (size_t)f * per;
     out.ntile = ss->cap / TR;
     out.vh = vh;
-    return tile_field_map(ctx, out);
+    return LQCD_OK;
   }
   static void p(cudaStream_t q, int G, int vh, const SState *sc, const Field &r, const Field &rhat, const Field &pp,
                 const Field &v, const int *gl, const int *gc, int) {
@@ -1727,7 +1728,7 @@ struct TileOps {
   static void hop(int, int, cudaStream_t q, lqcd_ctx *ctx, int p_out, const Field &in, const Field &out,
                   const Field &A, const Field &B, float cA, float cH, const int *gl, const int *gc, D4S *part, int nb,
                   int nrhs, unsigned long long *prof, int *err) {
-    // one persistent CTA per SM (the pipeline holds ~181 KiB of shared memory)
+    // one persistent CTA per SM (it allocates all TMEM columns)
     tile_hop(EPI, q, num_sms(ctx->device), ctx, p_out, in, out, A, B, cA, cH, gl, gc, part, nb, nrhs, prof, err);
   }
 };

@@ -2,8 +2,6 @@
 // BiCGstab for the all-to-all inversions): BF16 sloppy fields in 128-RHS tiles
 // (layout in tile.cuh), the tensor-core hopping term, the element-wise Krylov
 // updates on tiles, and the BF16 link bundle the hop reads.
-#include <cudaTypedefs.h>
-
 #include <algorithm>
 #include <cstring>
 
@@ -82,44 +80,10 @@ static TSpin make_spin_table() {
   return t;
 }
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
-  return fn;
-}
-
-int tile_field_map(lqcd_ctx *ctx, TileField &f) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
-  if (!enc) return set_error(ctx, LQCD_ERR_CUDA, "tile path: cuTensorMapEncodeTiled is unavailable");
-  // 2-d view: [ntile * Vh * 48 rows][64 RHS] BF16, rows of 128 bytes; boxes of
-  // 64 RHS x 48 rows (one neighbour block, both halves), 128-byte swizzle
-  const cuuint64_t dim[2] = {64, (cuuint64_t)f.ntile * f.vh * 48};
-  const cuuint64_t stride[1] = {128};
-  const cuuint32_t box[2] = {64, 48};
-  const cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(&f.map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)f.d, dim, stride, box, estr,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return set_error(ctx, LQCD_ERR_CUDA, "tile path: cuTensorMapEncodeTiled failed (%d)", (int)r);
-  const cuuint32_t sbox[2] = {32, 24};
-  r = enc(&f.smap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)f.d, dim, stride, sbox, estr,
-          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return set_error(ctx, LQCD_ERR_CUDA, "tile path: cuTensorMapEncodeTiled (store) failed (%d)", (int)r);
-  return LQCD_OK;
-}
-
 int tile_hop(int epi, cudaStream_t q, int G, lqcd_ctx *ctx, int p_out, const TileField &in, const TileField &out,
              const TileField &A, const TileField &B, float cA, float cH, const int *tlist, const int *tcount, D4S *part,
              int nch, int nrhs, unsigned long long *prof, int *err) {
-  static bool attr_set[5] = {false, false, false, false, false};
+  if (!in.d || !out.d) return set_error(ctx, LQCD_ERR_INVALID, "tile hop: null field");
   THopArgs a;
   a.g = ctx->geom;
   a.p_out = p_out;
@@ -139,35 +103,33 @@ int tile_hop(int epi, cudaStream_t q, int G, lqcd_ctx *ctx, int p_out, const Til
   a.err = err;
   static const TSpin spin = make_spin_table();
   a.spin = spin;
-  cudaError_t e = cudaSuccess;
-#define THOP_CASE(E)                                                                                 \
-  case E:                                                                                            \
-    if (!attr_set[E]) {                                                                              \
-      e = cudaFuncSetAttribute(k_thop<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM);      \
-      if (e != cudaSuccess) return cuda_error(ctx, e, "tile hop: shared-memory attribute");          \
-      attr_set[E] = true;                                                                            \
-    }                                                                                                \
-    KL k_thop<E><<<G, T_THREADS, T_SMEM, q>>>(in.map, a);                                           \
-    break;
-  switch (epi) {
-    THOP_CASE(EPI_PLAIN)
-    THOP_CASE(EPI_DOTR)
-    THOP_CASE(EPI_TS)
-    default:
-      return set_error(ctx, LQCD_ERR_INVALID, "tile hop: unknown epilogue %d", epi);
-  }
-#undef THOP_CASE
-  e = cudaGetLastError();
+  static bool attr_set[3] = {false, false, false};
+  auto go = [&](auto kern, int slot) {
+    if (!attr_set[slot]) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM);
+      if (e != cudaSuccess) return e;
+      attr_set[slot] = true;
+    }
+    KL kern<<<G, T_THREADS, T_SMEM, q>>>(a);
+    return cudaGetLastError();
+  };
+  cudaError_t e;
+  if (epi == EPI_PLAIN) e = go(k_thop<EPI_PLAIN>, 0);
+  else if (epi == EPI_DOTR) e = go(k_thop<EPI_DOTR>, 1);
+  else if (epi == EPI_TS) e = go(k_thop<EPI_TS>, 2);
+  else return set_error(ctx, LQCD_ERR_INVALID, "tile hop: unknown epilogue %d", epi);
   if (e != cudaSuccess) return cuda_error(ctx, e, "tile hop launch");
   return LQCD_OK;
 }
 
 // ==================================================== element-wise tile kernels
 // A block takes work items (active tile T, chunk ch of TCH sites) by grid
-// stride; thread (m, g) = (tid >> 4, tid & 15) owns the 8 right-hand sides
-// 8g .. 8g+7 of the tile and walks (site, complex component) units m, m + 16, ...
+// stride; thread (r, h) = (tid % TR, tid / TR) owns right-hand side r of the
+// tile and walks the sites j0 + h, j0 + h + 2, ...  Every tile-field access of
+// a warp is one 512-byte segment (chunk c of 32 consecutive right-hand sides).
 constexpr int TB = 256;  // threads per block of the element-wise tile kernels
 constexpr int TSB = 8;   // sites per transposition sub-block (x / FP32 side)
+constexpr int TXS = TSB * 24 + 4;  // floats per RHS row of the staging buffer (padded against bank conflicts)
 
 __device__ __forceinline__ void bf8_to_f(uint4 w, float f[8]) {
   const uint32_t u[4] = {w.x, w.y, w.z, w.w};
@@ -186,67 +148,37 @@ __device__ __forceinline__ uint4 f_to_bf8(const float f[8]) {
   }
   return make_uint4(u[0], u[1], u[2], u[3]);
 }
-// real k of the 8 right-hand sides 8g .. 8g+7 at (tile T, site j), in uint4 units;
-// real k + 1 (the imaginary part when k is even) is 64 elements = 8 uint4 further
-__device__ __forceinline__ size_t trow(int T, int vh, int j, int k, int g) {
-  return tile_elem(T, vh, j, k, 8 * g) / 8;
-}
-__device__ __forceinline__ void load_c8(const uint4 *f, size_t re_idx, float re[8], float im[8]) {
-  bf8_to_f(f[re_idx], re);
-  bf8_to_f(f[re_idx + 8], im);
-}
-__device__ __forceinline__ void store_c8(uint4 *f, size_t re_idx, const float re[8], const float im[8]) {
-  f[re_idx] = f_to_bf8(re);
-  f[re_idx + 8] = f_to_bf8(im);
-}
 __device__ __forceinline__ float2 sc2(double2 v) { return make_float2((float)v.x, (float)v.y); }
 
 // p = r + beta (p - omega v); members flagged for restart take rhat = r, p = r
 __global__ void __launch_bounds__(TB) k_tile_p(int vh, int nch, const SState *sc, const uint4 *r, uint4 *rhat, uint4 *p,
                                                const uint4 *v, const int *tlist, const int *tcount) {
   const int n_items = *tcount * nch;
-  const int g = threadIdx.x & 15, m = threadIdx.x >> 4;
+  const int rr = threadIdx.x % TR, h = threadIdx.x / TR;
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
     const int T = tlist[w / nch], ch = w % nch;
     const int j0 = ch * TCH, ns = min(TCH, vh - j0);
-    float2 be[8], om[8];
-    unsigned restart = 0;
+    const SState &S = sc[T * TR + rr];
+    const float2 be = sc2(S.beta), om = sc2(S.omega);
+    const bool rs = S.restart != 0;
+    for (int js = h; js < ns; js += TB / TR) {
+      const size_t e0 = tile_chunk(T, vh, j0 + js, 0, rr);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const SState &s = sc[T * TR + 8 * g + i];
-      be[i] = sc2(s.beta);
-      om[i] = sc2(s.omega);
-      restart |= (s.restart ? 1u : 0u) << i;
-    }
-    for (int u = m; u < ns * 12; u += 16) {
-      const int j = j0 + u / 12, c = u % 12;
-      const size_t ix = trow(T, vh, j, 2 * c, g);
-      float rr[8], ri[8], pr[8], pi[8], vr[8], vi[8];
-      load_c8(r, ix, rr, ri);
-      load_c8(p, ix, pr, pi);
-      load_c8(v, ix, vr, vi);
+      for (int c = 0; c < 3; ++c) {
+        float R[8], P[8], V[8];
+        bf8_to_f(r[e0 + c * TR], R);
+        bf8_to_f(p[e0 + c * TR], P);
+        bf8_to_f(v[e0 + c * TR], V);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        // t = p - omega v; p = r + beta t
-        const float tr = pr[i] - (om[i].x * vr[i] - om[i].y * vi[i]);
-        const float ti = pi[i] - (om[i].x * vi[i] + om[i].y * vr[i]);
-        const float nr = rr[i] + (be[i].x * tr - be[i].y * ti);
-        const float ni = ri[i] + (be[i].x * ti + be[i].y * tr);
-        const bool rs = (restart >> i) & 1u;
-        pr[i] = rs ? rr[i] : nr;
-        pi[i] = rs ? ri[i] : ni;
-      }
-      store_c8(p, ix, pr, pi);
-      if (restart) {
-        float hr[8], hi[8];
-        load_c8(rhat, ix, hr, hi);
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-          if ((restart >> i) & 1u) {
-            hr[i] = rr[i];
-            hi[i] = ri[i];
-          }
-        store_c8(rhat, ix, hr, hi);
+        for (int i = 0; i < 4; ++i) {
+          // t = p - omega v; p = r + beta t
+          const float tr = P[2 * i] - (om.x * V[2 * i] - om.y * V[2 * i + 1]);
+          const float ti = P[2 * i + 1] - (om.x * V[2 * i + 1] + om.y * V[2 * i]);
+          P[2 * i] = rs ? R[2 * i] : R[2 * i] + (be.x * tr - be.y * ti);
+          P[2 * i + 1] = rs ? R[2 * i + 1] : R[2 * i + 1] + (be.x * ti + be.y * tr);
+        }
+        p[e0 + c * TR] = f_to_bf8(P);
+        if (rs) rhat[e0 + c * TR] = r[e0 + c * TR];
       }
     }
   }
@@ -256,45 +188,42 @@ __global__ void __launch_bounds__(TB) k_tile_p(int vh, int nch, const SState *sc
 __global__ void __launch_bounds__(TB) k_tile_s(int vh, int nch, const SState *sc, const uint4 *r, const uint4 *v,
                                                uint4 *s, const int *tlist, const int *tcount) {
   const int n_items = *tcount * nch;
-  const int g = threadIdx.x & 15, m = threadIdx.x >> 4;
+  const int rr = threadIdx.x % TR, h = threadIdx.x / TR;
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
     const int T = tlist[w / nch], ch = w % nch;
     const int j0 = ch * TCH, ns = min(TCH, vh - j0);
-    float2 al[8];
+    const float2 al = sc2(sc[T * TR + rr].alpha);
+    for (int js = h; js < ns; js += TB / TR) {
+      const size_t e0 = tile_chunk(T, vh, j0 + js, 0, rr);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) al[i] = sc2(sc[T * TR + 8 * g + i].alpha);
-    for (int u = m; u < ns * 12; u += 16) {
-      const int j = j0 + u / 12, c = u % 12;
-      const size_t ix = trow(T, vh, j, 2 * c, g);
-      float rr[8], ri[8], vr[8], vi[8];
-      load_c8(r, ix, rr, ri);
-      load_c8(v, ix, vr, vi);
+      for (int c = 0; c < 3; ++c) {
+        float R[8], V[8];
+        bf8_to_f(r[e0 + c * TR], R);
+        bf8_to_f(v[e0 + c * TR], V);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        rr[i] -= al[i].x * vr[i] - al[i].y * vi[i];
-        ri[i] -= al[i].x * vi[i] + al[i].y * vr[i];
+        for (int i = 0; i < 4; ++i) {
+          R[2 * i] -= al.x * V[2 * i] - al.y * V[2 * i + 1];
+          R[2 * i + 1] -= al.x * V[2 * i + 1] + al.y * V[2 * i];
+        }
+        s[e0 + c * TR] = f_to_bf8(R);
       }
-      store_c8(s, ix, rr, ri);
     }
   }
 }
 
-// fixed-order reduction of the per-thread partials (8 RHS x 3 values per
-// thread, 16 threads per RHS group) into part[rhs][nch] as (re, im, nn, 0)
-__device__ __forceinline__ void tile_reduce_store(float *red, const float acc[8][3], int T, int ch, int nch, D4S *part) {
-  const int g = threadIdx.x & 15, m = threadIdx.x >> 4;
+// fixed-order reduction of the per-thread partials (one RHS and 3 values per
+// thread, TB / TR threads per RHS) into part[rhs][nch] as (re, im, nn, 0)
+__device__ __forceinline__ void tile_reduce_store(float *red, const float acc[3], int T, int ch, int nch, D4S *part) {
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) red[(m * TR + 8 * g + i) * 3 + q] = acc[i][q];
+  for (int q = 0; q < 3; ++q) red[threadIdx.x * 3 + q] = acc[q];
   __syncthreads();
   if (threadIdx.x < TR) {
     float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-    for (int mm = 0; mm < 16; ++mm) {
-      s0 += red[(mm * TR + threadIdx.x) * 3];
-      s1 += red[(mm * TR + threadIdx.x) * 3 + 1];
-      s2 += red[(mm * TR + threadIdx.x) * 3 + 2];
+    for (int hh = 0; hh < TB / TR; ++hh) {
+      s0 += red[(hh * TR + threadIdx.x) * 3];
+      s1 += red[(hh * TR + threadIdx.x) * 3 + 1];
+      s2 += red[(hh * TR + threadIdx.x) * 3 + 2];
     }
     part[(size_t)(T * TR + threadIdx.x) * nch + ch] = D4S{(double)s0, (double)s1, (double)s2, 0.0};
   }
@@ -308,63 +237,61 @@ __device__ __forceinline__ void tile_reduce_store(float *red, const float acc[8]
 __global__ void __launch_bounds__(TB) k_tile_xr(int vh, int nch, const SState *sc, const int *flags, F32F x,
                                                 const uint4 *p, const uint4 *s, const uint4 *t, uint4 *r,
                                                 const uint4 *rhat, const int *tlist, const int *tcount, D4S *part) {
-  extern __shared__ float xsm[];  // TR * TSB * 24 floats (also the reduction scratch)
+  extern __shared__ float xsm[];  // TR * TXS floats (also the reduction scratch)
   __shared__ int act[TR];
   const int n_items = *tcount * nch;
-  const int g = threadIdx.x & 15, m = threadIdx.x >> 4;
+  const int rr = threadIdx.x % TR, h = threadIdx.x / TR;
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
     const int T = tlist[w / nch], ch = w % nch;
     const int j0 = ch * TCH, ns = min(TCH, vh - j0);
-    float2 al[8], om[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      al[i] = sc2(sc[T * TR + 8 * g + i].alpha);
-      om[i] = sc2(sc[T * TR + 8 * g + i].omega);
-    }
+    const float2 al = sc2(sc[T * TR + rr].alpha), om = sc2(sc[T * TR + rr].omega);
+    __syncthreads();
     if (threadIdx.x < TR) act[threadIdx.x] = flags[T * TR + threadIdx.x] & FLAG_ACTIVE;
-    float acc[8][3];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = 0.f;
+    float acc[3] = {0.f, 0.f, 0.f};
     for (int b0 = 0; b0 < ns; b0 += TSB) {
       const int nb = min(TSB, ns - b0);
       __syncthreads();
-      for (int u = m; u < nb * 12; u += 16) {
-        const int js = u / 12, c = u % 12, j = j0 + b0 + js;
-        const size_t ix = trow(T, vh, j, 2 * c, g);
-        float pr[8], pi[8], sr[8], si[8], tr[8], ti[8], hr[8], hi[8];
-        load_c8(p, ix, pr, pi);
-        load_c8(s, ix, sr, si);
-        load_c8(t, ix, tr, ti);
-        load_c8(rhat, ix, hr, hi);
+      for (int js = h; js < nb; js += TB / TR) {
+        const size_t e0 = tile_chunk(T, vh, j0 + b0 + js, 0, rr);
+        float *qrow = xsm + (size_t)rr * TXS + js * 24;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float dr = al[i].x * pr[i] - al[i].y * pi[i] + (om[i].x * sr[i] - om[i].y * si[i]);
-          const float di = al[i].x * pi[i] + al[i].y * pr[i] + (om[i].x * si[i] + om[i].y * sr[i]);
-          float *q = xsm + ((size_t)(8 * g + i) * TSB + js) * 24 + 2 * c;
-          q[0] = dr;
-          q[1] = di;
-          const float nr = sr[i] - (om[i].x * tr[i] - om[i].y * ti[i]);
-          const float ni = si[i] - (om[i].x * ti[i] + om[i].y * tr[i]);
-          sr[i] = nr;
-          si[i] = ni;
-          acc[i][0] += hr[i] * nr + hi[i] * ni;
-          acc[i][1] += hr[i] * ni - hi[i] * nr;
-          acc[i][2] += nr * nr + ni * ni;
+        for (int c = 0; c < 3; ++c) {
+          float P[8], S[8], Tt[8], H[8], dx[8];
+          bf8_to_f(p[e0 + c * TR], P);
+          bf8_to_f(s[e0 + c * TR], S);
+          bf8_to_f(t[e0 + c * TR], Tt);
+          bf8_to_f(rhat[e0 + c * TR], H);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float pr = P[2 * i], pi = P[2 * i + 1], sr = S[2 * i], si = S[2 * i + 1];
+            dx[2 * i] = al.x * pr - al.y * pi + (om.x * sr - om.y * si);
+            dx[2 * i + 1] = al.x * pi + al.y * pr + (om.x * si + om.y * sr);
+            const float nr = sr - (om.x * Tt[2 * i] - om.y * Tt[2 * i + 1]);
+            const float ni = si - (om.x * Tt[2 * i + 1] + om.y * Tt[2 * i]);
+            S[2 * i] = nr;
+            S[2 * i + 1] = ni;
+            const float hr = H[2 * i], hi = H[2 * i + 1];
+            acc[0] += hr * nr + hi * ni;
+            acc[1] += hr * ni - hi * nr;
+            acc[2] += nr * nr + ni * ni;
+          }
+          reinterpret_cast<float4 *>(qrow + 8 * c)[0] = make_float4(dx[0], dx[1], dx[2], dx[3]);
+          reinterpret_cast<float4 *>(qrow + 8 * c)[1] = make_float4(dx[4], dx[5], dx[6], dx[7]);
+          r[e0 + c * TR] = f_to_bf8(S);
         }
-        store_c8(r, ix, sr, si);
       }
       __syncthreads();
       // x side: TSB-site runs of float4 per (rhs, k4)
       for (int idx = threadIdx.x; idx < TR * 6 * TSB; idx += TB) {
-        const int js = idx % TSB, k4 = (idx / TSB) % 6, rr = idx / (TSB * 6);
-        if (js >= nb || !act[rr]) continue;
-        const float *q = xsm + ((size_t)rr * TSB + js) * 24 + 4 * k4;
-        float4 *xp = x.d + ((size_t)(T * TR + rr) * 6 + k4) * vh + j0 + b0 + js;
+        const int js = idx % TSB, k4 = (idx / TSB) % 6, r2 = idx / (TSB * 6);
+        if (js >= nb || !act[r2]) continue;
+        const float4 d = *reinterpret_cast<const float4 *>(xsm + (size_t)r2 * TXS + js * 24 + 4 * k4);
+        float4 *xp = x.d + ((size_t)(T * TR + r2) * 6 + k4) * vh + j0 + b0 + js;
         float4 o = *xp;
-        o.x += q[0];
-        o.y += q[1];
-        o.z += q[2];
-        o.w += q[3];
+        o.x += d.x;
+        o.y += d.y;
+        o.z += d.z;
+        o.w += d.w;
         *xp = o;
       }
     }
@@ -380,59 +307,52 @@ __global__ void __launch_bounds__(TB) k_tile_copy(int vh, int nch, const int *fl
   extern __shared__ float xsm[];
   __shared__ int fl[TR];
   const int n_items = *tcount * nch;
-  const int g = threadIdx.x & 15, m = threadIdx.x >> 4;
+  const int rr = threadIdx.x % TR, h = threadIdx.x / TR;
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
     const int T = tlist[w / nch], ch = w % nch;
     const int j0 = ch * TCH, ns = min(TCH, vh - j0);
     __syncthreads();
     if (threadIdx.x < TR) fl[threadIdx.x] = flags[T * TR + threadIdx.x] & FLAG_RU;
     __syncthreads();
-    unsigned mine = 0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) mine |= (fl[8 * g + i] ? 1u : 0u) << i;
-    float acc[8][3];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = 0.f;
+    const bool mine = fl[rr] != 0;
+    float acc[3] = {0.f, 0.f, 0.f};
     for (int b0 = 0; b0 < ns; b0 += TSB) {
       const int nb = min(TSB, ns - b0);
       __syncthreads();
       for (int idx = threadIdx.x; idx < TR * 6 * TSB; idx += TB) {
-        const int js = idx % TSB, k4 = (idx / TSB) % 6, rr = idx / (TSB * 6);
-        if (js >= nb || !fl[rr]) continue;
-        const size_t gi = ((size_t)(T * TR + rr) * 6 + k4) * vh + j0 + b0 + js;
-        const float4 v = src.d[gi];
-        float *q = xsm + ((size_t)rr * TSB + js) * 24 + 4 * k4;
-        q[0] = v.x;
-        q[1] = v.y;
-        q[2] = v.z;
-        q[3] = v.w;
+        const int js = idx % TSB, k4 = (idx / TSB) % 6, r2 = idx / (TSB * 6);
+        if (js >= nb || !fl[r2]) continue;
+        const size_t gi = ((size_t)(T * TR + r2) * 6 + k4) * vh + j0 + b0 + js;
+        *reinterpret_cast<float4 *>(xsm + (size_t)r2 * TXS + js * 24 + 4 * k4) = src.d[gi];
         if (zero_x) x.d[gi] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       __syncthreads();
-      for (int u = m; u < nb * 12; u += 16) {
-        const int js = u / 12, c = u % 12, j = j0 + b0 + js;
-        const size_t ix = trow(T, vh, j, 2 * c, g);
-        float vr[8], vi[8], hr[8], hi[8];
-        load_c8(r, ix, vr, vi);
+      for (int js = h; js < nb; js += TB / TR) {
+        const size_t e0 = tile_chunk(T, vh, j0 + b0 + js, 0, rr);
+        const float *qrow = xsm + (size_t)rr * TXS + js * 24;
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-          if ((mine >> i) & 1u) {
-            const float *q = xsm + ((size_t)(8 * g + i) * TSB + js) * 24 + 2 * c;
-            vr[i] = q[0];
-            vi[i] = q[1];
+        for (int c = 0; c < 3; ++c) {
+          float V[8], H[8];
+          if (mine) {
+            const float4 a0 = reinterpret_cast<const float4 *>(qrow + 8 * c)[0];
+            const float4 a1 = reinterpret_cast<const float4 *>(qrow + 8 * c)[1];
+            V[0] = a0.x; V[1] = a0.y; V[2] = a0.z; V[3] = a0.w;
+            V[4] = a1.x; V[5] = a1.y; V[6] = a1.z; V[7] = a1.w;
+            // the stored member values are rounded to BF16; the partials use the
+            // FP32 source values, as the pair path does
+            r[e0 + c * TR] = f_to_bf8(V);
+          } else {
+            bf8_to_f(r[e0 + c * TR], V);
           }
-        if (mine) {
-          // the stored member values are rounded to BF16; the partials use the
-          // FP32 source values, as the pair path does
-          store_c8(r, ix, vr, vi);
-        }
-        if (use_rhat) load_c8(rhat, ix, hr, hi);
+          if (use_rhat) bf8_to_f(rhat[e0 + c * TR], H);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float qr = use_rhat ? hr[i] : vr[i], qi = use_rhat ? hi[i] : vi[i];
-          acc[i][0] += qr * vr[i] + qi * vi[i];
-          acc[i][1] += qr * vi[i] - qi * vr[i];
-          acc[i][2] += vr[i] * vr[i] + vi[i] * vi[i];
+          for (int i = 0; i < 4; ++i) {
+            const float vr = V[2 * i], vi = V[2 * i + 1];
+            const float qr = use_rhat ? H[2 * i] : vr, qi = use_rhat ? H[2 * i + 1] : vi;
+            acc[0] += qr * vr + qi * vi;
+            acc[1] += qr * vi - qi * vr;
+            acc[2] += vr * vr + vi * vi;
+          }
         }
       }
     }
@@ -440,7 +360,7 @@ __global__ void __launch_bounds__(TB) k_tile_copy(int vh, int nch, const int *fl
   }
 }
 
-constexpr size_t T_XR_SMEM = (size_t)TR * TSB * 24 * sizeof(float);  // 96 KiB (>= the reduction's 24 KiB)
+constexpr size_t T_XR_SMEM = (size_t)TR * TXS * sizeof(float);  // 98 KiB (>= the reduction's 3 KiB)
 
 int tile_p(cudaStream_t q, int G, int vh, const SState *sc, const TileField &r, const TileField &rhat,
            const TileField &p, const TileField &v, const int *tlist, const int *tcount) {

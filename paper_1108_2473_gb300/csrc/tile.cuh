@@ -3,9 +3,8 @@
 // of the operator D = 1 - kappa H).
 //
 // Layout.  A 16-bit (BF16) sloppy field holds its right-hand sides in tiles of
-// TR = 128: [tile][Vh][2 halves][24 reals][64 RHS] (tile_elem), so one site's
-// block of a tile (24 x 128 values, 6 KiB) is contiguous: 48 rows of 128 bytes,
-// one TMA box.  The 24 reals are ordered ((spin * 3 + colour) * 2 + re/im).
+// TR = 128; one site's block of a tile is [3 chunks][128 RHS][8 reals] (6 KiB,
+// tile_chunk), the 24 reals ordered ((spin * 3 + colour) * 2 + re/im).
 //
 // Hopping term on the tensor cores.  For an output site x of parity p,
 //   (H in)(x) = sum_{d=0..7} [P_d (x) C_d(x)] in(n_d(x)),
@@ -18,50 +17,50 @@
 // one M = 128, N = 32 (24 used), K = 192 product per (site, tile): twelve
 // tcgen05.mma kind::f16 instructions (BF16 in, FP32 accumulate in TMEM).
 //
-// Data flow per (site, tile) item, warp-specialised inside one persistent CTA
-// per SM, TNS-stage shared-memory ring:
-//   * warp 0: TMA -- T_NT tiled loads (one [48 rows][128 B] box per neighbour,
-//     128-byte swizzle) and one bulk copy of the site's link bundle into the
-//     stage; the A buffer is [neighbour][half][24 rows][64 RHS], eight MN-major
-//     SW128 blocks, which the MMAs address with per-step descriptors;
-//   * warps 10-13: the other 8 - T_NT neighbour blocks by cp.async (16 bytes
-//     per request, written to the same swizzled positions), so that the TMA
-//     engine and the load/store units share the ~48 KiB an item needs;
-//   * warps 2-5: build W (K-major, no swizzle) from the site's eight BF16 colour
-//     matrices into a ring of two W buffers; entries of zero spin blocks are
-//     written once at start;
-//   * warp 1 (one thread): the twelve MMAs into one of two TMEM accumulators,
-//     then tcgen05.commit to free the stage and to hand the accumulator on;
+// Data flow.  The neighbour blocks never pass through shared memory: loader
+// warps read them straight into registers (one thread per RHS row; chunk c of
+// 32 right-hand sides is one 512-byte warp load) and write them with
+// tcgen05.st into one of TNI tensor-memory stages of 96 columns (lane = RHS,
+// column 12 d + w = reals 2w, 2w+1 of neighbour d); the MMAs take A from TMEM
+// ([a-tmem] operand) and W from shared memory.  Measured on GB300, copies into
+// shared memory by the bulk-copy engine or by cp.async kept the tensor core
+// waiting (a bulk copy of a neighbour block landed thousands of cycles after
+// it was issued under this load), whereas the loader warps run several items
+// ahead of the MMAs.
+//
+// Roles inside one persistent CTA per SM, all walking the same (tile, site)
+// item sequence:
+//   * warp 1: TMEM allocation (two FP32 accumulators of TN columns and the TNI
+//     stages); one thread issues the twelve MMAs of an item and commits the
+//     stage, W and accumulator barriers;
+//   * warps 2-5: build W (K-major, no swizzle) into a ring of two W buffers
+//     from the site's eight BF16 colour matrices, whose words each builder
+//     thread loads T_LPF items ahead; entries of zero spin blocks are written
+//     once at start;
 //   * warps 6-9 (one thread per right-hand side = TMEM lane): read the 24 FP32
 //     results, apply the epilogue (out = cA A + cH D, optional dot products),
-//     store BF16 (streaming stores), and accumulate per-RHS partial sums over
-//     chunks of TCH sites.
+//     store BF16 (streaming stores) and accumulate per-RHS partial sums over
+//     chunks of TCH sites;
+//   * warps 10-25: loaders; warp w serves TMEM lane quarter w % 4 and the
+//     neighbours 2 lg, 2 lg + 1 of every item, lg = (w - 10) / 4, with the loads
+//     of the next item issued before the TMEM stores of the current one;
+//   * warp 0: work counters for the profiling hook only.
 // Every wait on an mbarrier is bounded; a wait that runs out sets an error
-// code, the other roles stop at their next wait, TMA copies in flight are
-// waited for (bounded), and TMEM is released before the kernel returns.
+// code, the other roles stop at their next wait, issued MMAs are waited for
+// (bounded by time only), and TMEM is released before the kernel returns.
 #pragma once
-
-#include <cuda.h>
 
 #include "tile_api.cuh"
 
 namespace lqcd {
 
-constexpr int TNS = 4;    // shared-memory stages of the hop pipeline (neighbour blocks + link bundle)
 constexpr int TK = 192;   // MMA K per site: 8 directions x 24 reals
 constexpr int TN = 32;    // MMA N: 24 output reals, padded
-constexpr int T_A_NBR = 6144;                  // one neighbour block in a stage: [2 halves][24][64] BF16
-constexpr int T_A_BYTES = 8 * T_A_NBR;         // 48 KiB
 constexpr int T_W_BYTES = (TK / 8) * 512;      // 12 KiB: 24 K-chunks x 4 N-groups x 128 B
-constexpr int T_NT = 0;                        // neighbours per item loaded by TMA; the rest by cp.async
-constexpr int T_NL = 256;                      // cp.async loader threads (warps 10 ..)
-constexpr int T_THREADS = 320 + T_NL;
-constexpr int T_L_BYTES = 8 * 9 * 4;           // one site's link bundle: 288 B
-constexpr int T_SMEM = 1024 + TNS * (T_A_BYTES + T_L_BYTES) + 2 * T_W_BYTES + 256;
-constexpr int T_TMEM_COLS = 64;                // two FP32 accumulators of TN columns
+constexpr int T_TMEM_COLS = 512;               // accumulators and loaded neighbour blocks
 
 // error codes written by the tile hop when a bounded wait runs out
-enum { THOP_ERR_TMA = 1, THOP_ERR_W = 2, THOP_ERR_MMA = 3, THOP_ERR_ACC = 4, THOP_ERR_EPI = 5 };
+enum { THOP_ERR_LOAD = 1, THOP_ERR_W = 2, THOP_ERR_MMA = 3, THOP_ERR_ACC = 4, THOP_ERR_EPI = 5 };
 
 // Spin structure of P_d = 1 -+ gamma_mu (DeGrand-Rossi): row s has the identity
 // and one off-diagonal entry at column so[d][s] with value (re, im) in {0, +-1}.
@@ -75,7 +74,7 @@ struct THopArgs {
   int p_out;
   const uint32_t *links;  // [2 parity][Vh][8 d][9] BF16x2 (re low, im high), signs and daggers folded in
   __nv_bfloat16 *out;
-  const __nv_bfloat16 *in; // the hop's input field (for the cp.async loaders)
+  const __nv_bfloat16 *in; // the hop's input field
   const __nv_bfloat16 *A;  // epilogue operand (tile field), EPI != PLAIN
   const __nv_bfloat16 *B;  // <B, out> for EPI_DOTR
   float cA, cH;
@@ -106,9 +105,6 @@ __device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
 __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_u32(b)) : "memory");
 }
-__device__ __forceinline__ void mbar_arrive_tx(uint64_t *b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(b)), "r"(bytes) : "memory");
-}
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
@@ -128,24 +124,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile
     }
   }
 }
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(map), "r"(x), "r"(y), "r"(s_u32(bar))
-      : "memory");
+// drain wait: bounded by time only, so that asynchronous work this thread
+// started (MMAs) has finished before TMEM or shared memory is
+// given up, even after another role has aborted
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t *b, uint32_t parity) {
+  const uint64_t t0 = global_ns();
+  while (!mbar_try(b, parity))
+    if (global_ns() - t0 > T_WAIT_NS) return false;
+  return true;
 }
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(s_u32(bar))
-               : "memory");
-}
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -156,9 +143,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
   return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | ((uint64_t)layout << 61);
 }
-// instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, A MN-major,
-// B K-major, N = TN, M = TR
-constexpr uint32_t T_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | ((uint32_t)(TN >> 3) << 17) |
+// instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both
+// K-major, N = TN, M = TR
+constexpr uint32_t T_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
                              ((uint32_t)(TR >> 4) << 24);
 
 __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
@@ -168,6 +155,24 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t
       "l"(adesc), "l"(bdesc), "r"(T_IDESC), "r"(accumulate)
       : "memory");
 }
+// D (+)= A B with A in tensor memory (lane = row, two BF16 of K per column)
+__device__ __forceinline__ void tc_mma_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(bdesc), "r"(T_IDESC), "r"(accumulate)
+      : "memory");
+}
+// one neighbour block of one RHS row (12 columns) from registers into TMEM
+__device__ __forceinline__ void tc_st12(uint32_t taddr, const uint4 v[3]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0].x),
+               "r"(v[0].y), "r"(v[0].z), "r"(v[0].w), "r"(v[1].x), "r"(v[1].y), "r"(v[1].z), "r"(v[1].w)
+               : "memory");
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr + 8), "r"(v[2].x),
+               "r"(v[2].y), "r"(v[2].z), "r"(v[2].w)
+               : "memory");
+}
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_u32(bar))
                : "memory");
@@ -207,45 +212,79 @@ __device__ __forceinline__ int neighbour(const Geom &g, const int c[4], int d) {
 
 // Work of one CTA: units u = blockIdx.x, blockIdx.x + gridDim.x, ... of
 // (active tile, chunk of TCH sites), tile-major; every role walks the same
-// sequence of (tile, site) items.  The grid-stride order keeps the whole GPU
-// on a window of gridDim.x consecutive chunks of one tile, so that the eight
-// uses of a neighbour block fall close together in time and hit in L2.
+// sequence of (tile, site) items with a TCur cursor (divisions once per unit,
+// not per item).  The grid-stride order keeps the whole GPU on a window of
+// gridDim.x consecutive chunks of one tile, so that the eight uses of a
+// neighbour block fall close together in time and hit in L2.
+struct TCur {
+  int u, j, jend, T, ch;
+};
 struct TItems {
   int u0, u1, ustep, nch, vh;
-  __device__ void init(int count, int nch_, int vh_) {
+  const int *tlist;
+  __device__ void init(int count, int nch_, int vh_, const int *tlist_) {
     nch = nch_;
     vh = vh_;
+    tlist = tlist_;
     u0 = blockIdx.x;
     u1 = count * nch;
     ustep = gridDim.x;
   }
+  __device__ bool set(TCur &c, int u) const {
+    if (u >= u1) return false;
+    c.u = u;
+    c.ch = u % nch;
+    c.T = tlist[u / nch];
+    c.j = c.ch * TCH;
+    c.jend = min(c.j + TCH, vh);
+    return true;
+  }
+  __device__ bool first(TCur &c) const { return set(c, u0); }
+  // the item after c; false past the last one
+  __device__ bool next(TCur &c) const { return ++c.j < c.jend || set(c, c.u + ustep); }
 };
-// results are stored with an L2 evict-first policy: they are not read again in
-// this launch, and the neighbour blocks still to be reused should stay in L2
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int x, int y, uint32_t src) {
-  uint64_t pol;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%1, %2}], [%3], %4;" ::"l"(
-                   map),
-               "r"(x), "r"(y), "r"(src), "l"(pol)
-               : "memory");
-  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+// coordinates of the parity-p site after the one with coordinates c (parity-local
+// index + 1, as coords_of orders them)
+__device__ __forceinline__ void coords_next(const Geom &g, int p, int c[4]) {
+  int xh = c[0] >> 1;
+  if (++xh == g.Lxh) {
+    xh = 0;
+    if (++c[1] == g.L[1]) {
+      c[1] = 0;
+      if (++c[2] == g.L[2]) {
+        c[2] = 0;
+        ++c[3];
+      }
+    }
+  }
+  c[0] = 2 * xh + ((c[1] + c[2] + c[3] + p) & 1);
 }
-__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// Loader warps: NG groups of four (one warp per TMEM lane quarter), each group
+// NPW neighbours of every item; TNI items in flight (TMEM stages).
+constexpr int TNI = 4;
+constexpr int T_NPW = 2;                          // neighbours per loader warp
+constexpr int T_NG = 8 / T_NPW;                   // loader warp groups
+constexpr int T_LW = 4 * T_NG;                    // loader warps (10 .. 10 + T_LW - 1)
+constexpr int T_THREADS = 320 + 32 * T_LW;
+constexpr int T_ACOLS = 8 * 12;                   // TMEM columns of one item's neighbour blocks
+constexpr int T_ACOL0 = 2 * TN;                   // after the two accumulators
+constexpr int T_LPF = 4;                          // items of link words the W builders hold in registers
+// the CTA needs ~26 KiB of shared memory; requesting more than half of an SM's
+// keeps it alone on its SM, as the TMEM allocation of all 512 columns requires
+constexpr int T_SMEM = 116 * 1024;
+static_assert(1024 + 2 * T_W_BYTES + 1024 <= T_SMEM, "tile hop shared memory");
+static_assert(T_ACOL0 + TNI * T_ACOLS <= T_TMEM_COLS, "tile hop tensor memory");
+static_assert(T_THREADS <= 1024, "tile hop threads");
 
 template <int EPI>
-__global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ CUtensorMap tin, THopArgs a) {
+__global__ void __launch_bounds__(T_THREADS, 1) k_thop(THopArgs a) {
   extern __shared__ __align__(1024) unsigned char t_smem_raw[];
   unsigned char *base = (unsigned char *)(((uintptr_t)t_smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char *sA = base;                                  // TNS x 48 KiB neighbour blocks
-  unsigned char *sW = base + TNS * T_A_BYTES;                // 2 x 12 KiB W ring
-  unsigned char *sL = sW + 2 * T_W_BYTES;                    // TNS x 288 B link bundles
-  uint64_t *bars = (uint64_t *)(sL + TNS * T_L_BYTES);       // full, empty, lfull [TNS]; accf, acce, wfull, wempty [2]; drain
-  uint64_t *full = bars, *empty = bars + TNS, *lfull = bars + 2 * TNS;
-  uint64_t *accf = bars + 3 * TNS, *acce = bars + 3 * TNS + 2;
-  uint64_t *wfull = bars + 3 * TNS + 4, *wempty = bars + 3 * TNS + 6;
-  uint64_t *drain = bars + 3 * TNS + 8;
+  unsigned char *sW = base;  // 2 x 12 KiB W ring
+  uint64_t *bars = (uint64_t *)(sW + 2 * T_W_BYTES);
+  uint64_t *afull = bars, *aempty = bars + TNI;
+  uint64_t *accf = bars + 2 * TNI, *acce = accf + 2, *wfull = accf + 4, *wempty = accf + 6, *drain = accf + 8;
   uint32_t *tslot = (uint32_t *)(drain + 1);
   volatile int *abort = (volatile int *)(tslot + 1);
 
@@ -253,15 +292,14 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
   const Geom &g = a.g;
   const int count = *a.tcount;
   TItems it;
-  it.init(count, a.nch, g.Vh);
+  it.init(count, a.nch, g.Vh, a.tlist);
 
   // zero the W buffers (zero spin blocks stay zero), set up barriers and TMEM
   for (int i = tid; i < 2 * T_W_BYTES / 16; i += T_THREADS) reinterpret_cast<uint4 *>(sW)[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
-    for (int s = 0; s < TNS; ++s) {
-      mbar_init(full + s, 1 + T_NL);  // TMA producer, cp.async loaders
-      mbar_init(empty + s, 1);
-      mbar_init(lfull + s, 1);
+    for (int s = 0; s < TNI; ++s) {
+      mbar_init(afull + s, T_LW);  // one arrival per loader warp
+      mbar_init(aempty + s, 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(accf + b, 1);
@@ -279,7 +317,6 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  if (warp == 0 && lane == 0) asm volatile("prefetch.tensormap [%0];" ::"l"(&tin) : "memory");
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
@@ -287,108 +324,62 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
   const uint32_t tmem = *tslot;
 
   if (warp == 0) {
-    // ------------------------------------------------------------ TMA producer
-    // the whole warp walks the items; lanes 0..T_NT-1 each issue one neighbour
-    // block and lane 31 the link bundle
-    int q = 0;
-    int last_q[TNS];
-    for (int s = 0; s < TNS; ++s) last_q[s] = -1;
-    const int dn = lane;
-    for (int u = it.u0; u < it.u1 && !*abort; u += it.ustep) {
-      const int T = a.tlist[u / it.nch], ch = u % it.nch;
-      const int j0 = ch * TCH, j1 = min(j0 + TCH, it.vh);
-      if (a.prof && lane == 0)
-        atomicAdd(a.prof + EPI, (unsigned long long)(j1 - j0) * (unsigned long long)min(TR, a.nrhs - T * TR));
-      bool ok = true;
-      for (int j = j0; j < j1; ++j, ++q) {
-        const int s = q % TNS;
-        const bool got = q < TNS || mbar_wait(empty + s, ((q / TNS) - 1) & 1, abort);
-        if (!__all_sync(0xffffffffu, got)) {
-          if (lane == 0) atomicCAS(a.err, 0, THOP_ERR_TMA);
-          *abort = 1;
-          ok = false;
-          break;
-        }
-        if (lane == 0) {
-          mbar_arrive_tx(lfull + s, T_L_BYTES);
-          mbar_arrive_tx(full + s, T_NT * T_A_NBR);
-        }
-        __syncwarp();
-        if (lane < T_NT) {
-          int c[4];
-          coords_of(g, a.p_out, j, c);
-          const int row = (T * it.vh + neighbour(g, c, dn)) * 48;
-          tma_load_2d(s_u32(sA + s * T_A_BYTES) + dn * T_A_NBR, &tin, 0, row, full + s);
-        } else if (lane == 31) {
-          // the site's link bundle for the W builders
-          bulk_load(s_u32(sL + s * T_L_BYTES), a.links + (size_t)(a.p_out * g.Vh + j) * 72, T_L_BYTES, lfull + s);
-        }
-        last_q[s] = q;
+    // ------------------------------------------------------------ bookkeeping
+    if (lane == 0 && a.prof)
+      for (int v = it.u0; v < it.u1; v += it.ustep) {
+        const int T = a.tlist[v / it.nch], ch = v % it.nch;
+        atomicAdd(a.prof + EPI, (unsigned long long)(min(ch * TCH + TCH, it.vh) - ch * TCH) *
+                                    (unsigned long long)min(TR, a.nrhs - T * TR));
       }
-      if (!ok) break;
-    }
-    // copies in flight must land before the CTA exits (normally already consumed)
-    if (lane == 0)
-      for (int s = 0; s < TNS; ++s)
-        if (last_q[s] >= 0) {
-          mbar_wait(full + s, (last_q[s] / TNS) & 1, abort);
-          mbar_wait(lfull + s, (last_q[s] / TNS) & 1, abort);
-        }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       int q = 0;
       bool issued = false;
-      for (int u = it.u0; u < it.u1 && !*abort; u += it.ustep) {
-        const int ch = u % it.nch;
-        const int j0 = ch * TCH, j1 = min(j0 + TCH, it.vh);
-        for (int j = j0; j < j1; ++j, ++q) {
-          const int s = q % TNS, acc = q & 1;
-          if (!mbar_wait(full + s, (q / TNS) & 1, abort)) {
-            atomicCAS(a.err, 0, THOP_ERR_MMA);
-            *abort = 1;
-            break;
-          }
-          if (!mbar_wait(wfull + acc, (q >> 1) & 1, abort)) {
-            atomicCAS(a.err, 0, THOP_ERR_W);
-            *abort = 1;
-            break;
-          }
-          if (q >= 2 && !mbar_wait(acce + acc, ((q >> 1) - 1) & 1, abort)) {
-            atomicCAS(a.err, 0, THOP_ERR_ACC);
-            *abort = 1;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t aaddr = s_u32(sA + s * T_A_BYTES), waddr = s_u32(sW + acc * T_W_BYTES);
-          // K = 192 = 8 neighbours x 24 reals in twelve steps of 16: rows 0..15 of
-          // neighbour d (K-groups 3d, 3d+1: SBO 1 KiB), and rows 16..23 of the
-          // neighbours d, d + 1 together (SBO 6 KiB); the W chunks follow the
-          // same K order (LBO 512 B, resp. 3 x 512 B); LBO of A = the 3 KiB half
-#pragma unroll
-          for (int d = 0; d < 8; ++d) {
-            tc_mma(tmem + acc * TN, smem_desc(aaddr + d * T_A_NBR, 3072, 1024, 2),
-                   smem_desc(waddr + 3 * d * 512, 512, 128, 0), d > 0);
-            if (d & 1)
-              tc_mma(tmem + acc * TN, smem_desc(aaddr + (d - 1) * T_A_NBR + 2048, 3072, T_A_NBR, 2),
-                     smem_desc(waddr + (3 * (d - 1) + 2) * 512, 3 * 512, 128, 0), 1);
-          }
-          tc_commit(empty + s);
-          tc_commit(wempty + acc);
-          tc_commit(accf + acc);
-          issued = true;
+      TCur cur;
+      for (bool more = it.first(cur); more && !*abort; more = it.next(cur), ++q) {
+        const int grp = q % TNI, acc = q & 1;
+        if (!mbar_wait(wfull + acc, (q >> 1) & 1, abort)) {
+          atomicCAS(a.err, 0, THOP_ERR_W);
+          *abort = 1;
+          break;
         }
-        if (*abort) break;
+        if (q >= 2 && !mbar_wait(acce + acc, ((q >> 1) - 1) & 1, abort)) {
+          atomicCAS(a.err, 0, THOP_ERR_ACC);
+          *abort = 1;
+          break;
+        }
+        if (!mbar_wait(afull + grp, (q / TNI) & 1, abort)) {
+          atomicCAS(a.err, 0, THOP_ERR_MMA);
+          *abort = 1;
+          break;
+        }
+        tc_fence_after();
+        // K = 192 in twelve steps of 16: step k reads K-chunks 2k, 2k + 1, i.e.
+        // TMEM columns 8k .. 8k+7 of the item's stage (chunk 3 d + c of
+        // neighbour d at columns 12 d + 4 c), and W K-chunks 2k, 2k + 1 (LBO
+        // 512 B, SBO 128 B)
+        const uint32_t waddr = s_u32(sW + acc * T_W_BYTES), tbase = tmem + T_ACOL0 + grp * T_ACOLS;
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+          tc_mma_ts(tmem + acc * TN, tbase + 8 * k, smem_desc(waddr + k * 1024, 512, 128, 0), k > 0);
+        tc_commit(aempty + grp);
+        tc_commit(wempty + acc);
+        tc_commit(accf + acc);
+        issued = true;
       }
       // every MMA issued must have completed before TMEM is released
       if (issued) {
         tc_commit(drain);
-        mbar_wait(drain, 0, abort);
+        mbar_wait_drain(drain, 0);
       }
     }
   } else if (warp < 6) {
     // ------------------------------------------------------------ W builders
-    const int b = tid - 64;  // 0..127; 96 of them own one (direction, spin, colour) output row pair
+    // Thread b < 96 owns one (direction, spin, colour) output row pair and
+    // reads its three link words of each item straight from global memory,
+    // T_LPF items ahead of the item it builds.
+    const int b = tid - 64;
     const bool active = b < 96;
     const int d = b / 12, s = (b % 12) / 3, c = b % 3;
     int so = 0, pr = 0, pi = 0;
@@ -397,192 +388,197 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(const __grid_constant__ C
       pr = a.spin.pr[d][s];
       pi = a.spin.pi[d][s];
     }
-    int q = 0;
-    for (int u = it.u0; u < it.u1 && !*abort; u += it.ustep) {
-      const int ch = u % it.nch;
-      const int j0 = ch * TCH, j1 = min(j0 + TCH, it.vh);
-      for (int j = j0; j < j1; ++j, ++q) {
-        // W buffer q % 2 is free once the MMAs of item q - 2 are done; the link
-        // bundle comes with the item's stage
-        const int st = q % TNS, wb = q & 1;
-        if ((q >= 2 && !mbar_wait(wempty + wb, ((q >> 1) - 1) & 1, abort)) ||
-            !mbar_wait(lfull + st, (q / TNS) & 1, abort)) {
-          atomicCAS(a.err, 0, THOP_ERR_W);
-          *abort = 1;
-          break;
-        }
-        if (active) {
-          unsigned char *W = sW + wb * T_W_BYTES;
-          const uint32_t *L = reinterpret_cast<const uint32_t *>(sL + st * T_L_BYTES) + d * 9 + c * 3;
-          const int nr = (s * 3 + c) * 2;
+    const uint32_t *lk = a.links + (size_t)a.p_out * g.Vh * 72 + d * 9 + c * 3;
+    uint32_t lw[T_LPF][3];
+    TCur pf;
+    bool pf_more = it.first(pf);
 #pragma unroll
-          for (int cc = 0; cc < 3; ++cc) {
-            const uint32_t w = L[cc];
-            // identity block: z = C[c][cc]
-            const int kd = d * 24 + (s * 3 + cc) * 2;
-            const uint32_t cr = w & 0xffffu, ci = w >> 16;
-            *reinterpret_cast<uint32_t *>(W + w_off(kd, nr)) = cr | ((ci ^ 0x8000u) << 16);      // (zr, -zi)
-            *reinterpret_cast<uint32_t *>(W + w_off(kd, nr + 1)) = ci | (cr << 16);             // (zi, zr)
-            // off-diagonal block: z = p C[c][cc], p = pr + i pi in {+-1, +-i}
-            uint32_t zr, zi;
-            if (pr != 0) {
-              const uint32_t sg = pr < 0 ? 0x8000u : 0u;
-              zr = cr ^ sg;
-              zi = ci ^ sg;
-            } else {  // i pi (cr + i ci) = -pi ci + i pi cr
-              const uint32_t sg = pi < 0 ? 0x8000u : 0u;
-              zr = ci ^ 0x8000u ^ sg;
-              zi = cr ^ sg;
-            }
-            const int ko = d * 24 + (so * 3 + cc) * 2;
-            *reinterpret_cast<uint32_t *>(W + w_off(ko, nr)) = zr | ((zi ^ 0x8000u) << 16);
-            *reinterpret_cast<uint32_t *>(W + w_off(ko, nr + 1)) = zi | (zr << 16);
-          }
-        }
-        fence_async_smem();
-        mbar_arrive(wfull + wb);
+    for (int i = 0; i < T_LPF; ++i) {
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) lw[i][cc] = (active && pf_more) ? __ldg(lk + (size_t)pf.j * 72 + cc) : 0u;
+      if (pf_more) pf_more = it.next(pf);
+    }
+    int q = 0;
+    TCur cur;
+    for (bool more = it.first(cur); more && !*abort; more = it.next(cur), ++q) {
+      // W buffer q % 2 is free once the MMAs of item q - 2 are done
+      const int wb = q & 1;
+      if (q >= 2 && !mbar_wait(wempty + wb, ((q >> 1) - 1) & 1, abort)) {
+        atomicCAS(a.err, 0, THOP_ERR_W);
+        *abort = 1;
+        break;
       }
+      uint32_t L[3] = {lw[0][0], lw[0][1], lw[0][2]};
+#pragma unroll
+      for (int i = 0; i + 1 < T_LPF; ++i)
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) lw[i][cc] = lw[i + 1][cc];
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) lw[T_LPF - 1][cc] = (active && pf_more) ? __ldg(lk + (size_t)pf.j * 72 + cc) : 0u;
+      if (pf_more) pf_more = it.next(pf);
+      if (active) {
+        unsigned char *W = sW + wb * T_W_BYTES;
+        const int nr = (s * 3 + c) * 2;
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) {
+          const uint32_t w = L[cc];
+          // identity block: z = C[c][cc]
+          const int kd = d * 24 + (s * 3 + cc) * 2;
+          const uint32_t cr = w & 0xffffu, ci = w >> 16;
+          *reinterpret_cast<uint32_t *>(W + w_off(kd, nr)) = cr | ((ci ^ 0x8000u) << 16);      // (zr, -zi)
+          *reinterpret_cast<uint32_t *>(W + w_off(kd, nr + 1)) = ci | (cr << 16);             // (zi, zr)
+          // off-diagonal block: z = p C[c][cc], p = pr + i pi in {+-1, +-i}
+          uint32_t zr, zi;
+          if (pr != 0) {
+            const uint32_t sg = pr < 0 ? 0x8000u : 0u;
+            zr = cr ^ sg;
+            zi = ci ^ sg;
+          } else {  // i pi (cr + i ci) = -pi ci + i pi cr
+            const uint32_t sg = pi < 0 ? 0x8000u : 0u;
+            zr = ci ^ 0x8000u ^ sg;
+            zi = cr ^ sg;
+          }
+          const int ko = d * 24 + (so * 3 + cc) * 2;
+          *reinterpret_cast<uint32_t *>(W + w_off(ko, nr)) = zr | ((zi ^ 0x8000u) << 16);
+          *reinterpret_cast<uint32_t *>(W + w_off(ko, nr + 1)) = zi | (zr << 16);
+        }
+      }
+      fence_async_smem();
+      mbar_arrive(wfull + wb);
     }
   } else if (warp < 10) {
     // ------------------------------------------------------------ epilogue
     // One thread per right-hand side = TMEM lane; every step is warp-uniform
-    // (the accumulator wait is agreed on with __all_sync).  Each warp stages
-    // its 32 right-hand sides of the BF16 result in shared memory ([24][32])
-    // and writes them with one 2-d TMA store (box 32 x 24).
+    // (the accumulator wait is agreed on with __all_sync).  The item's epilogue
+    // operands are loaded before the accumulator wait.
     const int quarter = warp & 3;
     const int row = 32 * quarter + lane;
     const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
-    // epilogue operands (A, B) of item q + 1 are loaded while item q completes
-    uint32_t na[12], nb[12];
-    auto load_ops = [&](int T, int j) {
-      const size_t e0 = tile_elem(T, g.Vh, j, 0, row);  // real k at e0 + 64 k
-      if (EPI != EPI_PLAIN) {
-#pragma unroll
-        for (int k = 0; k < 12; ++k)
-          na[k] = (uint32_t)__bfloat16_as_ushort(a.A[e0 + (size_t)(2 * k) * 64]) |
-                  ((uint32_t)__bfloat16_as_ushort(a.A[e0 + (size_t)(2 * k + 1) * 64]) << 16);
-      }
-      if (EPI == EPI_DOTR) {
-#pragma unroll
-        for (int k = 0; k < 12; ++k)
-          nb[k] = (uint32_t)__bfloat16_as_ushort(a.B[e0 + (size_t)(2 * k) * 64]) |
-                  ((uint32_t)__bfloat16_as_ushort(a.B[e0 + (size_t)(2 * k + 1) * 64]) << 16);
-      }
-    };
-    if (it.u0 < it.u1) load_ops(a.tlist[it.u0 / it.nch], (it.u0 % it.nch) * TCH);
+    const uint4 *A4 = reinterpret_cast<const uint4 *>(a.A), *B4 = reinterpret_cast<const uint4 *>(a.B);
+    uint4 *O4 = reinterpret_cast<uint4 *>(a.out);
     int q = 0;
-    for (int u = it.u0; u < it.u1 && !*abort; u += it.ustep) {
-      const int T = a.tlist[u / it.nch], ch = u % it.nch;
-      const int j0 = ch * TCH, j1 = min(j0 + TCH, it.vh);
-      const int rhs = T * TR + row;
-      float sre = 0.f, sim = 0.f, snn = 0.f;
-      bool ok = true;
-      for (int j = j0; j < j1; ++j, ++q) {
-        const int acc = q & 1;
-        uint32_t ca[12], cb[12];
+    float sre = 0.f, sim = 0.f, snn = 0.f;
+    TCur cur;
+    for (bool more = it.first(cur); more && !*abort;) {
+      const int T = cur.T, ch = cur.ch;
+      const size_t e0 = tile_chunk(T, g.Vh, cur.j, 0, row);
+      const int acc = q & 1;
+      uint4 ca[3], cb[3];
+      if (EPI != EPI_PLAIN)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ca[c] = A4[e0 + c * TR];
+      if (EPI == EPI_DOTR)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) cb[c] = B4[e0 + c * TR];
+      const bool got = mbar_wait(accf + acc, (q >> 1) & 1, abort);
+      if (!__all_sync(0xffffffffu, got)) {
+        atomicCAS(a.err, 0, THOP_ERR_EPI);
+        *abort = 1;
+        break;
+      }
+      tc_fence_after();
+      float v[24];
+      tc_ld24(tmem + lane_off + acc * TN, v);
+      tc_fence_before();
+      mbar_arrive(acce + acc);
+#pragma unroll
+      for (int k = 0; k < 24; ++k) v[k] *= a.cH;
+      if (EPI != EPI_PLAIN) {
+        const uint32_t *aw = reinterpret_cast<const uint32_t *>(ca);
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-          ca[k] = na[k];
-          cb[k] = nb[k];
-        }
-        // next item: the following site of this unit, else the first site of the next unit
-        if (EPI != EPI_PLAIN) {
-          if (j + 1 < j1) load_ops(T, j + 1);
-          else if (u + it.ustep < it.u1) load_ops(a.tlist[(u + it.ustep) / it.nch], ((u + it.ustep) % it.nch) * TCH);
-        }
-        const bool got = mbar_wait(accf + acc, (q >> 1) & 1, abort);
-        if (!__all_sync(0xffffffffu, got)) {
-          atomicCAS(a.err, 0, THOP_ERR_EPI);
-          *abort = 1;
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        float v[24];
-        tc_ld24(tmem + lane_off + acc * TN, v);
-        tc_fence_before();
-        mbar_arrive(acce + acc);
-#pragma unroll
-        for (int k = 0; k < 24; ++k) v[k] *= a.cH;
-        if (EPI != EPI_PLAIN) {
-#pragma unroll
-          for (int k = 0; k < 12; ++k) {
-            const float a0 = __uint_as_float(ca[k] << 16), a1 = __uint_as_float(ca[k] & 0xffff0000u);
-            v[2 * k] = fmaf(a.cA, a0, v[2 * k]);
-            v[2 * k + 1] = fmaf(a.cA, a1, v[2 * k + 1]);
-            if (EPI == EPI_TS) {  // <out, A> and |out|^2
-              sre = fmaf(v[2 * k], a0, fmaf(v[2 * k + 1], a1, sre));
-              sim = fmaf(v[2 * k], a1, fmaf(-v[2 * k + 1], a0, sim));
-              snn = fmaf(v[2 * k], v[2 * k], fmaf(v[2 * k + 1], v[2 * k + 1], snn));
-            }
+          const float a0 = __uint_as_float(aw[k] << 16), a1 = __uint_as_float(aw[k] & 0xffff0000u);
+          v[2 * k] = fmaf(a.cA, a0, v[2 * k]);
+          v[2 * k + 1] = fmaf(a.cA, a1, v[2 * k + 1]);
+          if (EPI == EPI_TS) {  // <out, A> and |out|^2
+            sre = fmaf(v[2 * k], a0, fmaf(v[2 * k + 1], a1, sre));
+            sim = fmaf(v[2 * k], a1, fmaf(-v[2 * k + 1], a0, sim));
+            snn = fmaf(v[2 * k], v[2 * k], fmaf(v[2 * k + 1], v[2 * k + 1], snn));
           }
-        }
-        if (EPI == EPI_DOTR) {  // <B, out>
-#pragma unroll
-          for (int k = 0; k < 12; ++k) {
-            const float b0 = __uint_as_float(cb[k] << 16), b1 = __uint_as_float(cb[k] & 0xffff0000u);
-            sre = fmaf(b0, v[2 * k], fmaf(b1, v[2 * k + 1], sre));
-            sim = fmaf(b0, v[2 * k + 1], fmaf(-b1, v[2 * k], sim));
-          }
-        }
-        // streaming stores: the results are not read again in this launch
-        {
-          unsigned short *o = reinterpret_cast<unsigned short *>(a.out) + tile_elem(T, g.Vh, j, 0, row);
-#pragma unroll
-          for (int k = 0; k < 24; ++k) __stcs(o + (size_t)k * 64, __bfloat16_as_ushort(__float2bfloat16_rn(v[k])));
         }
       }
-      if (!ok) break;
-      if (EPI == EPI_DOTR || EPI == EPI_TS)
-        a.part[(size_t)rhs * it.nch + ch] = D4S{(double)sre, (double)sim, 0.0, (double)snn};
+      if (EPI == EPI_DOTR) {  // <B, out>
+        const uint32_t *bw = reinterpret_cast<const uint32_t *>(cb);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          const float b0 = __uint_as_float(bw[k] << 16), b1 = __uint_as_float(bw[k] & 0xffff0000u);
+          sre = fmaf(b0, v[2 * k], fmaf(b1, v[2 * k + 1], sre));
+          sim = fmaf(b0, v[2 * k + 1], fmaf(-b1, v[2 * k], sim));
+        }
+      }
+      // streaming stores: the results are not read again in this launch
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          __nv_bfloat162 p2 = __floats2bfloat162_rn(v[8 * c + 2 * h], v[8 * c + 2 * h + 1]);
+          w[h] = *reinterpret_cast<uint32_t *>(&p2);
+        }
+        __stcs(O4 + e0 + c * TR, make_uint4(w[0], w[1], w[2], w[3]));
+      }
+      ++q;
+      const int u_prev = cur.u;
+      more = it.next(cur);
+      if (!more || cur.u != u_prev) {  // the unit's chunk is complete
+        if (EPI == EPI_DOTR || EPI == EPI_TS)
+          a.part[(size_t)(T * TR + row) * it.nch + ch] = D4S{(double)sre, (double)sim, 0.0, (double)snn};
+        sre = sim = snn = 0.f;
+      }
     }
   } else {
-    // ------------------------------------------------------------ cp.async loaders
-    // Neighbours T_NT..7 of each item, 16 bytes per request; a thread's copies of
-    // item q are fenced to the async proxy and announced on full[] once they have
-    // landed, right after the copies of item q + 1 have been issued.
-    const int l = tid - 320;
-    constexpr int PER = (8 - T_NT) * 384 / T_NL;  // 16-byte chunks per thread and item
-    int q = 0, pend = -1;
-    for (int u = it.u0; u < it.u1 && !*abort; u += it.ustep) {
-      const int T = a.tlist[u / it.nch], ch = u % it.nch;
-      const int j0 = ch * TCH, j1 = min(j0 + TCH, it.vh);
-      bool ok = true;
-      for (int j = j0; j < j1; ++j, ++q) {
-        const int s = q % TNS;
-        const bool got = q < TNS || mbar_wait(empty + s, ((q / TNS) - 1) & 1, abort);
-        if (!__all_sync(0xffffffffu, got)) {
-          if (lane == 0) atomicCAS(a.err, 0, THOP_ERR_TMA);
-          *abort = 1;
-          ok = false;
-          break;
-        }
-        int c[4];
-        coords_of(g, a.p_out, j, c);
-        int nb[8 - T_NT];
-#pragma unroll
-        for (int d = T_NT; d < 8; ++d) nb[d - T_NT] = neighbour(g, c, d);
-        const uint32_t sbase = s_u32(sA + s * T_A_BYTES);
-#pragma unroll
-        for (int m = 0; m < PER; ++m) {
-          const int ci = l + T_NL * m, dd = ci / 384, w = ci % 384, row = w >> 3, c16 = w & 7;
-          const uint4 *src = reinterpret_cast<const uint4 *>(a.in) + ((size_t)(T * it.vh + nb[dd]) * 384 + w);
-          cp_async16(sbase + (T_NT + dd) * T_A_NBR + row * 128 + ((c16 ^ (row & 7)) << 4), src);
-        }
-        cp_async_commit();
-        if (pend >= 0) {
-          cp_async_wait1();
-          fence_async_smem();
-          mbar_arrive(full + pend);
-        }
-        pend = s;
+    // ------------------------------------------------------------ loaders
+    // Warp w: TMEM lane quarter w % 4 (the lanes its tcgen05.st may reach) and
+    // the neighbours T_NPW lg .. + T_NPW - 1, lg = (w - 10) / 4, of every item,
+    // one thread per RHS row.  The loads of item q + 1 are in flight while item
+    // q waits for its stage and is written to TMEM; the warp announces the stage
+    // on afull once its stores have completed.
+    const uint4 *in4 = reinterpret_cast<const uint4 *>(a.in);
+    const int quarter = warp & 3, lg = (warp - 10) >> 2;
+    const int row = 32 * quarter + lane;
+    const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
+    uint4 cur_v[3 * T_NPW], nxt_v[3 * T_NPW];
+    int cc[4], cu = -1;
+    auto load = [&](const TCur &c0, uint4 *v) {
+      if (c0.u != cu) {
+        coords_of(g, a.p_out, c0.j, cc);
+        cu = c0.u;
+      } else {
+        coords_next(g, a.p_out, cc);
       }
-      if (!ok) break;
-    }
-    cp_async_wait_all();  // no copy may land after the CTA has left
-    if (pend >= 0) {
-      fence_async_smem();
-      mbar_arrive(full + pend);
+#pragma unroll
+      for (int b = 0; b < T_NPW; ++b) {
+        const size_t e = tile_chunk(c0.T, g.Vh, neighbour(g, cc, T_NPW * lg + b), 0, row);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[3 * b + k] = __ldg(in4 + e + k * TR);
+      }
+    };
+    int q = 0;
+    TCur cur;
+    bool more = it.first(cur);
+    if (more) load(cur, nxt_v);
+    while (more && !*abort) {
+#pragma unroll
+      for (int k = 0; k < 3 * T_NPW; ++k) cur_v[k] = nxt_v[k];
+      more = it.next(cur);
+      if (more) load(cur, nxt_v);
+      const int s = q % TNI;
+      // stage s is free once the MMAs of item q - TNI have completed
+      const bool got = q < TNI || mbar_wait(aempty + s, ((q / TNI) - 1) & 1, abort);
+      if (!__all_sync(0xffffffffu, got)) {
+        if (lane == 0) atomicCAS(a.err, 0, THOP_ERR_LOAD);
+        *abort = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t col = tmem + lane_off + T_ACOL0 + s * T_ACOLS + 12 * T_NPW * lg;
+#pragma unroll
+      for (int b = 0; b < T_NPW; ++b) tc_st12(col + 12 * b, cur_v + 3 * b);
+      tc_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(afull + s);
+      ++q;
     }
   }
   tc_fence_before();

@@ -2,8 +2,6 @@
 // (sloppy.cu).  Layout and kernels are described in tile.cuh.
 #pragma once
 
-#include <cuda.h>
-
 #include "sloppy.cuh"
 
 namespace lqcd {
@@ -11,25 +9,24 @@ namespace lqcd {
 constexpr int TR = 128;  // right-hand sides per tile (the MMA M of the tensor-core hop)
 constexpr int TCH = 32;  // sites per reduction chunk (and work unit) of the tile kernels
 
-// Element (real k, right-hand side r) of site j of tile T in a tile field:
-// [tile][site][half = r / 64][24 reals][64 RHS], so that one site's block of a
-// tile (6 KiB) is 48 rows of 128 bytes, each half a contiguous 3 KiB.
+// A site's block of a tile is [3 chunks][TR right-hand sides][8 reals] (6 KiB):
+// chunk c holds reals 8c .. 8c+7 of every right-hand side as one 16-byte row, so
+// that a warp reading chunk c of 32 consecutive right-hand sides reads 512
+// contiguous bytes and each thread receives 8 consecutive reals of its own RHS.
+// tile_chunk is the uint4 index of (tile T, site j, chunk c, RHS r) in a field,
+// tile_elem the BF16 index of (T, j, real k, r).
+__host__ __device__ inline size_t tile_chunk(int T, int vh, int j, int c, int r) {
+  return (((size_t)T * vh + j) * 3 + c) * TR + r;
+}
 __host__ __device__ inline size_t tile_elem(int T, int vh, int j, int k, int r) {
-  return ((((size_t)T * vh + j) * 2 + (r >> 6)) * 24 + k) * 64 + (r & 63);
+  return tile_chunk(T, vh, j, k >> 3, r) * 8 + (k & 7);
 }
 
-// One BF16 sloppy field in 128-RHS tiles (element order of tile_elem), with the
-// TMA tensor maps of the tensor-core hop (built by tile_field_map) over the 2-d
-// view [ntile * vh * 48 rows][64 RHS]: `map` loads a neighbour block (64 x 48,
-// 128-byte swizzle), `smap` stores an epilogue warp's share of an output block
-// (32 x 24, no swizzle).
+// One BF16 sloppy field in 128-RHS tiles (element order of tile_elem).
 struct TileField {
   __nv_bfloat16 *d = nullptr;
   int ntile = 0, vh = 0;
-  CUtensorMap map, smap;
 };
-
-int tile_field_map(lqcd_ctx *ctx, TileField &f);
 
 // out = cA A + cH (H in) at the sites of parity p_out for the listed tiles;
 // EPI_DOTR adds partials <B, out>, EPI_TS <out, A> and |out|^2 per RHS and
