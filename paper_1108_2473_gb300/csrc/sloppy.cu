@@ -212,45 +212,55 @@ __device__ __forceinline__ void load_link32(const float4 *U, int p, int mu, int 
   u[2][2] = make_float2(c2.x, -c2.y);
 }
 
-template <int MU>
-__device__ __forceinline__ void hop_dir32(const Geom &g, int p_out, const int c[4], int i, const F32F &in, int rhs,
-                                          const float4 *links, float2 acc[4][3]) {
-  float2 v[12], h[2][3], x[2][3], u[3][3], ps[4][3];
+// FP32 hop in direction MU for NR right-hand sides of one site: each link is
+// loaded and reconstructed once and applied to all of them
+template <int MU, int NR>
+__device__ __forceinline__ void hop_dir32n(const Geom &g, int p_out, const int c[4], int i, const F32F &in,
+                                           const int rhs[NR], const float4 *links, float2 acc[NR][4][3]) {
+  float2 u[3][3];
   {  // forward: (1 - gamma_mu) U_mu(x) psi(x + mu)
     int cn[4] = {c[0], c[1], c[2], c[3]};
     cn[MU] = (c[MU] + 1 == g.L[MU]) ? 0 : c[MU] + 1;
-    int sn = site_of(g, cn);
-    in.load(rhs, sn >> 1, v);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) ps[k / 3][k % 3] = v[k];
+    const int sn = site_of(g, cn);
     load_link32(links, p_out, MU, i, g.Vh, u);
-    spin_project<MU, -1>(ps, h);
-    su3_mul<false>(u, h, x);
-    if (MU == 3 && c[3] == g.L[3] - 1) {
 #pragma unroll
-      for (int a = 0; a < 2; ++a)
+    for (int r = 0; r < NR; ++r) {
+      float2 v[12], h[2][3], x[2][3], ps[4][3];
+      in.load(rhs[r], sn >> 1, v);
 #pragma unroll
-        for (int b = 0; b < 3; ++b) x[a][b] = make_float2(-x[a][b].x, -x[a][b].y);
+      for (int k = 0; k < 12; ++k) ps[k / 3][k % 3] = v[k];
+      spin_project<MU, -1>(ps, h);
+      su3_mul<false>(u, h, x);
+      if (MU == 3 && c[3] == g.L[3] - 1) {
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) x[a][b] = make_float2(-x[a][b].x, -x[a][b].y);
+      }
+      spin_accum<MU, -1>(acc[r], x);
     }
-    spin_accum<MU, -1>(acc, x);
   }
   {  // backward: (1 + gamma_mu) U_mu(x - mu)^+ psi(x - mu)
     int cn[4] = {c[0], c[1], c[2], c[3]};
     cn[MU] = (c[MU] == 0) ? g.L[MU] - 1 : c[MU] - 1;
-    int sn = site_of(g, cn);
-    in.load(rhs, sn >> 1, v);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) ps[k / 3][k % 3] = v[k];
+    const int sn = site_of(g, cn);
     load_link32(links, 1 - p_out, MU, sn >> 1, g.Vh, u);
-    spin_project<MU, +1>(ps, h);
-    su3_mul<true>(u, h, x);
-    if (MU == 3 && c[3] == 0) {
 #pragma unroll
-      for (int a = 0; a < 2; ++a)
+    for (int r = 0; r < NR; ++r) {
+      float2 v[12], h[2][3], x[2][3], ps[4][3];
+      in.load(rhs[r], sn >> 1, v);
 #pragma unroll
-        for (int b = 0; b < 3; ++b) x[a][b] = make_float2(-x[a][b].x, -x[a][b].y);
+      for (int k = 0; k < 12; ++k) ps[k / 3][k % 3] = v[k];
+      spin_project<MU, +1>(ps, h);
+      su3_mul<true>(u, h, x);
+      if (MU == 3 && c[3] == 0) {
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) x[a][b] = make_float2(-x[a][b].x, -x[a][b].y);
+      }
+      spin_accum<MU, +1>(acc[r], x);
     }
-    spin_accum<MU, +1>(acc, x);
   }
 }
 
@@ -349,51 +359,64 @@ __device__ __forceinline__ void group_reduce_store2(D4S v0, D4S v1, D4S *dst0, D
 
 // FP32 hopping term: out = cA A + cB B + cH (H in) at the sites of parity p_out.
 // EPI_PLAIN: A, B unused.  EPI_AXPY: B unused.  EPI_RES: partial |out|^2.
+// The FP32 hopping term on two right-hand sides per thread (list entries 2j and
+// 2j + 1; with an odd count the last thread recomputes entry 2j for its second
+// slot and stores nothing for it), which halves the link loads and the
+// reconstruction of the third link row per right-hand side.
 template <int EPI>
-__global__ void __launch_bounds__(ST) k_hop32(Geom g, int p_out, const float4 *links, F32F in, F32F out, F32F A,
-                                              F32F B, float cA, float cB, float cH, const int *list,
-                                              const int *count, D4S *part, int nbx) {
-  const int n_items = *count * nbx;
+__global__ void __launch_bounds__(ST, 4) k_hop32x2(Geom g, int p_out, const float4 *links, F32F in, F32F out, F32F A,
+                                                F32F B, float cA, float cB, float cH, const int *list,
+                                                const int *count, D4S *part, int nbx) {
+  const int cnt = *count;
+  const int n_items = (cnt + 1) / 2 * nbx;
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const int rhs = list[w / nbx], sb = w % nbx;
+    const int j = (w / nbx) * 2, sb = w % nbx;
+    const bool two = j + 1 < cnt;
+    const int rhs[2] = {list[j], two ? list[j + 1] : list[j]};
     const int i = sb * ST + threadIdx.x;
-    D4S red = {0, 0, 0, 0};
+    D4S red[2] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
     if (i < g.Vh) {
       int c[4];
       coords_of(g, p_out, i, c);
-      float2 acc[4][3];
+      float2 acc[2][4][3];
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int r = 0; r < 2; ++r)
 #pragma unroll
-        for (int b = 0; b < 3; ++b) acc[a][b] = make_float2(0.f, 0.f);
-      hop_dir32<0>(g, p_out, c, i, in, rhs, links, acc);
-      hop_dir32<1>(g, p_out, c, i, in, rhs, links, acc);
-      hop_dir32<2>(g, p_out, c, i, in, rhs, links, acc);
-      hop_dir32<3>(g, p_out, c, i, in, rhs, links, acc);
-      float2 o[12];
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int k = 0; k < 12; ++k) o[k] = make_float2(cH * acc[k / 3][k % 3].x, cH * acc[k / 3][k % 3].y);
-      if (EPI != EPI_PLAIN) {
-        float2 a[12];
-        A.load(rhs, i, a);
+          for (int b = 0; b < 3; ++b) acc[r][a][b] = make_float2(0.f, 0.f);
+      hop_dir32n<0, 2>(g, p_out, c, i, in, rhs, links, acc);
+      hop_dir32n<1, 2>(g, p_out, c, i, in, rhs, links, acc);
+      hop_dir32n<2, 2>(g, p_out, c, i, in, rhs, links, acc);
+      hop_dir32n<3, 2>(g, p_out, c, i, in, rhs, links, acc);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) o[k] = make_float2(fmaf(cA, a[k].x, o[k].x), fmaf(cA, a[k].y, o[k].y));
-      }
-      if (EPI == EPI_RES) {
-        float2 b[12];
-        B.load(rhs, i, b);
+      for (int r = 0; r < 2; ++r) {
+        float2 o[12];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) o[k] = make_float2(fmaf(cB, b[k].x, o[k].x), fmaf(cB, b[k].y, o[k].y));
-      }
-      out.store(rhs, i, o);
-      if (EPI == EPI_RES) {
-        float nn = 0.f;
+        for (int k = 0; k < 12; ++k) o[k] = make_float2(cH * acc[r][k / 3][k % 3].x, cH * acc[r][k / 3][k % 3].y);
+        if (EPI != EPI_PLAIN) {
+          float2 a[12];
+          A.load(rhs[r], i, a);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) nn += o[k].x * o[k].x + o[k].y * o[k].y;
-        red.c = nn;
+          for (int k = 0; k < 12; ++k) o[k] = make_float2(fmaf(cA, a[k].x, o[k].x), fmaf(cA, a[k].y, o[k].y));
+        }
+        if (EPI == EPI_RES) {
+          float2 b[12];
+          B.load(rhs[r], i, b);
+#pragma unroll
+          for (int k = 0; k < 12; ++k) o[k] = make_float2(fmaf(cB, b[k].x, o[k].x), fmaf(cB, b[k].y, o[k].y));
+        }
+        if (r == 0 || two) out.store(rhs[r], i, o);
+        if (EPI == EPI_RES) {
+          float nn = 0.f;
+#pragma unroll
+          for (int k = 0; k < 12; ++k) nn += o[k].x * o[k].x + o[k].y * o[k].y;
+          red[r].c = nn;
+        }
       }
     }
-    if (EPI == EPI_RES) block_reduce_store(red, part + (size_t)rhs * nbx + sb);
+    if (EPI == EPI_RES)
+      block_reduce_store2(red[0], red[1], part + (size_t)rhs[0] * nbx + sb, part + (size_t)rhs[1] * nbx + sb);
   }
 }
 
@@ -1951,7 +1974,7 @@ struct MixedRun : RunIface {
     } else {
       KL k_cvt32to32_both<<<G, ST, 0, st>>>(g, ss->r32, b32, o32, sb.scale, sb.cyc_list, counts + 2, nbx);
     }
-    KL k_hop32<EPI_AXPY><<<G, ST, 0, st>>>(g, 0, ctx->U32, o32, b32, b32, b32, 1.f, 0.f, kappa, sb.cyc_list,
+    KL k_hop32x2<EPI_AXPY><<<G, ST, 0, st>>>(g, 0, ctx->U32, o32, b32, b32, b32, 1.f, 0.f, kappa, sb.cyc_list,
                                            counts + 2, nullptr, nbx);
     Ops::copy(st, G, vh, sb.flags, b32, r, r, false, x32, true, sb.cyc_pairs, counts + 4, sb.part, nb);
     KL k_sfin_init<<<(int)hl.size(), 32, 0, st>>>(sb.sc, sb.flags, sb.cyc_list, counts + 2, sb.part, nb, floor2);
@@ -2010,9 +2033,9 @@ struct MixedRun : RunIface {
                                             delta * delta, p.max_iter, gs);
       KL k_build_lists<<<1, 1024, 0, q>>>(nrhs, sb.flags, gs, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
       // reliable update in FP32: r32 = b32 - x32 + kappa^2 H_eo H_oe x32
-      KL k_hop32<EPI_PLAIN><<<G, ST, 0, q>>>(g, 1, L32, x32, t32, t32, t32, 0.f, 0.f, 1.f, sb.ru_list, counts + 1,
+      KL k_hop32x2<EPI_PLAIN><<<G, ST, 0, q>>>(g, 1, L32, x32, t32, t32, t32, 0.f, 0.f, 1.f, sb.ru_list, counts + 1,
                                              nullptr, nbx);
-      KL k_hop32<EPI_RES><<<G, ST, 0, q>>>(g, 0, L32, t32, r32, b32, x32, 1.f, -1.f, k2, sb.ru_list, counts + 1,
+      KL k_hop32x2<EPI_RES><<<G, ST, 0, q>>>(g, 0, L32, t32, r32, b32, x32, 1.f, -1.f, k2, sb.ru_list, counts + 1,
                                            sb.part, nbx);
       KL k_sfin_ru<<<nrhs, 32, 0, q>>>(sb.sc, sb.flags, sb.ru_list, counts + 1, sb.part, nbx, p.max_iter);
       KL k_build_lists<<<1, 1024, 0, q>>>(nrhs, sb.flags, gs, sb.act_pairs, sb.ru_list, sb.ru_pairs, counts);
@@ -2050,7 +2073,7 @@ struct MixedRun : RunIface {
   int cycle_end() {
     int *counts = sb.counts;
     // odd half of the correction: e_o = o32 + kappa H_oe x32; x += |r| e
-    KL k_hop32<EPI_AXPY><<<G, ST, 0, st>>>(g, 1, ctx->U32, x32, o32, o32, o32, 1.f, 0.f, kappa, sb.cyc_list,
+    KL k_hop32x2<EPI_AXPY><<<G, ST, 0, st>>>(g, 1, ctx->U32, x32, o32, o32, o32, 1.f, 0.f, kappa, sb.cyc_list,
                                            counts + 2, nullptr, nbx);
     KL k_accum_df_both<<<G, ACC_SITES * 2, 0, st>>>(g, x32, o32, ss->xdf, sb.unscale, sb.cyc_list, counts + 2,
                                                     (vh + ACC_SITES - 1) / ACC_SITES);
