@@ -199,8 +199,19 @@ int lqcd_batch_destroy(lqcd_batch *batch);
  * every timing is printed to stderr; LQCD_HOP_VARIANT=<digit> overrides the
  * variant the solves use (for tests and profiling); LQCD_NO_GRAPH makes the
  * solver launch its inner iterations directly instead of through CUDA graphs
- * (kernel profilers do not see kernels inside graphs with conditional nodes). */
+ * (kernel profilers do not see kernels inside graphs with conditional nodes).
+ * The timings assume every right-hand side active in every iteration; after
+ * each BF16 mixed solve of nrhs right-hand sides the choice between the two
+ * layouts is revised from the solve's per-RHS iteration counts, since a layout
+ * keeps computing a pair or a tile until its slowest member has converged (each
+ * layout's time per iteration is weighted by the mean over its groups of the
+ * group's largest iteration count). */
 int lqcd_autotune(lqcd_ctx *ctx, int nrhs, int precision, int *best_blocks_per_sm, int *best_hop_variant);
+/* The launch choice later solves of (nrhs, precision) will use -- after the
+ * autotuner, any revision by earlier solves and the LQCD_HOP_VARIANT override --
+ * as for lqcd_autotune (host ints, each may be NULL; hop variant 5 is the tile
+ * layout).  Host only; LQCD_ERR_INVALID for a null ctx. */
+int lqcd_tuned_choice(const lqcd_ctx *ctx, int nrhs, int precision, int *blocks_per_sm, int *hop_variant);
 
 /* Point sources e_{x,spin,colour} (Sec. II: exact all-to-all propagator from
  * one inversion per site, spin and colour).  sites: host array of n_sites

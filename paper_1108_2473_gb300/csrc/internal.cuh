@@ -198,6 +198,15 @@ struct lqcd_ctx {
   int prof_prec = 0;
   // autotuned launch grid (blocks per SM) per (nrhs, precision)
   std::vector<std::pair<long long, int>> tuned;
+  // the autotuner's timings per key: best pair-layout code and its ms per inner
+  // iteration, ms of the tile layout (< 0 if not timed); the choice is revised
+  // after every solve from its per-RHS iteration counts
+  struct TuneRec {
+    long long key;
+    int pair_code;
+    float pair_ms, tile_ms;
+  };
+  std::vector<TuneRec> tune_ms;
 };
 
 namespace lqcd {

@@ -2166,6 +2166,33 @@ static void count_loop_launches(RunIface *run, const SloppyState *ss) {
 // configuration; the host synchronises once per cycle.  While profiling the
 // iterations are launched directly, four per host poll, so that every hop
 // launch gets its own events.
+// Revision of the tuned layout after a solve.  The autotuner times inner
+// iterations with every right-hand side active, but a layout keeps computing a
+// group -- a pair (2 RHS) or a tile (TR RHS) -- until its slowest member has
+// converged.  With the solve's per-RHS iteration counts, a layout's cost is its
+// time per full iteration times sum_groups(size x max iterations in the group) /
+// (its groups' total size); the cheaper layout becomes the choice for the key.
+static void revise_layout(lqcd_ctx *ctx, int nrhs, int precision, const lqcd_solve_stats *stats) {
+  const long long key = (long long)nrhs * 8 + precision;
+  const lqcd_ctx::TuneRec *t = nullptr;
+  for (auto &r : ctx->tune_ms)
+    if (r.key == key) t = &r;
+  if (!t || t->tile_ms < 0.f) return;
+  auto weighted = [&](int gsz) {
+    double w = 0.0;
+    for (int g0 = 0; g0 < nrhs; g0 += gsz) {
+      int m = 0;
+      for (int i = g0; i < std::min(nrhs, g0 + gsz); ++i) m = std::max(m, stats[i].iterations);
+      w += (double)gsz * m;
+    }
+    return w / (double)(((nrhs + gsz - 1) / gsz) * gsz);
+  };
+  const double pair_cost = t->pair_ms * weighted(2), tile_cost = t->tile_ms * weighted(TR);
+  const int code = tile_cost < pair_cost ? 10 + TILE_VARIANT : t->pair_code;
+  for (auto &kv : ctx->tuned)
+    if (kv.first == key) kv.second = code;
+}
+
 static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const lqcd_solver_params &p,
                        lqcd_solve_stats *stats, cudaStream_t st, double t0) {
   std::unique_ptr<RunIface> run(make_run(ctx, b, x, nrhs, p, stats, st, t0));
@@ -2211,7 +2238,9 @@ static int mixed_block(lqcd_ctx *ctx, const double2 *b, double2 *x, int nrhs, co
     rc = run->poll();
     if (rc) return rc;
   }
-  return run->finish();
+  rc = run->finish();
+  if (p.precision == LQCD_PREC_MIXED_BF16) revise_layout(ctx, nrhs, p.precision, stats);
+  return rc;
 }
 
 // Uneven batch: one CUDA graph with a branch per lattice (k_loop_init -> WHILE
@@ -2512,13 +2541,22 @@ static int autotune_hop(lqcd_ctx *ctx, int nrhs, int precision, int *best, int *
       if (rc) return rc;
       consider(c * 10 + variant, ms);
     }
+  const int pair_code = best_code;
+  const float pair_ms = best_ms;
+  float tile_ms = -1.f;
   if (tiles) {
-    float ms = 0.f;
-    rc = time_code<TileOps>(ctx, nrhs, precision, 10 + TILE_VARIANT, &ms);
+    rc = time_code<TileOps>(ctx, nrhs, precision, 10 + TILE_VARIANT, &tile_ms);
     if (rc) return rc;
-    consider(10 + TILE_VARIANT, ms);
+    consider(10 + TILE_VARIANT, tile_ms);
   }
   long long key = (long long)nrhs * 8 + precision;
+  bool rec = false;
+  for (auto &t : ctx->tune_ms)
+    if (t.key == key) {
+      t = lqcd_ctx::TuneRec{key, pair_code, pair_ms, tile_ms};
+      rec = true;
+    }
+  if (!rec) ctx->tune_ms.push_back(lqcd_ctx::TuneRec{key, pair_code, pair_ms, tile_ms});
   bool found = false;
   for (auto &kv : ctx->tuned)
     if (kv.first == key) {
@@ -2532,6 +2570,16 @@ static int autotune_hop(lqcd_ctx *ctx, int nrhs, int precision, int *best, int *
 }
 
 }  // namespace lqcd
+
+extern "C" int lqcd_tuned_choice(const lqcd_ctx *ctx, int nrhs, int precision, int *blocks_per_sm,
+                                 int *hop_variant) {
+  LQCD_TRACE("lqcd_tuned_choice");
+  if (!ctx) return set_error(nullptr, LQCD_ERR_INVALID, "lqcd_tuned_choice: null context");
+  const int code = tuned_code(ctx, nrhs, precision);
+  if (blocks_per_sm) *blocks_per_sm = code / 10;
+  if (hop_variant) *hop_variant = code % 10;
+  return LQCD_OK;
+}
 
 extern "C" int lqcd_autotune(lqcd_ctx *ctx, int nrhs, int precision, int *best_blocks_per_sm,
                              int *best_hop_variant) {

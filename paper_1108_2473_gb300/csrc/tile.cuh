@@ -17,22 +17,25 @@
 // one M = 128, N = 32 (24 used), K = 192 product per (site, tile): twelve
 // tcgen05.mma kind::f16 instructions (BF16 in, FP32 accumulate in TMEM).
 //
-// Data flow.  The neighbour blocks never pass through shared memory: loader
-// warps read them straight into registers (one thread per RHS row; chunk c of
-// 32 right-hand sides is one 512-byte warp load) and write them with
-// tcgen05.st into one of TNI tensor-memory stages of 96 columns (lane = RHS,
-// column 12 d + w = reals 2w, 2w+1 of neighbour d); the MMAs take A from TMEM
-// ([a-tmem] operand) and W from shared memory.  Measured on GB300, copies into
-// shared memory by the bulk-copy engine or by cp.async kept the tensor core
-// waiting (a bulk copy of a neighbour block landed thousands of cycles after
-// it was issued under this load), whereas the loader warps run several items
-// ahead of the MMAs.
+// Data flow.  In this layout a site's block of a tile is already the canonical
+// K-major, no-swizzle MMA operand: core matrices of 8 right-hand sides x 16 B,
+// 128 B apart, and the K-chunks of 8 reals 2 KiB apart.  The eight neighbour
+// blocks of an item, copied side by side into a shared-memory stage by eight
+// bulk copies (cp.async.bulk, 6 KiB each), form the whole A = [128 RHS][192],
+// which the twelve MMAs address with one descriptor advanced by 4 KiB per K step.
+// TNI = 4 stages keep up to 192 KiB of copies in flight per SM without holding
+// registers.  Each item's MMAs end in one tcgen05.commit, to an item-done
+// barrier that every reuse waits on (the stage, the W buffer, the accumulator):
+// each commit costs the issuing thread ~85 cycles, so per-buffer commits (up to
+// eleven per item in earlier versions) had kept the tensor core waiting.
 //
-// Roles inside one persistent CTA per SM, all walking the same (tile, site)
-// item sequence:
-//   * warp 1: TMEM allocation (two FP32 accumulators of TN columns and the TNI
-//     stages); one thread issues the twelve MMAs of an item and commits the
-//     stage, W and accumulator barriers;
+// Roles inside one persistent CTA per SM (223 KiB of shared memory, 64 TMEM
+// columns), all walking the same (tile, site) item sequence:
+//   * warp 0: bulk-copy producer; lane d < 8 copies neighbour block d of item q
+//     into stage q % TNI once item q - TNI is done, after lane 0 has announced
+//     the stage's 48 KiB on its full barrier;
+//   * warp 1: TMEM allocation (two FP32 accumulators of TN columns); one thread
+//     issues the twelve MMAs of an item and one commit;
 //   * warps 2-5: build W (K-major, no swizzle) into a ring of two W buffers
 //     from the site's eight BF16 colour matrices, whose words each builder
 //     thread loads T_LPF items ahead; entries of zero spin blocks are written
@@ -40,14 +43,11 @@
 //   * warps 6-9 (one thread per right-hand side = TMEM lane): read the 24 FP32
 //     results, apply the epilogue (out = cA A + cH D, optional dot products),
 //     store BF16 (streaming stores) and accumulate per-RHS partial sums over
-//     chunks of TCH sites;
-//   * warps 10-25: loaders; warp w serves TMEM lane quarter w % 4 and the
-//     neighbours 2 lg, 2 lg + 1 of every item, lg = (w - 10) / 4, with the loads
-//     of the next item issued before the TMEM stores of the current one;
-//   * warp 0: work counters for the profiling hook only.
+//     chunks of TCH sites.
 // Every wait on an mbarrier is bounded; a wait that runs out sets an error
-// code, the other roles stop at their next wait, issued MMAs are waited for
-// (bounded by time only), and TMEM is released before the kernel returns.
+// code, the other roles stop at their next wait, bulk copies in flight and
+// issued MMAs are waited for (bounded by time only), and TMEM is released
+// before the kernel returns.
 #pragma once
 
 #include "tile_api.cuh"
@@ -57,7 +57,6 @@ namespace lqcd {
 constexpr int TK = 192;   // MMA K per site: 8 directions x 24 reals
 constexpr int TN = 32;    // MMA N: 24 output reals, padded
 constexpr int T_W_BYTES = (TK / 8) * 512;      // 12 KiB: 24 K-chunks x 4 N-groups x 128 B
-constexpr int T_TMEM_COLS = 512;               // accumulators and loaded neighbour blocks
 
 // error codes written by the tile hop when a bounded wait runs out
 enum { THOP_ERR_LOAD = 1, THOP_ERR_W = 2, THOP_ERR_MMA = 3, THOP_ERR_ACC = 4, THOP_ERR_EPI = 5 };
@@ -133,6 +132,14 @@ __device__ __forceinline__ bool mbar_wait_drain(uint64_t *b, uint32_t parity) {
     if (global_ns() - t0 > T_WAIT_NS) return false;
   return true;
 }
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(s_u32(bar))
+               : "memory");
+}
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -155,24 +162,6 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t
       "l"(adesc), "l"(bdesc), "r"(T_IDESC), "r"(accumulate)
       : "memory");
 }
-// D (+)= A B with A in tensor memory (lane = row, two BF16 of K per column)
-__device__ __forceinline__ void tc_mma_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}" ::"r"(tmem_d),
-      "r"(tmem_a), "l"(bdesc), "r"(T_IDESC), "r"(accumulate)
-      : "memory");
-}
-// one neighbour block of one RHS row (12 columns) from registers into TMEM
-__device__ __forceinline__ void tc_st12(uint32_t taddr, const uint4 v[3]) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0].x),
-               "r"(v[0].y), "r"(v[0].z), "r"(v[0].w), "r"(v[1].x), "r"(v[1].y), "r"(v[1].z), "r"(v[1].w)
-               : "memory");
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr + 8), "r"(v[2].x),
-               "r"(v[2].y), "r"(v[2].z), "r"(v[2].w)
-               : "memory");
-}
-__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_commit(uint64_t *bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_u32(bar))
                : "memory");
@@ -260,31 +249,25 @@ __device__ __forceinline__ void coords_next(const Geom &g, int p, int c[4]) {
   c[0] = 2 * xh + ((c[1] + c[2] + c[3] + p) & 1);
 }
 
-// Loader warps: NG groups of four (one warp per TMEM lane quarter), each group
-// NPW neighbours of every item; TNI items in flight (TMEM stages).
-constexpr int TNI = 4;
-constexpr int T_NPW = 2;                          // neighbours per loader warp
-constexpr int T_NG = 8 / T_NPW;                   // loader warp groups
-constexpr int T_LW = 4 * T_NG;                    // loader warps (10 .. 10 + T_LW - 1)
-constexpr int T_THREADS = 320 + 32 * T_LW;
-constexpr int T_ACOLS = 8 * 12;                   // TMEM columns of one item's neighbour blocks
-constexpr int T_ACOL0 = 2 * TN;                   // after the two accumulators
-constexpr int T_LPF = 4;                          // items of link words the W builders hold in registers
-// the CTA needs ~26 KiB of shared memory; requesting more than half of an SM's
-// keeps it alone on its SM, as the TMEM allocation of all 512 columns requires
-constexpr int T_SMEM = 116 * 1024;
-static_assert(1024 + 2 * T_W_BYTES + 1024 <= T_SMEM, "tile hop shared memory");
-static_assert(T_ACOL0 + TNI * T_ACOLS <= T_TMEM_COLS, "tile hop tensor memory");
-static_assert(T_THREADS <= 1024, "tile hop threads");
+// Stages in shared memory, one bulk copy per neighbour block, one commit per item.
+constexpr int TNI = 4;                          // items in flight (shared-memory stages)
+constexpr int T_BLK_BYTES = 3 * TR * 16;        // one site block of a tile: 6 KiB
+constexpr int T_A_BYTES = 8 * T_BLK_BYTES;      // an item's eight neighbour blocks side by side: 48 KiB
+constexpr int T_DONE = 16;                      // item-done barriers (deeper than any role lags)
+constexpr int T_THREADS = 320;
+constexpr int T_TMEM_COLS = 64;                 // two FP32 accumulators of TN columns
+constexpr int T_LPF = 4;                        // items of link words the W builders hold in registers
+constexpr int T_SMEM = 1024 + TNI * T_A_BYTES + 2 * T_W_BYTES + 1024;
+static_assert(T_SMEM <= 227 * 1024, "tile hop shared memory");
 
 template <int EPI>
 __global__ void __launch_bounds__(T_THREADS, 1) k_thop(THopArgs a) {
   extern __shared__ __align__(1024) unsigned char t_smem_raw[];
   unsigned char *base = (unsigned char *)(((uintptr_t)t_smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char *sW = base;  // 2 x 12 KiB W ring
+  unsigned char *sA = base;                       // TNI x 48 KiB
+  unsigned char *sW = sA + TNI * T_A_BYTES;       // 2 x 12 KiB W ring
   uint64_t *bars = (uint64_t *)(sW + 2 * T_W_BYTES);
-  uint64_t *afull = bars, *aempty = bars + TNI;
-  uint64_t *accf = bars + 2 * TNI, *acce = accf + 2, *wfull = accf + 4, *wempty = accf + 6, *drain = accf + 8;
+  uint64_t *full = bars, *done = bars + TNI, *acce = done + T_DONE, *wfull = acce + 2, *drain = wfull + 2;
   uint32_t *tslot = (uint32_t *)(drain + 1);
   volatile int *abort = (volatile int *)(tslot + 1);
 
@@ -294,18 +277,13 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(THopArgs a) {
   TItems it;
   it.init(count, a.nch, g.Vh, a.tlist);
 
-  // zero the W buffers (zero spin blocks stay zero), set up barriers and TMEM
   for (int i = tid; i < 2 * T_W_BYTES / 16; i += T_THREADS) reinterpret_cast<uint4 *>(sW)[i] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
-    for (int s = 0; s < TNI; ++s) {
-      mbar_init(afull + s, T_LW);  // one arrival per loader warp
-      mbar_init(aempty + s, 1);
-    }
+    for (int s = 0; s < TNI; ++s) mbar_init(full + s, 1);
+    for (int s = 0; s < T_DONE; ++s) mbar_init(done + s, 1);
     for (int b = 0; b < 2; ++b) {
-      mbar_init(accf + b, 1);
       mbar_init(acce + b, 128);
       mbar_init(wfull + b, 128);
-      mbar_init(wempty + b, 1);
     }
     mbar_init(drain, 1);
     *abort = 0;
@@ -324,13 +302,44 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(THopArgs a) {
   const uint32_t tmem = *tslot;
 
   if (warp == 0) {
-    // ------------------------------------------------------------ bookkeeping
+    // ------------------------------------------------------------ bulk-copy producer
+    // lane d < 8 copies neighbour block d of item q into stage q % TNI once the
+    // MMAs of item q - TNI (the stage's last user) have completed; lane 0 first
+    // announces the stage's 48 KiB on its full barrier.
     if (lane == 0 && a.prof)
       for (int v = it.u0; v < it.u1; v += it.ustep) {
         const int T = a.tlist[v / it.nch], ch = v % it.nch;
         atomicAdd(a.prof + EPI, (unsigned long long)(min(ch * TCH + TCH, it.vh) - ch * TCH) *
                                     (unsigned long long)min(TR, a.nrhs - T * TR));
       }
+    const uint4 *in4 = reinterpret_cast<const uint4 *>(a.in);
+    int q = 0, last_q = -1, cu = -1, cc[4];
+    TCur cur;
+    for (bool more = it.first(cur); more && !*abort; more = it.next(cur), ++q) {
+      const int st = q % TNI, qr = q - TNI;
+      const bool got = qr < 0 || lane > 0 || mbar_wait(done + qr % T_DONE, (qr / T_DONE) & 1, abort);
+      if (!__all_sync(0xffffffffu, got)) {
+        if (lane == 0) atomicCAS(a.err, 0, THOP_ERR_LOAD);
+        *abort = 1;
+        break;
+      }
+      if (cur.u != cu) {
+        coords_of(g, a.p_out, cur.j, cc);
+        cu = cur.u;
+      } else {
+        coords_next(g, a.p_out, cc);
+      }
+      if (lane == 0) mbar_arrive_tx(full + st, T_A_BYTES);
+      __syncwarp();
+      if (lane < 8) {
+        const size_t src = tile_chunk(cur.T, g.Vh, neighbour(g, cc, lane), 0, 0);
+        bulk_load(s_u32(sA + (size_t)st * T_A_BYTES + lane * T_BLK_BYTES), in4 + src, T_BLK_BYTES, full + st);
+      }
+      last_q = q;
+    }
+    // copies in flight must land before the CTA exits (normally already consumed)
+    if (lane == 0)
+      for (int qq = max(0, last_q - TNI + 1); qq <= last_q; ++qq) mbar_wait_drain(full + qq % TNI, (qq / TNI) & 1);
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
@@ -338,7 +347,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(THopArgs a) {
       bool issued = false;
       TCur cur;
       for (bool more = it.first(cur); more && !*abort; more = it.next(cur), ++q) {
-        const int grp = q % TNI, acc = q & 1;
+        const int st = q % TNI, acc = q & 1;
         if (!mbar_wait(wfull + acc, (q >> 1) & 1, abort)) {
           atomicCAS(a.err, 0, THOP_ERR_W);
           *abort = 1;
@@ -349,26 +358,24 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(THopArgs a) {
           *abort = 1;
           break;
         }
-        if (!mbar_wait(afull + grp, (q / TNI) & 1, abort)) {
+        if (!mbar_wait(full + st, (q / TNI) & 1, abort)) {
           atomicCAS(a.err, 0, THOP_ERR_MMA);
           *abort = 1;
           break;
         }
+        // K = 192 in twelve steps of 16: step k reads K-chunks 2k, 2k + 1 of the
+        // eight neighbour blocks side by side (chunk c at 2 KiB c: LBO 2 KiB, SBO
+        // 128 B, no swizzle) and W K-chunks 2k, 2k + 1 (LBO 512 B, SBO 128 B); the
+        // descriptors' start fields advance by 4096 / 16 and 1024 / 16 per step
+        const uint64_t ad = smem_desc(s_u32(sA + (size_t)st * T_A_BYTES), 2048, 128, 0);
+        const uint64_t bd = smem_desc(s_u32(sW + acc * T_W_BYTES), 512, 128, 0);
+        const uint32_t dacc = tmem + acc * TN;
         tc_fence_after();
-        // K = 192 in twelve steps of 16: step k reads K-chunks 2k, 2k + 1, i.e.
-        // TMEM columns 8k .. 8k+7 of the item's stage (chunk 3 d + c of
-        // neighbour d at columns 12 d + 4 c), and W K-chunks 2k, 2k + 1 (LBO
-        // 512 B, SBO 128 B)
-        const uint32_t waddr = s_u32(sW + acc * T_W_BYTES), tbase = tmem + T_ACOL0 + grp * T_ACOLS;
 #pragma unroll
-        for (int k = 0; k < 12; ++k)
-          tc_mma_ts(tmem + acc * TN, tbase + 8 * k, smem_desc(waddr + k * 1024, 512, 128, 0), k > 0);
-        tc_commit(aempty + grp);
-        tc_commit(wempty + acc);
-        tc_commit(accf + acc);
+        for (int k = 0; k < 12; ++k) tc_mma(dacc, ad + (uint64_t)(256 * k), bd + (uint64_t)(64 * k), k > 0);
+        tc_commit(done + q % T_DONE);  // the stage, W buffer and accumulator wait on this
         issued = true;
       }
-      // every MMA issued must have completed before TMEM is released
       if (issued) {
         tc_commit(drain);
         mbar_wait_drain(drain, 0);
@@ -376,9 +383,6 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(THopArgs a) {
     }
   } else if (warp < 6) {
     // ------------------------------------------------------------ W builders
-    // Thread b < 96 owns one (direction, spin, colour) output row pair and
-    // reads its three link words of each item straight from global memory,
-    // T_LPF items ahead of the item it builds.
     const int b = tid - 64;
     const bool active = b < 96;
     const int d = b / 12, s = (b % 12) / 3, c = b % 3;
@@ -402,8 +406,8 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(THopArgs a) {
     TCur cur;
     for (bool more = it.first(cur); more && !*abort; more = it.next(cur), ++q) {
       // W buffer q % 2 is free once the MMAs of item q - 2 are done
-      const int wb = q & 1;
-      if (q >= 2 && !mbar_wait(wempty + wb, ((q >> 1) - 1) & 1, abort)) {
+      const int wb = q & 1, qr = q - 2;
+      if (qr >= 0 && !mbar_wait(done + qr % T_DONE, (qr / T_DONE) & 1, abort)) {
         atomicCAS(a.err, 0, THOP_ERR_W);
         *abort = 1;
         break;
@@ -446,11 +450,11 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(THopArgs a) {
       fence_async_smem();
       mbar_arrive(wfull + wb);
     }
-  } else if (warp < 10) {
+  } else {
     // ------------------------------------------------------------ epilogue
     // One thread per right-hand side = TMEM lane; every step is warp-uniform
-    // (the accumulator wait is agreed on with __all_sync).  The item's epilogue
-    // operands are loaded before the accumulator wait.
+    // (the wait is agreed on with __all_sync).  The item's epilogue operands are
+    // loaded before the wait for its MMAs.
     const int quarter = warp & 3;
     const int row = 32 * quarter + lane;
     const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
@@ -470,7 +474,7 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(THopArgs a) {
       if (EPI == EPI_DOTR)
 #pragma unroll
         for (int c = 0; c < 3; ++c) cb[c] = B4[e0 + c * TR];
-      const bool got = mbar_wait(accf + acc, (q >> 1) & 1, abort);
+      const bool got = mbar_wait(done + q % T_DONE, (q / T_DONE) & 1, abort);
       if (!__all_sync(0xffffffffu, got)) {
         atomicCAS(a.err, 0, THOP_ERR_EPI);
         *abort = 1;
@@ -525,60 +529,6 @@ __global__ void __launch_bounds__(T_THREADS, 1) k_thop(THopArgs a) {
           a.part[(size_t)(T * TR + row) * it.nch + ch] = D4S{(double)sre, (double)sim, 0.0, (double)snn};
         sre = sim = snn = 0.f;
       }
-    }
-  } else {
-    // ------------------------------------------------------------ loaders
-    // Warp w: TMEM lane quarter w % 4 (the lanes its tcgen05.st may reach) and
-    // the neighbours T_NPW lg .. + T_NPW - 1, lg = (w - 10) / 4, of every item,
-    // one thread per RHS row.  The loads of item q + 1 are in flight while item
-    // q waits for its stage and is written to TMEM; the warp announces the stage
-    // on afull once its stores have completed.
-    const uint4 *in4 = reinterpret_cast<const uint4 *>(a.in);
-    const int quarter = warp & 3, lg = (warp - 10) >> 2;
-    const int row = 32 * quarter + lane;
-    const uint32_t lane_off = (uint32_t)(32 * quarter) << 16;
-    uint4 cur_v[3 * T_NPW], nxt_v[3 * T_NPW];
-    int cc[4], cu = -1;
-    auto load = [&](const TCur &c0, uint4 *v) {
-      if (c0.u != cu) {
-        coords_of(g, a.p_out, c0.j, cc);
-        cu = c0.u;
-      } else {
-        coords_next(g, a.p_out, cc);
-      }
-#pragma unroll
-      for (int b = 0; b < T_NPW; ++b) {
-        const size_t e = tile_chunk(c0.T, g.Vh, neighbour(g, cc, T_NPW * lg + b), 0, row);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) v[3 * b + k] = __ldg(in4 + e + k * TR);
-      }
-    };
-    int q = 0;
-    TCur cur;
-    bool more = it.first(cur);
-    if (more) load(cur, nxt_v);
-    while (more && !*abort) {
-#pragma unroll
-      for (int k = 0; k < 3 * T_NPW; ++k) cur_v[k] = nxt_v[k];
-      more = it.next(cur);
-      if (more) load(cur, nxt_v);
-      const int s = q % TNI;
-      // stage s is free once the MMAs of item q - TNI have completed
-      const bool got = q < TNI || mbar_wait(aempty + s, ((q / TNI) - 1) & 1, abort);
-      if (!__all_sync(0xffffffffu, got)) {
-        if (lane == 0) atomicCAS(a.err, 0, THOP_ERR_LOAD);
-        *abort = 1;
-        break;
-      }
-      tc_fence_after();
-      const uint32_t col = tmem + lane_off + T_ACOL0 + s * T_ACOLS + 12 * T_NPW * lg;
-#pragma unroll
-      for (int b = 0; b < T_NPW; ++b) tc_st12(col + 12 * b, cur_v + 3 * b);
-      tc_wait_st();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(afull + s);
-      ++q;
     }
   }
   tc_fence_before();

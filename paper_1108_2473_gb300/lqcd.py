@@ -113,6 +113,7 @@ _SIGS = {
     "lqcd_batch_rhs": (_i, [_vp, ctypes.POINTER(_i)]),
     "lqcd_batch_destroy": (_i, [_vp]),
     "lqcd_autotune": (_i, [_vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "lqcd_tuned_choice": (_i, [_vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "lqcd_loops_stochastic": (_i, [_vp, ctypes.POINTER(lqcd_stochastic_params), ctypes.POINTER(lqcd_solver_params),
                                    _vp, _vp, ctypes.POINTER(lqcd_solve_stats), _vp]),
     "lqcd_gradient": (_i, [_vp, _vp, _vp, _i, _vp, _d, ctypes.POINTER(lqcd_solver_params), ctypes.POINTER(_d), _vp,
@@ -473,6 +474,14 @@ def lqcd_batch_run(batch, params, total_rhs=None, stream=None):
 
 def lqcd_batch_destroy(batch):
     return load().lqcd_batch_destroy(batch)
+
+
+def lqcd_tuned_choice(h, nrhs, precision):
+    """The launch choice later solves of (nrhs, precision) use: (blocks per SM, hop variant)."""
+    best = ctypes.c_int(0)
+    var = ctypes.c_int(0)
+    _check(load().lqcd_tuned_choice(h, int(nrhs), int(precision), ctypes.byref(best), ctypes.byref(var)), h)
+    return best.value, var.value
 
 
 def lqcd_autotune(h, nrhs, precision, with_variant=False):

@@ -119,3 +119,37 @@ def test_autotune_keeps_results_bit_identical():
             assert torch.equal(x0, x1)
         else:  # tensor-core SU(3) products: a different rounding, the same converged solution
             assert (x0 - x1).abs().max().item() <= 1e-8 * x0.abs().max().item()
+
+
+def test_tuned_layout_choice_is_revised_from_iteration_counts(monkeypatch):
+    """lqcd_tuned_choice reports the autotuner's pick until a BF16 solve revises
+    the choice between the pair and the 128-RHS tile layout from the solve's
+    per-RHS iteration counts: afterwards it is either the tile layout or the
+    autotuner's best pair configuration, and a solve with the revised choice
+    agrees with one forced onto the other layout."""
+    monkeypatch.delenv("LQCD_HOP_VARIANT", raising=False)
+    dims = (4, 4, 4, 8)
+    U = eps_su3_field(dims, 0.35, 2)
+    n = 128
+    b = gaussian_spinors(dims, n, 41).reshape(n, -1, 4, 3)
+    with lattice(dims, U, 0.12) as (L, h):
+        pr = L.LQCD_PREC_MIXED_BF16
+        bps, var = L.lqcd_autotune(h, n, pr, with_variant=True)
+        assert L.lqcd_tuned_choice(h, n, pr) == (bps, var)
+        bd = to_dev(b)
+        x0 = torch.empty_like(bd)
+        rc0, st0 = L.lqcd_solve_batch(h, bd, x0, L.solver_params(tol=1e-10, precision=pr))
+        assert rc0 == 0
+        bps2, var2 = L.lqcd_tuned_choice(h, n, pr)
+        assert (bps2, var2) == (1, 5) or var2 in (0, 1, 2, 3, 4)
+        if var == 5:
+            assert var2 == 5 or (bps2, var2) != (bps, var)
+        else:
+            assert (bps2, var2) in ((bps, var), (1, 5))
+        # the other layout gives the same solution to the solver's tolerance
+        monkeypatch.setenv("LQCD_HOP_VARIANT", "1" if var2 == 5 else "5")
+        x1 = torch.empty_like(bd)
+        rc1, st1 = L.lqcd_solve_batch(h, bd, x1, L.solver_params(tol=1e-10, precision=pr))
+        assert rc1 == 0
+        assert all(s["true_rel_residual"] <= 1e-10 for s in st0 + st1)
+        assert rel_err(to_np(x0, dims), to_np(x1, dims)) < 1e-8
