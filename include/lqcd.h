@@ -190,9 +190,11 @@ int lqcd_batch_destroy(lqcd_batch *batch);
  * complete inner iterations of the mixed solver (the four hopping-term launches
  * with their epilogues and the Krylov updates of the layout) for every
  * compiled variant -- the RHS-pair layout with its hop variants (register
- * budget, pairs per block, FP32-unit or mma.sync SU(3) products) on launch
- * grids of 2, 4, 8 and 16 blocks per SM, and, for BF16, the 128-RHS tile
- * layout with the tensor-core (tcgen05) hop -- and keep the fastest for later
+ * budget, pairs per block, FP32-unit or mma.sync SU(3) products; for BF16 on
+ * lattices with Lx Ly / 2 = 128 also the variant that stages a block's
+ * neighbour planes in shared memory, variant 6) on launch grids of 2, 4, 8 and
+ * 16 blocks per SM, and, for BF16, the 128-RHS tile layout with the
+ * tensor-core (tcgen05) hop, variant 5 -- and keep the fastest for later
  * solves of that (nrhs, precision).  *best_blocks_per_sm and *best_hop_variant
  * (host, each may be NULL) receive the choice.  Needs a gauge field.
  * Synchronises the device.  With LQCD_AUTOTUNE_VERBOSE set in the environment
@@ -210,7 +212,8 @@ int lqcd_autotune(lqcd_ctx *ctx, int nrhs, int precision, int *best_blocks_per_s
 /* The launch choice later solves of (nrhs, precision) will use -- after the
  * autotuner, any revision by earlier solves and the LQCD_HOP_VARIANT override --
  * as for lqcd_autotune (host ints, each may be NULL; hop variant 5 is the tile
- * layout).  Host only; LQCD_ERR_INVALID for a null ctx. */
+ * layout; an override to variant 6 where it does not apply reports variant 1,
+ * the kernel then launched).  Host only; LQCD_ERR_INVALID for a null ctx. */
 int lqcd_tuned_choice(const lqcd_ctx *ctx, int nrhs, int precision, int *blocks_per_sm, int *hop_variant);
 
 /* Point sources e_{x,spin,colour} (Sec. II: exact all-to-all propagator from

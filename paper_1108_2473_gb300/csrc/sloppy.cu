@@ -652,6 +652,166 @@ __global__ void __launch_bounds__(ST * PPB, MINB) k_hop_pair(Geom g, int p_out, 
   }
 }
 
+// ============================= pair hopping term, neighbour planes in shared memory
+// On lattices whose (z, t) planes hold ST sites of one parity (Lx Ly / 2 = ST),
+// the parity-local indices of a plane are one aligned block of ST, so a block
+// of the pair kernel covers exactly one plane of output sites.  The eight
+// neighbours of those sites lie in five planes of the other parity: the plane
+// itself (the x and y neighbours, wrap-arounds included), z + 1, z - 1, t + 1
+// and t - 1.  The block copies those five planes of its pair (and the plane of
+// the A operand) into shared memory with cp.async, which holds no registers
+// while the copies are in flight, then reads every neighbour spinor from shared
+// memory.  Links are loaded from global memory as in k_hop_pair, and the
+// arithmetic is that of k_hop_pair, term for term in the same order.
+constexpr int PLANE_VARIANT = 6;                            // its hop variant number
+constexpr int PL_SLOTS = 5;                                 // own, z + 1, z - 1, t + 1, t - 1
+constexpr int PL_SMEM_PLAIN = PL_SLOTS * 6 * ST * 16;       // 60 KiB
+constexpr int PL_SMEM_EPI = (PL_SLOTS + 1) * 6 * ST * 16;   // + the A operand's plane: 72 KiB
+
+__host__ __device__ inline bool planes_fit(const Geom &g) { return g.Lxh * g.L[1] == ST; }
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+// the 24 packed values of the site at offset loc of plane slot `slot`
+__device__ __forceinline__ void load_plane(const uint4 *sm, int slot, int loc, float2 v[24]) {
+  const uint4 *p = sm + slot * 6 * ST + loc;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const uint4 q = p[k * ST];
+    v[4 * k] = b2f(q.x);
+    v[4 * k + 1] = b2f(q.y);
+    v[4 * k + 2] = b2f(q.z);
+    v[4 * k + 3] = b2f(q.w);
+  }
+}
+
+template <int MU>
+__device__ __forceinline__ void hop_dir_plane(const Geom &g, int p_out, const int c[4], int i, const uint4 *sm,
+                                              const uint4 *links, CP acc[4][3]) {
+  constexpr int FWD = MU < 2 ? 0 : (MU == 2 ? 1 : 3), BWD = MU < 2 ? 0 : (MU == 2 ? 2 : 4);
+  float2 v[24], nrm;
+  CP h[2][3], u[3][3];
+  {  // forward: (1 - gamma_mu) U_mu(x) psi(x + mu); the t-boundary sign rides on the norm
+    int cn[4] = {c[0], c[1], c[2], c[3]};
+    cn[MU] = (c[MU] + 1 == g.L[MU]) ? 0 : c[MU] + 1;
+    const int sn = site_of(g, cn);
+    load_plane(sm, FWD, (sn >> 1) & (ST - 1), v);
+    nrm = (MU == 3 && c[3] == g.L[3] - 1) ? make_float2(-1.f, -1.f) : make_float2(1.f, 1.f);
+    project_pair<MU, -1>(v, h);
+    load_link_pair(links, p_out, MU, i, g.Vh, u);
+    su3_accum_pair<MU, -1, false>(u, h, nrm, acc);
+  }
+  {  // backward: (1 + gamma_mu) U_mu(x - mu)^+ psi(x - mu)
+    int cn[4] = {c[0], c[1], c[2], c[3]};
+    cn[MU] = (c[MU] == 0) ? g.L[MU] - 1 : c[MU] - 1;
+    const int sn = site_of(g, cn);
+    load_plane(sm, BWD, (sn >> 1) & (ST - 1), v);
+    nrm = (MU == 3 && c[3] == 0) ? make_float2(-1.f, -1.f) : make_float2(1.f, 1.f);
+    project_pair<MU, +1>(v, h);
+    load_link_pair(links, 1 - p_out, MU, sn >> 1, g.Vh, u);
+    su3_accum_pair<MU, +1, true>(u, h, nrm, acc);
+  }
+}
+
+// BF16 pairs only; one block of ST threads per (pair, plane) item, grid-stride
+// over the items pair by pair (as k_hop_pair), at most three blocks per SM
+// (72 KiB of shared memory each).  Requires planes_fit(g) and nbx = Lz Lt.
+template <int EPI>
+__global__ void __launch_bounds__(ST, 3) k_hop_pair_pl(Geom g, int p_out, const uint4 *links, BF16P in, BF16P out,
+                                                       BF16P A, BF16P B, float cA, float cH, const int *plist,
+                                                       const int *pcount, D4S *part, int nbx, int nrhs,
+                                                       unsigned long long *prof) {
+  extern __shared__ uint4 pl_sm[];
+  const int count = *pcount;
+  const int n_items = count * nbx;
+  const float2 cA2 = make_float2(cA, cA), cH2 = make_float2(cH, cH);
+  const int tid = threadIdx.x, Lz = g.L[2], Lt = g.L[3];
+  const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(pl_sm + tid);
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int P = plist[w / nbx], sb = w % nbx;
+    const int z = sb % Lz, t = sb / Lz;
+    const int pl[PL_SLOTS] = {sb, (z + 1 == Lz ? 0 : z + 1) + Lz * t, (z == 0 ? Lz - 1 : z - 1) + Lz * t,
+                              z + Lz * (t + 1 == Lt ? 0 : t + 1), z + Lz * (t == 0 ? Lt - 1 : t - 1)};
+    {
+      const uint4 *src = in.d + (size_t)P * 6 * in.vh + tid;
+#pragma unroll
+      for (int s = 0; s < PL_SLOTS; ++s)
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          cp_async16(s_base + (uint32_t)((s * 6 + k) * ST * 16), src + (size_t)k * in.vh + (size_t)pl[s] * ST);
+      if (EPI != EPI_PLAIN) {
+        const uint4 *sa = A.d + (size_t)P * 6 * A.vh + (size_t)sb * ST + tid;
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+          cp_async16(s_base + (uint32_t)(((PL_SLOTS * 6) + k) * ST * 16), sa + (size_t)k * A.vh);
+      }
+      asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    if (prof && tid == 0) atomicAdd(prof + EPI, (unsigned long long)ST * (2 * P + 1 < nrhs ? 2 : 1));
+    const int i = sb * ST + tid;
+    int c[4];
+    coords_of(g, p_out, i, c);
+    CP acc[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) acc[a][b] = CP{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    hop_dir_plane<0>(g, p_out, c, i, pl_sm, links, acc);
+    hop_dir_plane<1>(g, p_out, c, i, pl_sm, links, acc);
+    hop_dir_plane<2>(g, p_out, c, i, pl_sm, links, acc);
+    hop_dir_plane<3>(g, p_out, c, i, pl_sm, links, acc);
+    float2 o[24];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      o[2 * k] = M2(acc[k / 3][k % 3].re, cH2);
+      o[2 * k + 1] = M2(acc[k / 3][k % 3].im, cH2);
+    }
+    float2 a[24];
+    if (EPI != EPI_PLAIN) {
+      load_plane(pl_sm, PL_SLOTS, tid, a);
+#pragma unroll
+      for (int k = 0; k < 24; ++k) o[k] = F2(cA2, a[k], o[k]);
+    }
+    store_pair(out, P, i, o);
+    D4S r0 = {0, 0, 0, 0}, r1 = {0, 0, 0, 0};
+    if (EPI == EPI_DOTR) {  // <B, out> = sum conj(B) out
+      float2 rb[24];
+      load_scaled(B, P, i, rb);
+      float2 re = make_float2(0.f, 0.f), ip = re, im = re;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        re = F2(rb[2 * k], o[2 * k], re);
+        re = F2(rb[2 * k + 1], o[2 * k + 1], re);
+        ip = F2(rb[2 * k], o[2 * k + 1], ip);
+        im = F2(rb[2 * k + 1], o[2 * k], im);
+      }
+      const float2 imag = S2(ip, im);
+      r0 = D4S{re.x, imag.x, 0, 0};
+      r1 = D4S{re.y, imag.y, 0, 0};
+    } else if (EPI == EPI_TS) {  // <out, A> and |out|^2
+      float2 re = make_float2(0.f, 0.f), ip = re, im = re, nn = re;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        re = F2(o[2 * k], a[2 * k], re);
+        re = F2(o[2 * k + 1], a[2 * k + 1], re);
+        ip = F2(o[2 * k], a[2 * k + 1], ip);
+        im = F2(o[2 * k + 1], a[2 * k], im);
+        nn = F2(o[2 * k], o[2 * k], nn);
+        nn = F2(o[2 * k + 1], o[2 * k + 1], nn);
+      }
+      const float2 imag = S2(ip, im);
+      r0 = D4S{re.x, imag.x, 0, nn.x};
+      r1 = D4S{re.y, imag.y, 0, nn.y};
+    }
+    if (EPI == EPI_DOTR || EPI == EPI_TS)
+      group_reduce_store2<1>(r0, r1, part + (size_t)(2 * P) * nbx + sb, part + (size_t)(2 * P + 1) * nbx + sb, true);
+    __syncthreads();  // the next item's copies overwrite the planes
+  }
+}
+
 // ======================================== pair hopping term on tensor cores
 // The SU(3) products of the hopping term are moved onto the tensor cores with
 // mma.sync m16n8k8 (tf32 in, FP32 accumulate); spin projection, the norms and
@@ -962,7 +1122,7 @@ __global__ void __launch_bounds__(128, MMA_MINB) k_hop_mma(Geom g, int p_out, co
   }
 }
 
-// The pair-layout variants of the hopping term (0-4; see HOP_VARIANTS below).
+// The pair-layout variants of the hopping term (0-4 and 6; see HOP_VARIANTS below).
 template <class SP, int EPI>
 static void launch_hop_pair(int variant, int G, cudaStream_t q, const lqcd_ctx *ctx, Geom g, int p_out, SP in, SP out,
                             SP A, SP B, float cA, float cH, const int *plist, const int *pcount, D4S *part, int nbx,
@@ -984,6 +1144,22 @@ static void launch_hop_pair(int variant, int G, cudaStream_t q, const lqcd_ctx *
     case 4:
       KL k_hop_mma<SP, EPI><<<G, 128, 0, q>>>(g, p_out, ctx->Utf, in, out, A, B, cA, cH, plist, pcount, part, nbx, nrhs,
                                               prof);
+      break;
+    case PLANE_VARIANT:
+      if constexpr (std::is_same<SP, BF16P>::value) {
+        if (planes_fit(g)) {
+          constexpr int smem = EPI == EPI_PLAIN ? PL_SMEM_PLAIN : PL_SMEM_EPI;
+          static bool attr = false;  // a refused attribute makes the launch fail, which the caller reports
+          if (!attr) attr = cudaFuncSetAttribute(k_hop_pair_pl<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 smem) == cudaSuccess;
+          KL k_hop_pair_pl<EPI><<<G, ST, smem, q>>>(g, p_out, L16, in, out, A, B, cA, cH, plist, pcount, part, nbx,
+                                                    nrhs, prof);
+          break;
+        }
+      }
+      // other precisions and geometries: the register-capped pair kernel
+      KL k_hop_pair<SP, EPI, 4, 1><<<G, ST, 0, q>>>(g, p_out, L16, in, out, A, B, cA, cH, plist, pcount, part, nbx,
+                                                     nrhs, prof);
       break;
     default:
       KL k_hop_pair<SP, EPI, 1, 1><<<G, ST, 0, q>>>(g, p_out, L16, in, out, A, B, cA, cH, plist, pcount, part, nbx,
@@ -1662,13 +1838,15 @@ template <> BF16P pair_field<BF16P>(SloppyState *st, int f, int vh) {
 //   2: pair layout, two pairs per block (256 threads), the same register cap
 //   3: pair layout, four pairs per block (512 threads), the same register cap
 //   4: pair layout, SU(3) products on the tensor cores (mma.sync, k_hop_mma)
-//   5: RHS-tile layout (BF16 only): neighbour tiles written to TMEM by loader warps, tcgen05.mma
-//      with A from TMEM (k_thop)
-constexpr int HOP_VARIANTS = 6;
+//   5: RHS-tile layout (BF16 only): neighbour blocks bulk-copied into shared memory, tcgen05.mma
+//      into TMEM accumulators (k_thop)
+//   6: pair layout (BF16, lattices with Lx Ly / 2 = 128): one (z, t) plane per block, the five
+//      neighbour planes staged in shared memory by cp.async (k_hop_pair_pl); else variant 1
+constexpr int HOP_VARIANTS = 7;
 constexpr int TILE_VARIANT = 5;
 
 // autotuned launch choice per (nrhs, precision): code = blocks_per_sm * 10 + hop variant;
-// LQCD_HOP_VARIANT=0..5 in the environment overrides the variant (for tests)
+// LQCD_HOP_VARIANT=0..6 in the environment overrides the variant (for tests)
 static int tuned_code(const lqcd_ctx *ctx, int nrhs, int precision) {
   long long key = (long long)nrhs * 8 + precision;
   int code = 80;
@@ -1678,6 +1856,8 @@ static int tuned_code(const lqcd_ctx *ctx, int nrhs, int precision) {
   if (force && force[0] >= '0' && force[0] < '0' + HOP_VARIANTS && force[1] == 0)
     code = code / 10 * 10 + (force[0] - '0');
   if (precision != LQCD_PREC_MIXED_BF16 && code % 10 == TILE_VARIANT) code = code / 10 * 10 + 1;  // tiles: BF16 only
+  if (code % 10 == PLANE_VARIANT && !(precision == LQCD_PREC_MIXED_BF16 && planes_fit(ctx->geom)))
+    code = code / 10 * 10 + 1;  // the variant that launch_hop_pair falls back to
   return code;
 }
 
@@ -2534,13 +2714,15 @@ static int autotune_hop(lqcd_ctx *ctx, int nrhs, int precision, int *best, int *
       best_code = code;
     }
   };
-  for (int variant = 0; variant < TILE_VARIANT; ++variant)
+  for (int variant = 0; variant < HOP_VARIANTS; ++variant) {
+    if (variant == TILE_VARIANT || (variant == PLANE_VARIANT && !(tiles && planes_fit(ctx->geom)))) continue;
     for (int c : cand) {
       float ms = 0.f;
       rc = time_code<PairOps<SP>>(ctx, nrhs, precision, c * 10 + variant, &ms);
       if (rc) return rc;
       consider(c * 10 + variant, ms);
     }
+  }
   const int pair_code = best_code;
   const float pair_ms = best_ms;
   float tile_ms = -1.f;

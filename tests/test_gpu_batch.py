@@ -141,7 +141,7 @@ def test_tuned_layout_choice_is_revised_from_iteration_counts(monkeypatch):
         rc0, st0 = L.lqcd_solve_batch(h, bd, x0, L.solver_params(tol=1e-10, precision=pr))
         assert rc0 == 0
         bps2, var2 = L.lqcd_tuned_choice(h, n, pr)
-        assert (bps2, var2) == (1, 5) or var2 in (0, 1, 2, 3, 4)
+        assert (bps2, var2) == (1, 5) or var2 in (0, 1, 2, 3, 4, 6)
         if var == 5:
             assert var2 == 5 or (bps2, var2) != (bps, var)
         else:
