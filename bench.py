@@ -71,7 +71,8 @@ HOP_KERNEL = {0: "k_hop_pair<*, *, 1, 1> (pair layout, FFMA2)", 1: "k_hop_pair<*
               2: "k_hop_pair<*, *, 2, 2> (pair layout, FFMA2)", 3: "k_hop_pair<*, *, 1, 4> (pair layout, FFMA2)",
               4: "k_hop_mma (pair layout, mma.sync tf32)",
               5: "k_thop (128-RHS tiles, neighbour blocks bulk-copied to shared memory, tcgen05.mma)",
-              6: "k_hop_pair_pl (pair layout, FFMA2, neighbour planes staged in shared memory by cp.async)"}
+              6: "k_hop_pair_pl (pair layout, FFMA2, neighbour planes staged in shared memory by cp.async)",
+              7: "k_hop_pair<*, *, 4, 1, true> (pair layout, FFMA2, reconstruct-12 links)"}
 
 
 class Clocks:

@@ -190,7 +190,8 @@ int lqcd_batch_destroy(lqcd_batch *batch);
  * complete inner iterations of the mixed solver (the four hopping-term launches
  * with their epilogues and the Krylov updates of the layout) for every
  * compiled variant -- the RHS-pair layout with its hop variants (register
- * budget, pairs per block, FP32-unit or mma.sync SU(3) products; for BF16 on
+ * budget, pairs per block, FP32-unit or mma.sync SU(3) products, full or
+ * reconstruct-12 FP16 links (variant 7); for BF16 on
  * lattices with Lx Ly / 2 = 128 also the variant that stages a block's
  * neighbour planes in shared memory, variant 6) on launch grids of 2, 4, 8 and
  * 16 blocks per SM, and, for BF16, the 128-RHS tile layout with the

@@ -434,6 +434,30 @@ __device__ __forceinline__ void load_link_pair(const uint4 *U, int p, int mu, in
   for (int k = 0; k < 9; ++k) u[k / 3][k % 3] = CP{h2f(w[2 * k]), h2f(w[2 * k + 1])};
 }
 
+// Rows 0 and 1 of the same FP16 link (the first three uint4 of its layout);
+// row 2 rebuilt as conj(row 0 x row 1), u[2][c] = conj(u[0][a] u[1][b] - u[0][b] u[1][a])
+// for (a, b, c) cyclic, which holds for SU(3) links (the mixed solver requires
+// them): two of the five loads per link traded for 30 packed FP32 operations.
+__device__ __forceinline__ void load_link_pair_r12(const uint4 *U, int p, int mu, int i, int vh, CP u[3][3]) {
+  const size_t base = ((size_t)(p * 4 + mu) * 5) * vh + i;
+  uint4 q[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) q[k] = U[base + (size_t)k * vh];
+  const unsigned w[12] = {q[0].x, q[0].y, q[0].z, q[0].w, q[1].x, q[1].y,
+                          q[1].z, q[1].w, q[2].x, q[2].y, q[2].z, q[2].w};
+#pragma unroll
+  for (int k = 0; k < 6; ++k) u[k / 3][k % 3] = CP{h2f(w[2 * k]), h2f(w[2 * k + 1])};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int a = (c + 1) % 3, b = (c + 2) % 3;
+    const CP &x = u[0][a], &y = u[1][b], &v = u[0][b], &z = u[1][a];
+    // Re = x.re y.re - x.im y.im - v.re z.re + v.im z.im; -Im = v.re z.im + v.im z.re - x.re y.im - x.im y.re
+    const float2 re = S2(F2(x.re, y.re, M2(v.im, z.im)), F2(x.im, y.im, M2(v.re, z.re)));
+    const float2 mim = S2(F2(v.re, z.im, M2(v.im, z.re)), F2(x.re, y.im, M2(x.im, y.re)));
+    u[2][c] = CP{re, mim};
+  }
+}
+
 // a + s i b and a + s b on pairs
 template <int S> __device__ __forceinline__ CP cp_addi(const CP &a, const CP &b) {
   return S > 0 ? CP{S2(a.re, b.im), A2(a.im, b.re)} : CP{A2(a.re, b.im), S2(a.im, b.re)};
@@ -541,7 +565,7 @@ __device__ __forceinline__ void su3_accum_pair(const CP u[3][3], const CP h[2][3
   }
 }
 
-template <int MU, class SP>
+template <int MU, class SP, bool R12 = false>
 __device__ __forceinline__ void hop_dir_pair(const Geom &g, int p_out, const int c[4], int i, const SP &in, int P,
                                              const uint4 *links, CP acc[4][3]) {
   float2 v[24], nrm;
@@ -553,7 +577,8 @@ __device__ __forceinline__ void hop_dir_pair(const Geom &g, int p_out, const int
     load_raw(in, P, sn >> 1, v, nrm);
     if (MU == 3 && c[3] == g.L[3] - 1) nrm = make_float2(-nrm.x, -nrm.y);
     project_pair<MU, -1>(v, h);
-    load_link_pair(links, p_out, MU, i, g.Vh, u);
+    if (R12) load_link_pair_r12(links, p_out, MU, i, g.Vh, u);
+    else load_link_pair(links, p_out, MU, i, g.Vh, u);
     su3_accum_pair<MU, -1, false>(u, h, nrm, acc);
   }
   {  // backward: (1 + gamma_mu) U_mu(x - mu)^+ psi(x - mu)
@@ -563,7 +588,8 @@ __device__ __forceinline__ void hop_dir_pair(const Geom &g, int p_out, const int
     load_raw(in, P, sn >> 1, v, nrm);
     if (MU == 3 && c[3] == 0) nrm = make_float2(-nrm.x, -nrm.y);
     project_pair<MU, +1>(v, h);
-    load_link_pair(links, 1 - p_out, MU, sn >> 1, g.Vh, u);
+    if (R12) load_link_pair_r12(links, 1 - p_out, MU, sn >> 1, g.Vh, u);
+    else load_link_pair(links, 1 - p_out, MU, sn >> 1, g.Vh, u);
     su3_accum_pair<MU, +1, true>(u, h, nrm, acc);
   }
 }
@@ -573,8 +599,8 @@ __device__ __forceinline__ void hop_dir_pair(const Geom &g, int p_out, const int
 // EPI_TS: partials <out, A> and |out|^2 per member.
 // A block of PPB * ST threads takes PPB active pairs on the same ST sites, so
 // the links those sites read are fetched from L2 once per block and then hit
-// in L1 for the other pairs.
-template <class SP, int EPI, int MINB, int PPB>
+// in L1 for the other pairs.  R12: links from rows 0 and 1 (load_link_pair_r12).
+template <class SP, int EPI, int MINB, int PPB, bool R12 = false>
 __global__ void __launch_bounds__(ST * PPB, MINB) k_hop_pair(Geom g, int p_out, const uint4 *links, SP in, SP out,
                                                        SP A, SP B, float cA, float cH, const int *plist,
                                                        const int *pcount, D4S *part, int nbx, int nrhs,
@@ -599,10 +625,10 @@ __global__ void __launch_bounds__(ST * PPB, MINB) k_hop_pair(Geom g, int p_out, 
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) acc[a][b] = CP{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-      hop_dir_pair<0>(g, p_out, c, i, in, P, links, acc);
-      hop_dir_pair<1>(g, p_out, c, i, in, P, links, acc);
-      hop_dir_pair<2>(g, p_out, c, i, in, P, links, acc);
-      hop_dir_pair<3>(g, p_out, c, i, in, P, links, acc);
+      hop_dir_pair<0, SP, R12>(g, p_out, c, i, in, P, links, acc);
+      hop_dir_pair<1, SP, R12>(g, p_out, c, i, in, P, links, acc);
+      hop_dir_pair<2, SP, R12>(g, p_out, c, i, in, P, links, acc);
+      hop_dir_pair<3, SP, R12>(g, p_out, c, i, in, P, links, acc);
       float2 o[24];
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
@@ -664,6 +690,7 @@ __global__ void __launch_bounds__(ST * PPB, MINB) k_hop_pair(Geom g, int p_out, 
 // memory.  Links are loaded from global memory as in k_hop_pair, and the
 // arithmetic is that of k_hop_pair, term for term in the same order.
 constexpr int PLANE_VARIANT = 6;                            // its hop variant number
+constexpr int R12_VARIANT = 7;                              // variant 1 with reconstruct-12 links
 constexpr int PL_SLOTS = 5;                                 // own, z + 1, z - 1, t + 1, t - 1
 constexpr int PL_SMEM_PLAIN = PL_SLOTS * 6 * ST * 16;       // 60 KiB
 constexpr int PL_SMEM_EPI = (PL_SLOTS + 1) * 6 * ST * 16;   // + the A operand's plane: 72 KiB
@@ -1122,7 +1149,7 @@ __global__ void __launch_bounds__(128, MMA_MINB) k_hop_mma(Geom g, int p_out, co
   }
 }
 
-// The pair-layout variants of the hopping term (0-4 and 6; see HOP_VARIANTS below).
+// The pair-layout variants of the hopping term (0-4, 6 and 7; see HOP_VARIANTS below).
 template <class SP, int EPI>
 static void launch_hop_pair(int variant, int G, cudaStream_t q, const lqcd_ctx *ctx, Geom g, int p_out, SP in, SP out,
                             SP A, SP B, float cA, float cH, const int *plist, const int *pcount, D4S *part, int nbx,
@@ -1160,6 +1187,10 @@ static void launch_hop_pair(int variant, int G, cudaStream_t q, const lqcd_ctx *
       // other precisions and geometries: the register-capped pair kernel
       KL k_hop_pair<SP, EPI, 4, 1><<<G, ST, 0, q>>>(g, p_out, L16, in, out, A, B, cA, cH, plist, pcount, part, nbx,
                                                      nrhs, prof);
+      break;
+    case R12_VARIANT:
+      KL k_hop_pair<SP, EPI, 4, 1, true><<<G, ST, 0, q>>>(g, p_out, L16, in, out, A, B, cA, cH, plist, pcount, part,
+                                                           nbx, nrhs, prof);
       break;
     default:
       KL k_hop_pair<SP, EPI, 1, 1><<<G, ST, 0, q>>>(g, p_out, L16, in, out, A, B, cA, cH, plist, pcount, part, nbx,
@@ -1842,11 +1873,12 @@ template <> BF16P pair_field<BF16P>(SloppyState *st, int f, int vh) {
 //      into TMEM accumulators (k_thop)
 //   6: pair layout (BF16, lattices with Lx Ly / 2 = 128): one (z, t) plane per block, the five
 //      neighbour planes staged in shared memory by cp.async (k_hop_pair_pl); else variant 1
-constexpr int HOP_VARIANTS = 7;
+//   7: variant 1 with reconstruct-12 links (rows 0 and 1 loaded, row 2 rebuilt)
+constexpr int HOP_VARIANTS = 8;
 constexpr int TILE_VARIANT = 5;
 
 // autotuned launch choice per (nrhs, precision): code = blocks_per_sm * 10 + hop variant;
-// LQCD_HOP_VARIANT=0..6 in the environment overrides the variant (for tests)
+// LQCD_HOP_VARIANT=0..7 in the environment overrides the variant (for tests)
 static int tuned_code(const lqcd_ctx *ctx, int nrhs, int precision) {
   long long key = (long long)nrhs * 8 + precision;
   int code = 80;

@@ -112,12 +112,12 @@ def test_autotune_keeps_results_bit_identical():
         x0 = torch.empty_like(bd)
         L.lqcd_solve_batch(h, bd, x0, L.solver_params(tol=1e-10, precision=L.LQCD_PREC_MIXED_FP16))
         best, variant = L.lqcd_autotune(h, 4, L.LQCD_PREC_MIXED_FP16, with_variant=True)
-        assert best in (2, 4, 8, 16) and 0 <= variant <= 4  # FP16: pair variants only
+        assert best in (2, 4, 8, 16) and variant in (0, 1, 2, 3, 4, 7)  # FP16: pair variants only
         x1 = torch.empty_like(bd)
         L.lqcd_solve_batch(h, bd, x1, L.solver_params(tol=1e-10, precision=L.LQCD_PREC_MIXED_FP16))
         if variant < 4:  # the FP32-unit variants differ only in launch shape: same arithmetic
             assert torch.equal(x0, x1)
-        else:  # tensor-core SU(3) products: a different rounding, the same converged solution
+        else:  # tensor-core SU(3) products or rebuilt link rows: a different rounding, the same solution
             assert (x0 - x1).abs().max().item() <= 1e-8 * x0.abs().max().item()
 
 
@@ -141,7 +141,7 @@ def test_tuned_layout_choice_is_revised_from_iteration_counts(monkeypatch):
         rc0, st0 = L.lqcd_solve_batch(h, bd, x0, L.solver_params(tol=1e-10, precision=pr))
         assert rc0 == 0
         bps2, var2 = L.lqcd_tuned_choice(h, n, pr)
-        assert (bps2, var2) == (1, 5) or var2 in (0, 1, 2, 3, 4, 6)
+        assert (bps2, var2) == (1, 5) or var2 in (0, 1, 2, 3, 4, 6, 7)
         if var == 5:
             assert var2 == 5 or (bps2, var2) != (bps, var)
         else:

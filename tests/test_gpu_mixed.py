@@ -15,13 +15,13 @@ pytestmark = pytest.mark.gpu
 PRECS = ["fp16", "bf16"]
 
 
-@pytest.fixture(autouse=True, params=["0", "1", "4", "5"], ids=["hop-ffma2", "hop-ffma2-capped", "hop-mma",
-                                                               "hop-tcgen05-tiles"])
+@pytest.fixture(autouse=True, params=["0", "1", "4", "5", "7"], ids=["hop-ffma2", "hop-ffma2-capped", "hop-mma",
+                                                                    "hop-tcgen05-tiles", "hop-ffma2-recon12"])
 def hop_variant(request, monkeypatch):
-    """Every test here runs with the FP32-unit pair hop (uncapped / register-capped),
-    the mma.sync pair hop, and the RHS-tile solver with the tcgen05 hop (BF16
-    only; FP16 solves fall back to variant 1).  LQCD_HOP_VARIANT is read at
-    solve setup."""
+    """Every test here runs with the FP32-unit pair hop (uncapped / register-capped,
+    and register-capped with reconstruct-12 links), the mma.sync pair hop, and
+    the RHS-tile solver with the tcgen05 hop (BF16 only; FP16 solves fall back
+    to variant 1).  LQCD_HOP_VARIANT is read at solve setup."""
     monkeypatch.setenv("LQCD_HOP_VARIANT", request.param)
     return request.param
 
