@@ -193,8 +193,8 @@ int lqcd_batch_destroy(lqcd_batch *batch);
  * budget, pairs per block, FP32-unit or mma.sync SU(3) products, full or
  * reconstruct-12 FP16 links (variant 7); for BF16 on
  * lattices with Lx Ly / 2 = 128 also the variant that stages a block's
- * neighbour planes in shared memory, variant 6) on launch grids of 2, 4, 8 and
- * 16 blocks per SM, and, for BF16, the 128-RHS tile layout with the
+ * neighbour planes in shared memory, variant 6) on launch grids of 2 to 256
+ * blocks per SM (powers of two), and, for BF16, the 128-RHS tile layout with the
  * tensor-core (tcgen05) hop, variant 5 -- and keep the fastest for later
  * solves of that (nrhs, precision).  *best_blocks_per_sm and *best_hop_variant
  * (host, each may be NULL) receive the choice.  Needs a gauge field.

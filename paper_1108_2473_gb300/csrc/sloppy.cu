@@ -2733,7 +2733,7 @@ static int autotune_hop(lqcd_ctx *ctx, int nrhs, int precision, int *best, int *
   // one allocation serves both layouts (a capacity in whole tiles is also whole pairs)
   int rc = sloppy_alloc(ctx, nrhs, tiles ? TR : 2);
   if (rc) return rc;
-  const int cand[4] = {2, 4, 8, 16};
+  const int cand[8] = {2, 4, 8, 16, 32, 64, 128, 256};
   const bool verbose = getenv("LQCD_AUTOTUNE_VERBOSE") != nullptr;  // timings to stderr
   float best_ms = 1e30f;
   int best_code = 80;
