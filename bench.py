@@ -641,8 +641,9 @@ def run_ours(args, rank, world, local_rank):
     # ---------------------------------------------------------- roofline
     peak, peak_kind = _peaks()
     hop_s = prof["hop_ms"] / 1e3
-    # algorithmic bytes by the survey's count: 48 B of 16-bit spinor per output
-    # (site, RHS) plus FP16 reconstruct-12 links (8 x 24 B per site) once per launch
+    # algorithmic bytes of the hopping term: per output (site, RHS) one 16-bit
+    # spinor read (each input read once) and one written, 2 x 48 B, plus FP16
+    # reconstruct-12 links (8 x 24 B per site) once per launch
     vh = V // 2
     alg_bytes = 96.0 * prof["hop_site_rhs"] + prof["hop_launches"] * vh * 8 * 24.0
     achieved = alg_bytes / hop_s / 1e9 if hop_s > 0 else 0.0
