@@ -594,6 +594,55 @@ __device__ __forceinline__ void hop_dir_pair(const Geom &g, int p_out, const int
   }
 }
 
+// Epilogue of the pair hopping term at output site i of pair P: o = cH acc
+// (+ cA a unless EPI_PLAIN), stored to out; EPI_DOTR: partials <B, o> per
+// member; EPI_TS: partials <o, a> and |o|^2 per member (r0, r1 untouched for
+// EPI_PLAIN).
+template <class SP, int EPI>
+__device__ __forceinline__ void pair_epilogue(const CP acc[4][3], const float2 a[24], float2 cA2, float2 cH2,
+                                              const SP &out, const SP &B, int P, int i, D4S &r0, D4S &r1) {
+  float2 o[24];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    o[2 * k] = M2(acc[k / 3][k % 3].re, cH2);
+    o[2 * k + 1] = M2(acc[k / 3][k % 3].im, cH2);
+  }
+  if (EPI != EPI_PLAIN) {
+#pragma unroll
+    for (int k = 0; k < 24; ++k) o[k] = F2(cA2, a[k], o[k]);
+  }
+  store_pair(out, P, i, o);
+  if (EPI == EPI_DOTR) {  // <B, out> = sum conj(B) out
+    float2 rb[24];
+    load_scaled(B, P, i, rb);
+    float2 re = make_float2(0.f, 0.f), ip = re, im = re;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      re = F2(rb[2 * k], o[2 * k], re);
+      re = F2(rb[2 * k + 1], o[2 * k + 1], re);
+      ip = F2(rb[2 * k], o[2 * k + 1], ip);
+      im = F2(rb[2 * k + 1], o[2 * k], im);
+    }
+    const float2 imag = S2(ip, im);
+    r0 = D4S{re.x, imag.x, 0, 0};
+    r1 = D4S{re.y, imag.y, 0, 0};
+  } else if (EPI == EPI_TS) {  // <out, A> and |out|^2
+    float2 re = make_float2(0.f, 0.f), ip = re, im = re, nn = re;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      re = F2(o[2 * k], a[2 * k], re);
+      re = F2(o[2 * k + 1], a[2 * k + 1], re);
+      ip = F2(o[2 * k], a[2 * k + 1], ip);
+      im = F2(o[2 * k + 1], a[2 * k], im);
+      nn = F2(o[2 * k], o[2 * k], nn);
+      nn = F2(o[2 * k + 1], o[2 * k + 1], nn);
+    }
+    const float2 imag = S2(ip, im);
+    r0 = D4S{re.x, imag.x, 0, nn.x};
+    r1 = D4S{re.y, imag.y, 0, nn.y};
+  }
+}
+
 // Sloppy hopping term on RHS pairs: out = cA A + cH (H in) at parity p_out.
 // EPI_PLAIN: out = cH H in.  EPI_DOTR: partial <B, out> per member.
 // EPI_TS: partials <out, A> and |out|^2 per member.
@@ -629,48 +678,9 @@ __global__ void __launch_bounds__(ST * PPB, MINB) k_hop_pair(Geom g, int p_out, 
       hop_dir_pair<1, SP, R12>(g, p_out, c, i, in, P, links, acc);
       hop_dir_pair<2, SP, R12>(g, p_out, c, i, in, P, links, acc);
       hop_dir_pair<3, SP, R12>(g, p_out, c, i, in, P, links, acc);
-      float2 o[24];
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        o[2 * k] = M2(acc[k / 3][k % 3].re, cH2);
-        o[2 * k + 1] = M2(acc[k / 3][k % 3].im, cH2);
-      }
       float2 a[24];
-      if (EPI != EPI_PLAIN) {
-        load_scaled(A, P, i, a);
-#pragma unroll
-        for (int k = 0; k < 24; ++k) o[k] = F2(cA2, a[k], o[k]);
-      }
-      store_pair(out, P, i, o);
-      if (EPI == EPI_DOTR) {  // <B, out> = sum conj(B) out
-        float2 rb[24];
-        load_scaled(B, P, i, rb);
-        float2 re = make_float2(0.f, 0.f), ip = re, im = re;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-          re = F2(rb[2 * k], o[2 * k], re);
-          re = F2(rb[2 * k + 1], o[2 * k + 1], re);
-          ip = F2(rb[2 * k], o[2 * k + 1], ip);
-          im = F2(rb[2 * k + 1], o[2 * k], im);
-        }
-        const float2 imag = S2(ip, im);
-        r0 = D4S{re.x, imag.x, 0, 0};
-        r1 = D4S{re.y, imag.y, 0, 0};
-      } else if (EPI == EPI_TS) {  // <out, A> and |out|^2
-        float2 re = make_float2(0.f, 0.f), ip = re, im = re, nn = re;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-          re = F2(o[2 * k], a[2 * k], re);
-          re = F2(o[2 * k + 1], a[2 * k + 1], re);
-          ip = F2(o[2 * k], a[2 * k + 1], ip);
-          im = F2(o[2 * k + 1], a[2 * k], im);
-          nn = F2(o[2 * k], o[2 * k], nn);
-          nn = F2(o[2 * k + 1], o[2 * k + 1], nn);
-        }
-        const float2 imag = S2(ip, im);
-        r0 = D4S{re.x, imag.x, 0, nn.x};
-        r1 = D4S{re.y, imag.y, 0, nn.y};
-      }
+      if (EPI != EPI_PLAIN) load_scaled(A, P, i, a);
+      pair_epilogue<SP, EPI>(acc, a, cA2, cH2, out, B, P, i, r0, r1);
     }
     if (EPI == EPI_DOTR || EPI == EPI_TS)
       group_reduce_store2<PPB>(r0, r1, part + (size_t)(2 * P) * nbx + sb, part + (size_t)(2 * P + 1) * nbx + sb,
@@ -790,49 +800,10 @@ __global__ void __launch_bounds__(ST, 3) k_hop_pair_pl(Geom g, int p_out, const 
     hop_dir_plane<1>(g, p_out, c, i, pl_sm, links, acc);
     hop_dir_plane<2>(g, p_out, c, i, pl_sm, links, acc);
     hop_dir_plane<3>(g, p_out, c, i, pl_sm, links, acc);
-    float2 o[24];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      o[2 * k] = M2(acc[k / 3][k % 3].re, cH2);
-      o[2 * k + 1] = M2(acc[k / 3][k % 3].im, cH2);
-    }
     float2 a[24];
-    if (EPI != EPI_PLAIN) {
-      load_plane(pl_sm, PL_SLOTS, tid, a);
-#pragma unroll
-      for (int k = 0; k < 24; ++k) o[k] = F2(cA2, a[k], o[k]);
-    }
-    store_pair(out, P, i, o);
+    if (EPI != EPI_PLAIN) load_plane(pl_sm, PL_SLOTS, tid, a);
     D4S r0 = {0, 0, 0, 0}, r1 = {0, 0, 0, 0};
-    if (EPI == EPI_DOTR) {  // <B, out> = sum conj(B) out
-      float2 rb[24];
-      load_scaled(B, P, i, rb);
-      float2 re = make_float2(0.f, 0.f), ip = re, im = re;
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        re = F2(rb[2 * k], o[2 * k], re);
-        re = F2(rb[2 * k + 1], o[2 * k + 1], re);
-        ip = F2(rb[2 * k], o[2 * k + 1], ip);
-        im = F2(rb[2 * k + 1], o[2 * k], im);
-      }
-      const float2 imag = S2(ip, im);
-      r0 = D4S{re.x, imag.x, 0, 0};
-      r1 = D4S{re.y, imag.y, 0, 0};
-    } else if (EPI == EPI_TS) {  // <out, A> and |out|^2
-      float2 re = make_float2(0.f, 0.f), ip = re, im = re, nn = re;
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        re = F2(o[2 * k], a[2 * k], re);
-        re = F2(o[2 * k + 1], a[2 * k + 1], re);
-        ip = F2(o[2 * k], a[2 * k + 1], ip);
-        im = F2(o[2 * k + 1], a[2 * k], im);
-        nn = F2(o[2 * k], o[2 * k], nn);
-        nn = F2(o[2 * k + 1], o[2 * k + 1], nn);
-      }
-      const float2 imag = S2(ip, im);
-      r0 = D4S{re.x, imag.x, 0, nn.x};
-      r1 = D4S{re.y, imag.y, 0, nn.y};
-    }
+    pair_epilogue<BF16P, EPI>(acc, a, cA2, cH2, out, B, P, i, r0, r1);
     if (EPI == EPI_DOTR || EPI == EPI_TS)
       group_reduce_store2<1>(r0, r1, part + (size_t)(2 * P) * nbx + sb, part + (size_t)(2 * P + 1) * nbx + sb, true);
     __syncthreads();  // the next item's copies overwrite the planes
