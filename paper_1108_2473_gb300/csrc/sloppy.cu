@@ -270,29 +270,7 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// fixed-order block reduction of one or two D4S (all ST threads participate)
-__device__ __forceinline__ void block_reduce_store(D4S v, D4S *dst) {
-  __shared__ D4S sh[ST / 32];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  v.a = warp_sum_d(v.a);
-  v.b = warp_sum_d(v.b);
-  v.c = warp_sum_d(v.c);
-  v.d = warp_sum_d(v.d);
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    D4S t = sh[0];
-#pragma unroll
-    for (int k = 1; k < ST / 32; ++k) {
-      t.a += sh[k].a;
-      t.b += sh[k].b;
-      t.c += sh[k].c;
-      t.d += sh[k].d;
-    }
-    *dst = t;
-  }
-  __syncthreads();
-}
+// fixed-order block reduction of two D4S (all ST threads participate)
 __device__ __forceinline__ void block_reduce_store2(D4S v0, D4S v1, D4S *dst0, D4S *dst1) {
   __shared__ D4S sh[2][ST / 32];
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
